@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: tet elements/s of the fused force + K*w map and the implicit
+step, on the 64^3 mixed-precision neo-Hookean cube-grid workload.
+
+Workload (stands in for the paper's FEM meshes, which are not available):
+64 x 64 x 64 cubes, 5 tets per cube (274,625 vertices, 1,310,720 tets),
+rest positions jittered by 1% of the edge, E log-uniform in [1e4, 1e6] per tet,
+nu = 0.4, FP32 element math.  A timed step is one fused force + K*w map over
+every tet (the metric's kernel) with inputs resident in HBM; L2 (129 MB) is
+flushed by a 256 MB write before every timed step.  The implicit step (FP32
+element maps + FP64 CG, 10 steps, rtol 1e-8) is timed in the same run next to
+the plain FP64 form.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the baseline for this path: there is no reference code to run).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, each rank runs an independent replica of the
+workload (the single-mesh path is not sharded), value = all ranks' tets / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import meshgen  # noqa: E402
+
+METRIC = "tet elements/s for force+K·v (% of HBM roofline); implicit-step ms vs FP64 form"
+UNIT = "tets/s"
+N_SIDE = 64
+SEED = 2
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload():
+    m = meshgen.cube_grid(N_SIDE, jitter=0.01, seed=SEED)
+    mu, lam = meshgen.material_loguniform_E(m.n_tets, 1e4, 1e6, 0.4, SEED)
+    u = meshgen.random_displacement(m.X, N_SIDE, amp=0.05, seed=SEED, smooth=0.01)
+    w = meshgen.random_field(m.n_verts, seed=SEED)
+    return m, mu, lam, u, w
+
+
+def algorithmic_bytes_per_tet(n_verts, n_tets):
+    """Bytes the fused FP32 map must move once per tet: keys (4 x int32),
+    Dm^-1 (9 x f32), V (f32), per-tet (mu, lambda) (2 x f32), plus per vertex
+    u and w read and f and K*w written (4 x 3 x f32) amortised over tets."""
+    per_tet = 16 + 36 + 4 + 8
+    per_vertex = 4 * 12
+    return per_tet + per_vertex * n_verts / n_tets
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for name, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds, m, mu, lam, u, w):
+    """FP64 oracle force + K*w on a contiguous sample of the same mesh's tets,
+    timed on this host's cores (single thread)."""
+    from oracle import fem
+    sample = min(m.n_tets, 131072)
+    tets = m.tets[:sample]
+    B, V = fem.rest_shape(m.X, tets)
+    mu_s, lam_s = mu[:sample], lam[:sample]
+    x = m.X + u
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        fem.tet_forces(x, tets, B, V, mu_s, lam_s, fem.NEOHOOKEAN)
+        fem.tet_Kv(x, w, tets, B, V, mu_s, lam_s, fem.NEOHOOKEAN)
+        done += sample
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle force+K*w over the first {sample} tets of the 64^3 mesh, "
+                      f"repeated for {el:.1f} s ({done} tet evaluations), numpy single thread"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    m, mu, lam, u, w = workload()
+    from oracle import fem
+    sample = 65536
+    tets = m.tets[:sample]
+    B, V = fem.rest_shape(m.X, tets)
+    x = m.X + u
+    for _ in range(args.warmup):
+        fem.tet_forces(x, tets, B, V, mu[:sample], lam[:sample], fem.NEOHOOKEAN)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fem.tet_forces(x, tets, B, V, mu[:sample], lam[:sample], fem.NEOHOOKEAN)
+        fem.tet_Kv(x, w, tets, B, V, mu[:sample], lam[:sample], fem.NEOHOOKEAN)
+    el = time.perf_counter() - t0
+    value = sample * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "64^3 cube grid, 5 tets/cube, NH, E log-uniform [1e4,1e6], nu 0.4",
+                       "n_tets": m.n_tets, "n_verts": m.n_verts, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: FP64 oracle force+K*w over the first {sample} tets"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1506_07577_gb300 import abi
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    m, mu, lam, u, w = workload()
+    stream = torch.cuda.Stream(device=dev)
+    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream)
+    u32 = dm.vertex_field("u32", torch.float32, value=u)
+    w32 = dm.vertex_field("w32", torch.float32, value=w)
+    f = dm.vertex_field("f", torch.float32)
+    Kw = dm.vertex_field("Kw", torch.float32)
+    opts = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_ATOMIC)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    nt = m.n_tets
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        f.zero_()
+        Kw.zero_()
+        if ev is not None:
+            ev[1].record(stream)
+        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", opts)
+        if ev is not None:
+            ev[2].record(stream)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            flush.fill_(float(i))
+            step()
+        abi.ebb_ctx_sync(dm.ctx)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            step(evs[k])
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        abi.ebb_ctx_sync(dm.ctx)
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    kern_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = nt * args.steps * world / total_s
+
+    # ---- end to end: pinned host inputs -> device -> map -> host outputs ----
+    uh = u32.cpu().pin_memory()
+    wh = w32.cpu().pin_memory()
+    fh = torch.empty_like(f, device="cpu").pin_memory()
+    kh = torch.empty_like(Kw, device="cpu").pin_memory()
+    with torch.cuda.stream(stream):
+        e2e_ms = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u32.copy_(uh, non_blocking=True)
+            w32.copy_(wh, non_blocking=True)
+            step()
+            fh.copy_(f, non_blocking=True)
+            kh.copy_(Kw, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = (uh.numel() + wh.numel()) * 4
+    d2h = (fh.numel() + kh.numel()) * 4
+
+    # ---- parity spot check on sampled vertices (FP64 oracle, rank 0) ----
+    err = None
+    if rank == 0:
+        from oracle import fem
+        rng = np.random.default_rng(0)
+        sample = rng.choice(m.n_verts, size=32, replace=False)
+        sel = np.isin(m.tets, sample).any(axis=1)
+        sub = m.tets[sel]
+        B, V = fem.rest_shape(m.X, sub)
+        x = m.X + u
+        fo = fem.tet_forces(x, sub, B, V, mu[sel], lam[sel], fem.NEOHOOKEAN)[sample]
+        ko = fem.tet_Kv(x, w, sub, B, V, mu[sel], lam[sel], fem.NEOHOOKEAN)[sample]
+        fg = fh.double().numpy().T[sample]
+        kg = kh.double().numpy().T[sample]
+        err = max(float(np.max(np.abs(fg - fo)) / np.max(np.abs(fo))),
+                  float(np.max(np.abs(kg - ko)) / np.max(np.abs(ko))))
+
+    # ---- implicit step: mixed form vs plain FP64 form -------------------
+    imp = implicit_steps(dm, m, abi, torch, stream, args)
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    peak, peak_kind = _peaks()
+    bpt = algorithmic_bytes_per_tet(m.n_verts, nt)
+    kern_avg = sum(kern_ms) / len(kern_ms) / 1e3
+    achieved = bpt * nt / kern_avg / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic>",
+            "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
+
+    dm.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64^3 cube grid, 5 tets/cube (274,625 verts, 1,310,720 tets), NH, "
+                                   "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, atomic scatter",
+                       "n_tets": nt, "n_verts": m.n_verts, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": nt * args.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "parity_max_rel_err_sampled": err,
+            "implicit_step": imp}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, m, mu, lam, u, w)
+    print(json.dumps(line), flush=True)
+
+
+def implicit_steps(dm, m, abi, torch, stream, args):
+    """10 implicit steps from rest under gravity, mixed form and FP64 form."""
+    uu = dm.vertex_field("u_state", torch.float64)
+    vv = dm.vertex_field("v_state", torch.float64)
+    dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(uu.device))
+    out = {}
+    res = {}
+    for name, prec in (("mixed", abi.EBB_PREC_F32), ("fp64", abi.EBB_PREC_F64)):
+        uu.zero_()
+        vv.zero_()
+        prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, precision=prec, max_iters=1000, rtol=1e-8)
+        times, iters = [], []
+        with torch.cuda.stream(stream):
+            for s in range(args.implicit_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rep = abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u_state", "v_state", "pinned", prm)
+                times.append(time.perf_counter() - t0)
+                iters.append(rep.iters)
+        res[name] = (uu.clone(), vv.clone())
+        out[name] = {"ms_per_step": 1e3 * sum(times) / len(times), "cg_iters": iters}
+    du = (res["mixed"][1] - res["fp64"][1]).abs().max().item() / res["fp64"][1].abs().max().item()
+    return {"steps": args.implicit_steps, "dt": 1e-3, "rtol": 1e-8,
+            "mixed_ms_per_step": out["mixed"]["ms_per_step"], "fp64_ms_per_step": out["fp64"]["ms_per_step"],
+            "speedup_vs_fp64_form": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
+            "cg_iters_mixed": out["mixed"]["cg_iters"], "cg_iters_fp64": out["fp64"]["cg_iters"],
+            "v_rel_diff_mixed_vs_fp64_form": du}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--implicit-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

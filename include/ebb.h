@@ -1,0 +1,223 @@
+/*
+ * ebb.h -- C ABI of the GB300 tetrahedral-FEM map library.
+ *
+ * The library implements the data-parallel hot path of Ebb's relational
+ * simulation model (Bernstein et al., "Ebb: A DSL for Physical Simulation on
+ * CPUs and GPUs", arXiv:1506.07577) for one sm_103a GPU:
+ *
+ *   - relations (unordered element sets) with fields bound to them
+ *     (Section 4.1, Section 5.1);
+ *   - a key-field tets.v[4] linking each tetrahedron to four vertices
+ *     (Section 5.1 "Key-fields", Section 5.2 "Example: FEM tetmesh");
+ *   - kernels mapped over the tets relation whose per-tet results are
+ *     reduced with += into vertex fields (Section 4.1, Section 6.2
+ *     "Reductions");
+ *   - the implicit backward-Euler step with a Jacobi-preconditioned CG solve
+ *     built on those maps (Section 7.2, Vega, StVK; Section 7.3, FreeFem++,
+ *     neo-Hookean).
+ *
+ * Conventions used by every call:
+ *   - All pointers handed to the library are DEVICE pointers on the context's
+ *     device unless stated otherwise.  The caller owns them; the library
+ *     borrows them and never frees them (interop without marshalling,
+ *     Section 4.3).
+ *   - Fields are column stores (Section 6.1 "Data Layout"): a field with
+ *     ncomp components over a relation of n rows occupies ncomp contiguous
+ *     planes of n elements each (component c of row i at ptr[c*n + i]).
+ *   - Every call returns an ebb_status_t; 0 is success.  No call aborts or
+ *     throws.  ebb_last_error() gives a human-readable message for the last
+ *     failure on a context.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous
+ *     unless stated otherwise.  Errors detected on the device (an inverted
+ *     element, a bad key) are raised through a device status word that is
+ *     read at the next synchronising call (ebb_ctx_sync,
+ *     ebb_relation_finalize, ebb_cg_implicit_step).
+ *   - Two contexts may share a device; a context must not be used from two
+ *     host threads at once.
+ */
+#ifndef EBB_GB300_H
+#define EBB_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ebb_ctx_s* ebb_ctx_t;
+typedef struct ebb_rel_s* ebb_rel_t;
+typedef int32_t ebb_status_t;
+
+/* ---- status codes ------------------------------------------------------ */
+#define EBB_OK                 0
+#define EBB_ERR_ARG            1  /* bad argument (null, size, dtype, unknown name) */
+#define EBB_ERR_KEY            2  /* key-field value < 0 or >= target size (Section 5.1) */
+#define EBB_ERR_PHASE          3  /* one field used in two phases by one map (Section 4.1) */
+#define EBB_ERR_INVERTED       4  /* rest tet with det(Dm) <= 0, or J <= 0 in neo-Hookean */
+#define EBB_ERR_CG_BREAKDOWN   5  /* p^T A p <= 0 inside PCG */
+#define EBB_ERR_NOT_CONVERGED  6  /* PCG hit max_iters above the tolerance */
+#define EBB_ERR_TIMEOUT        7  /* a bounded device wait gave up */
+#define EBB_ERR_CUDA           8  /* a CUDA runtime call failed */
+#define EBB_ERR_STATE          9  /* call out of order (e.g. map before finalize) */
+#define EBB_ERR_NOMEM         10  /* device allocation failed */
+
+typedef enum { EBB_F32 = 1, EBB_F64 = 2, EBB_I32 = 3, EBB_U8 = 4 } ebb_dtype_t;
+
+/* Material models.  Section 7.2 names St. Venant-Kirchhoff, Section 7.3
+ * neo-Hookean; the paper prints neither formula, the library uses the
+ * textbook forms:
+ *   StVK: E = (F^T F - I)/2, P = F (2 mu E + lambda tr(E) I)
+ *   NH:   P = mu (F - F^-T) + lambda ln(J) F^-T                               */
+typedef enum { EBB_STVK = 0, EBB_NEOHOOKEAN = 1 } ebb_model_t;
+
+/* Element arithmetic.  EBB_PREC_F64: FP64 everywhere.  EBB_PREC_F32: element
+ * maps in FP32 (Dm^-1 and volumes precomputed in FP64, stored in FP32); in
+ * ebb_cg_implicit_step the CG vectors, dot products and updates stay FP64. */
+typedef enum { EBB_PREC_F64 = 0, EBB_PREC_F32 = 1 } ebb_precision_t;
+
+/* Scatter (+= reduction) strategy.  ATOMIC: hardware atomic adds (Section
+ * 6.2 "Reductions").  COLOR: tets grouped by a vertex-conflict colouring, one
+ * colour at a time with plain read-modify-write; deterministic run to run
+ * (the colouring approach of Liszt discussed in Section 7.4).  AUTO: the
+ * library's tuned choice. */
+typedef enum { EBB_REDUCE_ATOMIC = 0, EBB_REDUCE_COLOR = 1, EBB_REDUCE_AUTO = 2 } ebb_reduce_t;
+
+/* ebb_relation_finalize flags */
+#define EBB_FINALIZE_COLOR    1u  /* build the vertex-conflict colouring of tets */
+
+/* map flags */
+#define EBB_MAP_ZERO_OUT      1u  /* zero the output fields before reducing into them */
+
+typedef struct {
+  ebb_model_t model;
+  double mu, lambda;            /* Lame parameters when the tets relation binds
+                                   no per-tet "mu"/"lambda" fields */
+  ebb_precision_t precision;
+  ebb_reduce_t reduce;
+  uint32_t flags;               /* EBB_MAP_* */
+} ebb_map_opts_t;
+
+typedef struct {
+  ebb_model_t model;
+  double mu, lambda;            /* as in ebb_map_opts_t */
+  ebb_precision_t precision;    /* F64: all FP64.  F32: mixed (see above) */
+  ebb_reduce_t reduce;
+  double dt;                    /* time step */
+  double gravity[3];            /* body acceleration g */
+  double rho;                   /* density; lumped mass m_i = sum rho V / 4 */
+  int32_t max_iters;            /* PCG iteration cap */
+  double rtol;                  /* stop when ||r||_2 <= rtol ||b||_2 */
+  int32_t fail_on_max_iters;    /* nonzero: hitting max_iters above rtol
+                                   returns EBB_ERR_NOT_CONVERGED */
+} ebb_step_params_t;
+
+typedef struct {
+  int32_t iters;                /* PCG iterations performed */
+  double rel_residual;          /* ||r||_2 / ||b||_2 at exit (0 if b == 0) */
+  ebb_status_t status;          /* same value the call returns */
+} ebb_cg_report_t;
+
+/* ---- contexts ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`, enqueuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: EBB_ERR_ARG (null out, bad device), EBB_ERR_CUDA. */
+ebb_status_t ebb_ctx_create(ebb_ctx_t* out, int device, void* cuda_stream);
+
+/* Change the stream later calls enqueue on. */
+ebb_status_t ebb_ctx_set_stream(ebb_ctx_t ctx, void* cuda_stream);
+
+/* Destroy a context and every relation created on it, freeing the library's
+ * internal device buffers (never the caller's).  NULL is accepted. */
+ebb_status_t ebb_ctx_destroy(ebb_ctx_t ctx);
+
+/* Synchronise the context's stream and return (then clear) the first error
+ * raised on the device since the last synchronising call. */
+ebb_status_t ebb_ctx_sync(ebb_ctx_t ctx);
+
+/* Message describing the last failed call on ctx ("" if none).  The string is
+ * owned by the context and valid until its next call. */
+const char* ebb_last_error(ebb_ctx_t ctx);
+
+/* ---- relations and fields (Section 4.1, Section 5.1) ------------------- */
+
+/* Create a relation of `size` rows (size >= 0).  The handle lives until the
+ * context is destroyed.  Errors: EBB_ERR_ARG. */
+ebb_status_t ebb_relation_create(ebb_ctx_t ctx, const char* name, int64_t size,
+                                 ebb_rel_t* out);
+
+/* Bind a caller-owned device array as field `name` of relation `rel`
+ * (ncomp planes of rel's size, dtype elements).  `key_target` is non-NULL
+ * exactly when the field is a key-field into that relation (dtype must be
+ * EBB_I32).  Rebinding a name replaces the pointer.  Fields the library
+ * knows by name:
+ *   verts.X       F64, 3   rest positions (read at finalize)
+ *   tets.v        I32, 4   key-field into verts (tets.v[4], Section 5.2)
+ *   tets.mu       F64, 1   optional per-tet Lame mu
+ *   tets.lambda   F64, 1   optional per-tet Lame lambda
+ * Other names are vertex fields used by maps (displacement, velocity,
+ * directions, outputs).  Errors: EBB_ERR_ARG. */
+ebb_status_t ebb_field_bind(ebb_rel_t rel, const char* name, ebb_dtype_t dtype,
+                            int32_t ncomp, void* device_ptr, ebb_rel_t key_target);
+
+/* Prepare a tets relation for maps: validates every key of tets.v against its
+ * target (EBB_ERR_KEY, with the first bad row in the message), computes per
+ * tet B = Dm^-1 and V = det(Dm)/6 in FP64 from verts.X (EBB_ERR_INVERTED if
+ * det(Dm) <= 0) plus FP32 copies, snapshots per-tet Lame fields, and with
+ * EBB_FINALIZE_COLOR builds the vertex-conflict colouring.  Synchronous.
+ * Rebinding verts.X, tets.v, tets.mu or tets.lambda requires finalizing
+ * again. */
+ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags);
+
+/* ---- maps over tets (Section 4.1 kernels, Section 6.2 reductions) ------- */
+/* Vertex-field arguments are names of fields bound on the key target of
+ * tets.v.  `u` is the displacement from the rest shape (x = X + u), so
+ * F = Ds Dm^-1 = I + Du Dm^-1.  Field dtypes must match opts->precision
+ * (F64 or F32, 3 components).  Outputs are reduce(+=) targets: the map adds
+ * into them (zero them first or pass EBB_MAP_ZERO_OUT).  An output that is
+ * also an input of the same map is a phase error (EBB_ERR_PHASE). */
+
+/* f += elastic force, f = -dE/dx (per tet H = -V P(F) Dm^-T; corners 1..3 get
+ * the columns of H, corner 0 minus their sum). */
+ebb_status_t ebb_map_tet_forces(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                const char* f_out, const ebb_map_opts_t* opts);
+
+/* Kw += K(u) w, K = d^2E/dx^2 (matrix-free, per tet V dP(F; dF) Dm^-T with
+ * dF = dDs(w) Dm^-1). */
+ebb_status_t ebb_map_tet_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                            const char* w, const char* Kw_out,
+                            const ebb_map_opts_t* opts);
+
+/* Fused: f += force and Kw += K(u) w in one pass sharing gathers and F. */
+ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                  const char* w, const char* f_out,
+                                  const char* Kw_out, const ebb_map_opts_t* opts);
+
+/* d += diag(K(u)) (closed form per tet corner and component): the Jacobi
+ * preconditioner of Section 7.2. */
+ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                               const char* d_out, const ebb_map_opts_t* opts);
+
+/* ---- implicit step (Section 7.2, Section 7.3) --------------------------- */
+
+/* One linearised backward-Euler step, in place on the F64 vertex fields
+ * `u` (displacement) and `v` (velocity):
+ *   A = M + dt^2 K(x_n),  b = dt (f(x_n) + M g - dt K(x_n) v_n),
+ *   A dv = b by Jacobi PCG from dv = 0 (rows/cols of pinned vertices
+ *   removed), v += dv, u += dt v.
+ * `pinned` names a U8 or I32 one-component vertex field (nonzero = pinned),
+ * or is NULL.  The PCG loop runs on the device without host round trips
+ * except one status read per batch of iterations.  Synchronous; fills
+ * *report (may be NULL).  Errors: EBB_ERR_CG_BREAKDOWN,
+ * EBB_ERR_NOT_CONVERGED (if requested), EBB_ERR_INVERTED, plus argument
+ * errors. */
+ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                  const char* v, const char* pinned,
+                                  const ebb_step_params_t* params,
+                                  ebb_cg_report_t* report);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBB_GB300_H */

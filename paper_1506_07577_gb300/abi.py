@@ -1,0 +1,196 @@
+"""Thin ctypes binding of the C ABI in ``include/ebb.h`` (same names).
+
+Argument marshalling only: every step of the tet path runs in the CUDA
+library ``libebb_gb300.so``.  There is no fallback: importing this module
+without the built library raises ``ImportError``.  Device memory comes from
+PyTorch tensors (their ``data_ptr()`` is handed to the library, which borrows
+it); the stream is a ``torch.cuda.Stream`` or ``None`` (legacy default).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libebb_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the tet FEM path has no CPU fallback)")
+
+_lib = C.CDLL(LIB_PATH)
+
+# ---- constants (mirror include/ebb.h) ------------------------------------
+EBB_OK = 0
+EBB_ERR_ARG = 1
+EBB_ERR_KEY = 2
+EBB_ERR_PHASE = 3
+EBB_ERR_INVERTED = 4
+EBB_ERR_CG_BREAKDOWN = 5
+EBB_ERR_NOT_CONVERGED = 6
+EBB_ERR_TIMEOUT = 7
+EBB_ERR_CUDA = 8
+EBB_ERR_STATE = 9
+EBB_ERR_NOMEM = 10
+STATUS_NAMES = {v: k for k, v in dict(globals()).items() if k.startswith("EBB_ERR_") or k == "EBB_OK"}
+
+EBB_F32, EBB_F64, EBB_I32, EBB_U8 = 1, 2, 3, 4
+EBB_STVK, EBB_NEOHOOKEAN = 0, 1
+EBB_PREC_F64, EBB_PREC_F32 = 0, 1
+EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO = 0, 1, 2
+EBB_FINALIZE_COLOR = 1
+EBB_MAP_ZERO_OUT = 1
+
+ebb_ctx_t = C.c_void_p
+ebb_rel_t = C.c_void_p
+ebb_status_t = C.c_int32
+
+
+class ebb_map_opts_t(C.Structure):
+    _fields_ = [("model", C.c_int), ("mu", C.c_double), ("lambda_", C.c_double),
+                ("precision", C.c_int), ("reduce", C.c_int), ("flags", C.c_uint32)]
+
+
+class ebb_step_params_t(C.Structure):
+    _fields_ = [("model", C.c_int), ("mu", C.c_double), ("lambda_", C.c_double),
+                ("precision", C.c_int), ("reduce", C.c_int), ("dt", C.c_double),
+                ("gravity", C.c_double * 3), ("rho", C.c_double), ("max_iters", C.c_int32),
+                ("rtol", C.c_double), ("fail_on_max_iters", C.c_int32)]
+
+
+class ebb_cg_report_t(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("rel_residual", C.c_double), ("status", C.c_int32)]
+
+
+_P = C.c_char_p
+_SIGS = {
+    "ebb_ctx_create": ([C.POINTER(ebb_ctx_t), C.c_int, C.c_void_p], ebb_status_t),
+    "ebb_ctx_set_stream": ([ebb_ctx_t, C.c_void_p], ebb_status_t),
+    "ebb_ctx_destroy": ([ebb_ctx_t], ebb_status_t),
+    "ebb_ctx_sync": ([ebb_ctx_t], ebb_status_t),
+    "ebb_last_error": ([ebb_ctx_t], C.c_char_p),
+    "ebb_relation_create": ([ebb_ctx_t, _P, C.c_int64, C.POINTER(ebb_rel_t)], ebb_status_t),
+    "ebb_field_bind": ([ebb_rel_t, _P, C.c_int, C.c_int32, C.c_void_p, ebb_rel_t], ebb_status_t),
+    "ebb_relation_finalize": ([ebb_rel_t, C.c_uint32], ebb_status_t),
+    "ebb_map_tet_forces": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_map_tet_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_map_tet_force_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
+                              C.POINTER(ebb_cg_report_t)], ebb_status_t),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+class EbbError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _b(s):
+    return None if s is None else s.encode()
+
+
+def _check(ctx, status):
+    if status != EBB_OK:
+        msg = _lib.ebb_last_error(ctx).decode() if ctx else ""
+        raise EbbError(status, msg)
+    return status
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+# ---- same-name wrappers ----------------------------------------------------
+def ebb_ctx_create(device=0, stream=None):
+    h = ebb_ctx_t()
+    st = _lib.ebb_ctx_create(C.byref(h), int(device), _stream_handle(stream))
+    if st != EBB_OK:
+        raise EbbError(st, "ebb_ctx_create failed")
+    return h
+
+
+def ebb_ctx_set_stream(ctx, stream):
+    return _check(ctx, _lib.ebb_ctx_set_stream(ctx, _stream_handle(stream)))
+
+
+def ebb_ctx_destroy(ctx):
+    return _lib.ebb_ctx_destroy(ctx)
+
+
+def ebb_ctx_sync(ctx):
+    return _check(ctx, _lib.ebb_ctx_sync(ctx))
+
+
+def ebb_last_error(ctx):
+    return _lib.ebb_last_error(ctx).decode()
+
+
+def ebb_relation_create(ctx, name, size):
+    h = ebb_rel_t()
+    _check(ctx, _lib.ebb_relation_create(ctx, _b(name), int(size), C.byref(h)))
+    return h
+
+
+_DT = {"torch.float32": EBB_F32, "torch.float64": EBB_F64, "torch.int32": EBB_I32, "torch.uint8": EBB_U8}
+
+
+def ebb_field_bind(ctx, rel, name, tensor, key_target=None):
+    """Bind a CUDA tensor shaped (ncomp, rows) or (rows,) as a column-store
+    field (ncomp contiguous planes).  The tensor must stay alive while bound."""
+    if not tensor.is_cuda or not tensor.is_contiguous():
+        raise ValueError("fields must be contiguous CUDA tensors")
+    dt = _DT.get(str(tensor.dtype))
+    if dt is None:
+        raise ValueError(f"unsupported dtype {tensor.dtype}")
+    ncomp = 1 if tensor.dim() == 1 else int(tensor.shape[0])
+    return _check(ctx, _lib.ebb_field_bind(rel, _b(name), dt, ncomp, C.c_void_p(tensor.data_ptr()), key_target))
+
+
+def ebb_relation_finalize(ctx, rel, flags=0):
+    return _check(ctx, _lib.ebb_relation_finalize(rel, int(flags)))
+
+
+def map_opts(model, mu=0.0, lam=0.0, precision=EBB_PREC_F64, reduce=EBB_REDUCE_ATOMIC, flags=0):
+    return ebb_map_opts_t(int(model), float(mu), float(lam), int(precision), int(reduce), int(flags))
+
+
+def ebb_map_tet_forces(ctx, tets, u, f_out, opts):
+    return _check(ctx, _lib.ebb_map_tet_forces(ctx, tets, _b(u), _b(f_out), C.byref(opts)))
+
+
+def ebb_map_tet_Kv(ctx, tets, u, w, Kw_out, opts):
+    return _check(ctx, _lib.ebb_map_tet_Kv(ctx, tets, _b(u), _b(w), _b(Kw_out), C.byref(opts)))
+
+
+def ebb_map_tet_force_Kv(ctx, tets, u, w, f_out, Kw_out, opts):
+    return _check(ctx, _lib.ebb_map_tet_force_Kv(ctx, tets, _b(u), _b(w), _b(f_out), _b(Kw_out), C.byref(opts)))
+
+
+def ebb_map_tet_diagK(ctx, tets, u, d_out, opts):
+    return _check(ctx, _lib.ebb_map_tet_diagK(ctx, tets, _b(u), _b(d_out), C.byref(opts)))
+
+
+def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,
+                reduce=EBB_REDUCE_ATOMIC, max_iters=1000, rtol=1e-8, fail_on_max_iters=False):
+    g = (C.c_double * 3)(*[float(x) for x in gravity])
+    return ebb_step_params_t(int(model), float(mu), float(lam), int(precision), int(reduce), float(dt), g,
+                             float(rho), int(max_iters), float(rtol), int(bool(fail_on_max_iters)))
+
+
+def ebb_cg_implicit_step(ctx, tets, u, v, pinned, params):
+    rep = ebb_cg_report_t()
+    _check(ctx, _lib.ebb_cg_implicit_step(ctx, tets, _b(u), _b(v), _b(pinned), C.byref(params), C.byref(rep)))
+    return rep

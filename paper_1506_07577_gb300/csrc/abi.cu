@@ -1,0 +1,517 @@
+// C ABI entry points: contexts, relations, fields, finalize and map calls.
+//
+// The runtime side of Ebb's relational model (Section 6.1): relations are
+// row counts with column-store fields bound to them; a key-field links tets
+// to vertices (Section 5.1); finalize validates keys (accesses cannot go out
+// of bounds, Section 5.1) and precomputes the per-tet rest-shape data the
+// maps read.  The phase rule of Section 4.1 is enforced per map call: a
+// field that a map reduces into may not also be read by it.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ebb_internal.h"
+
+using namespace ebb;
+
+namespace ebb {
+
+ebb_status_t set_error(ebb_ctx_s* ctx, ebb_status_t code, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return code;
+}
+
+ebb_status_t cuda_check(ebb_ctx_s* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return EBB_OK;
+  return set_error(ctx, EBB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace ebb
+
+namespace {
+
+size_t dtype_size(ebb_dtype_t d) {
+  switch (d) {
+    case EBB_F32: return 4;
+    case EBB_F64: return 8;
+    case EBB_I32: return 4;
+    case EBB_U8: return 1;
+  }
+  return 0;
+}
+
+// Rest-shape precomputation: B = Dm^-1 and V = det(Dm)/6 in FP64, plus FP32
+// copies.  Dm = [X1-X0, X2-X0, X3-X0] with X read through the keys.
+__global__ void rest_shape_kernel(int nt, int nv, const int4* __restrict__ keys, const double* __restrict__ X,
+                                  double* B64, double* V64, float* B32, float* V32, int* err) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int4 k = keys[t];
+  const int kk[4] = {k.x, k.y, k.z, k.w};
+  double D[9];
+  for (int c = 0; c < 3; ++c) {
+    const double x0 = X[(size_t)c * nv + kk[0]];
+    for (int j = 0; j < 3; ++j) D[c * 3 + j] = X[(size_t)c * nv + kk[j + 1]] - x0;
+  }
+  const double c00 = D[4] * D[8] - D[5] * D[7];
+  const double c01 = D[5] * D[6] - D[3] * D[8];
+  const double c02 = D[3] * D[7] - D[4] * D[6];
+  const double det = D[0] * c00 + D[1] * c01 + D[2] * c02;
+  if (!(det > 0.0)) {
+    if (atomicCAS(err + ERRW_CODE, 0, EBB_ERR_INVERTED) == 0) err[ERRW_INDEX] = t;
+  }
+  const double id = 1.0 / det;
+  // inverse = adj / det, adj = cof^T
+  double Bm[9];
+  Bm[0] = c00 * id;
+  Bm[3] = c01 * id;
+  Bm[6] = c02 * id;
+  Bm[1] = (D[2] * D[7] - D[1] * D[8]) * id;
+  Bm[4] = (D[0] * D[8] - D[2] * D[6]) * id;
+  Bm[7] = (D[1] * D[6] - D[0] * D[7]) * id;
+  Bm[2] = (D[1] * D[5] - D[2] * D[4]) * id;
+  Bm[5] = (D[2] * D[3] - D[0] * D[5]) * id;
+  Bm[8] = (D[0] * D[4] - D[1] * D[3]) * id;
+  for (int i = 0; i < 9; ++i) {
+    B64[(size_t)i * nt + t] = Bm[i];
+    B32[(size_t)i * nt + t] = (float)Bm[i];
+  }
+  V64[t] = det / 6.0;
+  V32[t] = (float)(det / 6.0);
+}
+
+__global__ void copy_material_kernel(int nt, const double* __restrict__ mu, const double* __restrict__ lam,
+                                     double* mu64, double* lam64, float* mu32, float* lam32) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const double m = mu[t], l = lam[t];
+  mu64[t] = m;
+  lam64[t] = l;
+  mu32[t] = (float)m;
+  lam32[t] = (float)l;
+}
+
+void free_tet_data(ebb_rel_s* r) {
+  cudaFree(r->keys);
+  r->keys = nullptr;
+  cudaFree(r->s64.B);
+  cudaFree(r->s64.V);
+  cudaFree(r->s64.mu);
+  cudaFree(r->s64.lam);
+  cudaFree(r->s32.B);
+  cudaFree(r->s32.V);
+  cudaFree(r->s32.mu);
+  cudaFree(r->s32.lam);
+  r->s64 = TetStreams<double>();
+  r->s32 = TetStreams<float>();
+  free_colouring(r);
+  free_step_scratch(r);
+  r->finalized = false;
+}
+
+const Field* find_field(const ebb_rel_s* r, const char* name) {
+  if (!r || !name) return nullptr;
+  auto it = r->fields.find(name);
+  return it == r->fields.end() ? nullptr : &it->second;
+}
+
+ebb_status_t read_device_error(ebb_ctx_s* ctx) {
+  cudaError_t e = cudaMemcpyAsync(ctx->h_err, ctx->d_err, ERRW_WORDS * sizeof(int), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "reading device status");
+  const int code = ctx->h_err[ERRW_CODE];
+  if (code == 0) return EBB_OK;
+  const int idx = ctx->h_err[ERRW_INDEX];
+  cudaMemsetAsync(ctx->d_err, 0, ERRW_WORDS * sizeof(int), ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  char buf[160];
+  if (code == EBB_ERR_INVERTED)
+    snprintf(buf, sizeof buf, "inverted element (det <= 0) at tet row %d", idx);
+  else if (code == EBB_ERR_KEY)
+    snprintf(buf, sizeof buf, "key out of range at row %d", idx);
+  else if (code == EBB_ERR_TIMEOUT)
+    snprintf(buf, sizeof buf, "bounded device wait timed out (site %d)", idx);
+  else
+    snprintf(buf, sizeof buf, "device error %d at index %d", code, idx);
+  return set_error(ctx, code, buf);
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* pa = (const char*)a;
+  const char* pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
+}
+
+// Resolve a vertex field used by a map; checks dtype and width.
+ebb_status_t vertex_field(ebb_ctx_s* ctx, ebb_rel_s* tets, const char* name, ebb_dtype_t want, int ncomp,
+                          void** out) {
+  if (!name) return set_error(ctx, EBB_ERR_ARG, "null field name");
+  const Field* f = find_field(tets->verts, name);
+  if (!f) return set_error(ctx, EBB_ERR_ARG, std::string("no vertex field named '") + name + "'");
+  if (f->dtype != want || f->ncomp != ncomp)
+    return set_error(ctx, EBB_ERR_ARG, std::string("vertex field '") + name + "' has the wrong dtype or width");
+  *out = f->ptr;
+  return EBB_OK;
+}
+
+struct MapCall {
+  const char* in[2] = {nullptr, nullptr};
+  const char* out[3] = {nullptr, nullptr, nullptr};
+  int nin = 0, nout = 0;
+};
+
+// One entry point for the four map calls.
+ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, const ebb_map_opts_t* opts) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!tets || !opts) return set_error(ctx, EBB_ERR_ARG, "null relation or options");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (opts->model != EBB_STVK && opts->model != EBB_NEOHOOKEAN)
+    return set_error(ctx, EBB_ERR_ARG, "unknown material model");
+  if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
+    return set_error(ctx, EBB_ERR_ARG, "unknown precision");
+  ebb_reduce_t reduce = opts->reduce;
+  if (reduce == EBB_REDUCE_AUTO) reduce = EBB_REDUCE_ATOMIC;
+  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR)
+    return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
+  if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
+    return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
+  const bool f64 = opts->precision == EBB_PREC_F64;
+  const ebb_dtype_t dt = f64 ? EBB_F64 : EBB_F32;
+  const size_t bytes = (size_t)tets->verts->size * 3 * (f64 ? 8 : 4);
+
+  void* in[2] = {nullptr, nullptr};
+  void* out[3] = {nullptr, nullptr, nullptr};
+  for (int i = 0; i < mc.nin; ++i) {
+    ebb_status_t s = vertex_field(ctx, tets, mc.in[i], dt, 3, &in[i]);
+    if (s) return s;
+  }
+  for (int i = 0; i < mc.nout; ++i) {
+    ebb_status_t s = vertex_field(ctx, tets, mc.out[i], dt, 3, &out[i]);
+    if (s) return s;
+  }
+  // Phase rule: a reduce target may not be read by the same map, nor be
+  // reduced into twice.
+  for (int i = 0; i < mc.nout; ++i) {
+    for (int j = 0; j < mc.nin; ++j)
+      if (ranges_overlap(out[i], bytes, in[j], bytes))
+        return set_error(ctx, EBB_ERR_PHASE, std::string("field '") + mc.out[i] +
+                                                 "' is both reduced into and read by one map");
+    for (int j = i + 1; j < mc.nout; ++j)
+      if (ranges_overlap(out[i], bytes, out[j], bytes))
+        return set_error(ctx, EBB_ERR_PHASE, "two reduce targets of one map overlap");
+  }
+  if (opts->flags & EBB_MAP_ZERO_OUT) {
+    for (int i = 0; i < mc.nout; ++i) {
+      ebb_status_t s = cuda_check(ctx, cudaMemsetAsync(out[i], 0, bytes, ctx->stream), "zeroing output");
+      if (s) return s;
+    }
+  }
+  cudaError_t e;
+  int oi = 0;
+  if (f64) {
+    MapIO<double> io;
+    io.u = (const double*)in[0];
+    io.w = mc.nin > 1 ? (const double*)in[1] : nullptr;
+    if (ops & OP_FORCE) io.f = (double*)out[oi++];
+    if (ops & OP_KV) io.Kw = (double*)out[oi++];
+    if (ops & OP_DIAG) io.d = (double*)out[oi++];
+    e = launch_tet_map<double>(tets, opts->model, ops, reduce, opts->mu, opts->lambda, io, nullptr, ctx->stream);
+  } else {
+    MapIO<float> io;
+    io.u = (const float*)in[0];
+    io.w = mc.nin > 1 ? (const float*)in[1] : nullptr;
+    if (ops & OP_FORCE) io.f = (float*)out[oi++];
+    if (ops & OP_KV) io.Kw = (float*)out[oi++];
+    if (ops & OP_DIAG) io.d = (float*)out[oi++];
+    e = launch_tet_map<float>(tets, opts->model, ops, reduce, (float)opts->mu, (float)opts->lambda, io, nullptr,
+                              ctx->stream);
+  }
+  return cuda_check(ctx, e, "launching tet map");
+}
+
+}  // namespace
+
+extern "C" {
+
+ebb_status_t ebb_ctx_create(ebb_ctx_t* out, int device, void* cuda_stream) {
+  if (!out) return EBB_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return EBB_ERR_ARG;
+  ebb_ctx_s* ctx = new (std::nothrow) ebb_ctx_s();
+  if (!ctx) return EBB_ERR_NOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_err, ERRW_WORDS * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_err, ERRW_WORDS * sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->d_err, 0, ERRW_WORDS * sizeof(int)) != cudaSuccess) {
+    cudaFree(ctx->d_err);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
+    delete ctx;
+    return EBB_ERR_CUDA;
+  }
+  *out = ctx;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_ctx_set_stream(ebb_ctx_t ctx, void* cuda_stream) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_ctx_destroy(ebb_ctx_t ctx) {
+  if (!ctx) return EBB_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (ebb_rel_s* r : ctx->rels) {
+    free_tet_data(r);
+    delete r;
+  }
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_err);
+  delete ctx;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_ctx_sync(ebb_ctx_t ctx) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  return read_device_error(ctx);
+}
+
+const char* ebb_last_error(ebb_ctx_t ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+ebb_status_t ebb_relation_create(ebb_ctx_t ctx, const char* name, int64_t size, ebb_rel_t* out) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!out || !name) return set_error(ctx, EBB_ERR_ARG, "null name or output");
+  if (size < 0 || size > (int64_t)0x7fffffff / 9)
+    return set_error(ctx, EBB_ERR_ARG, "relation size out of range [0, 2^31/9)");
+  ebb_rel_s* r = new (std::nothrow) ebb_rel_s();
+  if (!r) return set_error(ctx, EBB_ERR_NOMEM, "out of host memory");
+  r->ctx = ctx;
+  r->name = name;
+  r->size = size;
+  ctx->rels.push_back(r);
+  *out = r;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_field_bind(ebb_rel_t rel, const char* name, ebb_dtype_t dtype, int32_t ncomp, void* device_ptr,
+                            ebb_rel_t key_target) {
+  if (!rel) return EBB_ERR_ARG;
+  ebb_ctx_s* ctx = rel->ctx;
+  ctx->last_error.clear();
+  if (!name || !*name) return set_error(ctx, EBB_ERR_ARG, "empty field name");
+  if (dtype_size(dtype) == 0) return set_error(ctx, EBB_ERR_ARG, "unknown dtype");
+  if (ncomp < 1 || ncomp > 16) return set_error(ctx, EBB_ERR_ARG, "ncomp out of range [1,16]");
+  if (!device_ptr && rel->size > 0) return set_error(ctx, EBB_ERR_ARG, "null device pointer");
+  if (key_target && dtype != EBB_I32) return set_error(ctx, EBB_ERR_ARG, "key-fields must be I32");
+  if (key_target && key_target->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "key target in another context");
+  Field f;
+  f.name = name;
+  f.dtype = dtype;
+  f.ncomp = ncomp;
+  f.ptr = device_ptr;
+  f.key_target = key_target;
+  rel->fields[name] = f;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
+  if (!tets) return EBB_ERR_ARG;
+  ebb_ctx_s* ctx = tets->ctx;
+  ctx->last_error.clear();
+  const Field* kv = find_field(tets, "v");
+  if (!kv || kv->dtype != EBB_I32 || kv->ncomp != 4 || !kv->key_target)
+    return set_error(ctx, EBB_ERR_ARG, "tets needs key-field 'v' (I32, 4 components, key target = verts)");
+  ebb_rel_s* verts = kv->key_target;
+  const Field* X = find_field(verts, "X");
+  if (!X || X->dtype != EBB_F64 || X->ncomp != 3)
+    return set_error(ctx, EBB_ERR_ARG, "verts needs field 'X' (F64, 3 components): rest positions");
+  const Field* fmu = find_field(tets, "mu");
+  const Field* flam = find_field(tets, "lambda");
+  if ((fmu != nullptr) != (flam != nullptr))
+    return set_error(ctx, EBB_ERR_ARG, "bind both 'mu' and 'lambda' per tet, or neither");
+  if (fmu && (fmu->dtype != EBB_F64 || fmu->ncomp != 1 || flam->dtype != EBB_F64 || flam->ncomp != 1))
+    return set_error(ctx, EBB_ERR_ARG, "per-tet 'mu'/'lambda' must be F64 with 1 component");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
+
+  free_tet_data(tets);
+  tets->verts = verts;
+  const int nt = (int)tets->size;
+  const int nv = (int)verts->size;
+  if (nt == 0) {
+    tets->finalized = true;
+    return EBB_OK;
+  }
+
+  // Keys: validate on the host (accesses through keys can then never leave
+  // the target relation) and repack as one int4 per tet.
+  std::vector<int> hk((size_t)nt * 4);
+  ebb_status_t s = cuda_check(ctx, cudaMemcpyAsync(hk.data(), kv->ptr, hk.size() * sizeof(int),
+                                                   cudaMemcpyDeviceToHost, ctx->stream),
+                              "copying keys");
+  if (s) return s;
+  s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "copying keys");
+  if (s) return s;
+  std::vector<int4> packed(nt);
+  for (int t = 0; t < nt; ++t) {
+    int k[4];
+    for (int a = 0; a < 4; ++a) {
+      k[a] = hk[(size_t)a * nt + t];
+      if (k[a] < 0 || k[a] >= nv) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "key out of range at tet row %d corner %d (value %d, %d vertices)", t, a, k[a], nv);
+        return set_error(ctx, EBB_ERR_KEY, buf);
+      }
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (k[a] == k[b]) {
+          char buf[128];
+          snprintf(buf, sizeof buf, "tet row %d repeats vertex %d", t, k[a]);
+          return set_error(ctx, EBB_ERR_KEY, buf);
+        }
+    packed[t] = make_int4(k[0], k[1], k[2], k[3]);
+  }
+  cudaError_t e = cudaMalloc(&tets->keys, sizeof(int4) * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&tets->s64.B, sizeof(double) * 9 * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&tets->s64.V, sizeof(double) * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&tets->s32.B, sizeof(float) * 9 * nt);
+  if (e == cudaSuccess) e = cudaMalloc(&tets->s32.V, sizeof(float) * nt);
+  if (e == cudaSuccess && fmu) {
+    e = cudaMalloc(&tets->s64.mu, sizeof(double) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&tets->s64.lam, sizeof(double) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&tets->s32.mu, sizeof(float) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&tets->s32.lam, sizeof(float) * nt);
+  }
+  if (e != cudaSuccess) {
+    free_tet_data(tets);
+    cudaGetLastError();
+    return set_error(ctx, EBB_ERR_NOMEM, "device allocation for tet data failed");
+  }
+  e = cudaMemcpyAsync(tets->keys, packed.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) {
+    const int th = 256, gr = (nt + th - 1) / th;
+    rest_shape_kernel<<<gr, th, 0, ctx->stream>>>(nt, nv, tets->keys, (const double*)X->ptr, tets->s64.B,
+                                                  tets->s64.V, tets->s32.B, tets->s32.V, ctx->d_err);
+    if (fmu)
+      copy_material_kernel<<<gr, th, 0, ctx->stream>>>(nt, (const double*)fmu->ptr, (const double*)flam->ptr,
+                                                       tets->s64.mu, tets->s64.lam, tets->s32.mu, tets->s32.lam);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    free_tet_data(tets);
+    return cuda_check(ctx, e, "rest-shape precomputation");
+  }
+  s = read_device_error(ctx);
+  if (s) {
+    free_tet_data(tets);
+    return s;
+  }
+  if (flags & EBB_FINALIZE_COLOR) {
+    s = build_colouring(ctx, tets);
+    if (s) {
+      free_tet_data(tets);
+      return s;
+    }
+  }
+  tets->finalized = true;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_map_tet_forces(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* f_out,
+                                const ebb_map_opts_t* opts) {
+  MapCall mc;
+  mc.in[0] = u;
+  mc.nin = 1;
+  mc.out[0] = f_out;
+  mc.nout = 1;
+  return run_map(ctx, tets, mc, OP_FORCE, opts);
+}
+
+ebb_status_t ebb_map_tet_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* w, const char* Kw_out,
+                            const ebb_map_opts_t* opts) {
+  MapCall mc;
+  mc.in[0] = u;
+  mc.in[1] = w;
+  mc.nin = 2;
+  mc.out[0] = Kw_out;
+  mc.nout = 1;
+  return run_map(ctx, tets, mc, OP_KV, opts);
+}
+
+ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* w, const char* f_out,
+                                  const char* Kw_out, const ebb_map_opts_t* opts) {
+  MapCall mc;
+  mc.in[0] = u;
+  mc.in[1] = w;
+  mc.nin = 2;
+  mc.out[0] = f_out;
+  mc.out[1] = Kw_out;
+  mc.nout = 2;
+  return run_map(ctx, tets, mc, OP_FORCE | OP_KV, opts);
+}
+
+ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* d_out,
+                               const ebb_map_opts_t* opts) {
+  MapCall mc;
+  mc.in[0] = u;
+  mc.nin = 1;
+  mc.out[0] = d_out;
+  mc.nout = 1;
+  return run_map(ctx, tets, mc, OP_DIAG, opts);
+}
+
+ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v, const char* pinned,
+                                  const ebb_step_params_t* params, ebb_cg_report_t* report) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (report) {
+    report->iters = 0;
+    report->rel_residual = 0.0;
+    report->status = EBB_ERR_ARG;
+  }
+  if (!tets || !params || !u || !v) return set_error(ctx, EBB_ERR_ARG, "null argument");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (params->model != EBB_STVK && params->model != EBB_NEOHOOKEAN)
+    return set_error(ctx, EBB_ERR_ARG, "unknown material model");
+  if (params->precision != EBB_PREC_F64 && params->precision != EBB_PREC_F32)
+    return set_error(ctx, EBB_ERR_ARG, "unknown precision");
+  if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
+    return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
+  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_ATOMIC : params->reduce;
+  if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
+    return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
+  void *pu = nullptr, *pv = nullptr;
+  ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
+  if (s) return s;
+  s = vertex_field(ctx, tets, v, EBB_F64, 3, &pv);
+  if (s) return s;
+  const size_t bytes = (size_t)tets->verts->size * 3 * 8;
+  if (ranges_overlap(pu, bytes, pv, bytes))
+    return set_error(ctx, EBB_ERR_PHASE, "u and v overlap");
+  const void* pp = nullptr;
+  ebb_dtype_t pdt = EBB_U8;
+  if (pinned) {
+    const Field* f = find_field(tets->verts, pinned);
+    if (!f || f->ncomp != 1 || (f->dtype != EBB_U8 && f->dtype != EBB_I32))
+      return set_error(ctx, EBB_ERR_ARG, "pinned must name a U8 or I32 vertex field with 1 component");
+    pp = f->ptr;
+    pdt = f->dtype;
+  }
+  ebb_step_params_t p = *params;
+  p.reduce = reduce;
+  return run_implicit_step(ctx, tets, (double*)pu, (double*)pv, pp, pdt, &p, report);
+}
+
+}  // extern "C"

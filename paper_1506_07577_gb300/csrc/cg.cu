@@ -1,0 +1,486 @@
+// Linearised backward-Euler step with a Jacobi-preconditioned CG solve.
+//
+// Section 7.2: per time step the elastic forces and stiffness are evaluated,
+// a linear system is built and solved for the vertex velocities with a
+// Jacobi-preconditioned conjugate gradient solver written as data-parallel
+// kernels; Section 7.3 reuses the same integrator and solver.  The system is
+//   A = M + dt^2 K(x_n),   b = dt (f(x_n) + M g - dt K(x_n) v_n)
+// with pinned rows and columns removed, solved from dv = 0; then
+// v += dv, u += dt v.
+//
+// Global reductions (dot products) follow the two-pass scheme of Section 6.2
+// "Reductions": the first pass is fused into the kernel producing the values
+// (per-block partial sums), the second pass runs at the start of the kernel
+// that consumes the scalar -- every block re-reduces the partials in the same
+// order, so all blocks see the same bits and the result is deterministic.
+// Scalars never leave the device inside the loop; the host reads one status
+// word per batch of iterations.  CG vectors, dots and updates are FP64 in
+// both precisions; the element maps run in the element precision T.
+#include <cmath>
+#include <cstdio>
+#include <string>
+
+#include "ebb_internal.h"
+
+namespace ebb {
+
+namespace {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocks = 304;   // 2 blocks per SM on a 152-SM GB300
+constexpr int kChunk = 8;         // CG iterations launched between host status reads (even)
+
+struct CgScalars {
+  double rz[2];      // r.z, indexed by iteration parity
+  double rr;         // r.r after the last update
+  double bb;         // b.b
+  int active[2];     // iteration with parity s runs iff active[s]
+  int iter;          // iterations completed
+  int status;        // EBB_OK or EBB_ERR_CG_BREAKDOWN
+};
+
+template <typename PT>
+__device__ __forceinline__ bool is_pinned(const PT* pin, int v) {
+  return pin != nullptr && pin[v] != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block sum of two values; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[kVecThreads / 32], sb[kVecThreads / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sa[w] = a;
+    sb[w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    a = l < kVecThreads / 32 ? sa[l] : 0.0;
+    b = l < kVecThreads / 32 ? sb[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
+}
+
+// Second pass: sum kVecBlocks partial pairs in a fixed order; every thread of
+// the block gets the result.
+__device__ __forceinline__ void reduce_partials(const double* part, double& a, double& b) {
+  __shared__ double ra, rb;
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < kVecBlocks; i += kVecThreads) {
+    x += part[2 * i];
+    y += part[2 * i + 1];
+  }
+  block_sum2(x, y);
+  if (threadIdx.x == 0) {
+    ra = x;
+    rb = y;
+  }
+  __syncthreads();
+  a = ra;
+  b = rb;
+}
+
+// u32 = u, w32 = v (mixed precision), accumulators zeroed.
+template <typename T>
+__global__ void step_prep_kernel(int n, const double* __restrict__ u, const double* __restrict__ v, T* ue,
+                                 T* ve, T* acc_f, T* acc_kv, T* acc_d, T* acc_kp, bool copy) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (copy) {
+      ue[i] = (T)u[i];
+      ve[i] = (T)v[i];
+    }
+    acc_f[i] = T(0);
+    acc_kv[i] = T(0);
+    acc_d[i] = T(0);
+    acc_kp[i] = T(0);
+  }
+}
+
+__global__ void mass_kernel(int nt, const int4* __restrict__ keys, const double* __restrict__ V, double rho,
+                            double* m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int4 k = keys[t];
+  const double q = 0.25 * rho * V[t];
+  atomicAdd(m + k.x, q);
+  atomicAdd(m + k.y, q);
+  atomicAdd(m + k.z, q);
+  atomicAdd(m + k.w, q);
+}
+
+struct StepConst {
+  int nv;
+  double dt;
+  double g[3];
+  double rtol;
+  int max_iters;
+};
+
+// b = dt (f + m g - dt K v) (0 on pinned rows); r = b; z = r / diag(A);
+// p = z; y = 0.  Partials: (r.z, r.r).
+template <typename T, typename PT>
+__global__ void __launch_bounds__(kVecThreads)
+cg_init_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict__ mass,
+               const T* __restrict__ acc_f, const T* __restrict__ acc_kv, const T* __restrict__ acc_d,
+               double* r, double* p, double* y, double* dinv, T* pe, double* part) {
+  const int n = 3 * c.nv;
+  double rz = 0.0, rr = 0.0;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
+    const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
+    const int vtx = i - comp * c.nv;
+    double b = 0.0, di = 1.0;
+    if (!is_pinned(pin, vtx)) {
+      const double m = mass[vtx];
+      b = c.dt * ((double)acc_f[i] + m * c.g[comp] - c.dt * (double)acc_kv[i]);
+      di = 1.0 / (m + c.dt * c.dt * (double)acc_d[i]);
+    }
+    const double z = b * di;
+    r[i] = b;
+    p[i] = z;
+    y[i] = 0.0;
+    dinv[i] = di;
+    if (pe) pe[i] = (T)z;
+    rz += b * z;
+    rr += b * b;
+  }
+  block_sum2(rz, rr);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rz;
+    part[2 * blockIdx.x + 1] = rr;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) cg_start_kernel(StepConst c, const double* part, CgScalars* sc) {
+  double rz, rr;
+  reduce_partials(part, rz, rr);
+  if (threadIdx.x == 0) {
+    sc->rz[0] = rz;
+    sc->rz[1] = 0.0;
+    sc->rr = rr;
+    sc->bb = rr;
+    sc->iter = 0;
+    sc->status = EBB_OK;
+    sc->active[0] = (c.max_iters > 0 && sqrt(rr) > c.rtol * sqrt(rr)) ? 1 : 0;
+    sc->active[1] = 0;
+  }
+}
+
+// q = A p on free rows; partial p.q.
+template <typename T, typename PT>
+__global__ void __launch_bounds__(kVecThreads)
+cg_pq_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
+             const double* __restrict__ p, const T* __restrict__ acc_kp, const CgScalars* sc, double* part) {
+  if (!sc->active[s]) return;
+  const int n = 3 * c.nv;
+  const double dt2 = c.dt * c.dt;
+  double pq = 0.0, zero = 0.0;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
+    const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
+    const int vtx = i - comp * c.nv;
+    if (is_pinned(pin, vtx)) continue;
+    const double pi = p[i];
+    pq += pi * (mass[vtx] * pi + dt2 * (double)acc_kp[i]);
+  }
+  block_sum2(pq, zero);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = pq;
+    part[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+// alpha = rz / pq; y += alpha p; r -= alpha q; partials (r.z, r.r).
+template <typename T, typename PT>
+__global__ void __launch_bounds__(kVecThreads)
+cg_update_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
+                 const double* __restrict__ p, const T* __restrict__ acc_kp, const double* __restrict__ dinv,
+                 double* r, double* y, CgScalars* sc, const double* part_in, double* part_out) {
+  if (!sc->active[s]) return;
+  double pq, unused;
+  reduce_partials(part_in, pq, unused);
+  if (!(pq > 0.0)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->status = EBB_ERR_CG_BREAKDOWN;
+    return;
+  }
+  const double alpha = sc->rz[s] / pq;
+  const int n = 3 * c.nv;
+  const double dt2 = c.dt * c.dt;
+  double rz = 0.0, rr = 0.0;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
+    const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
+    const int vtx = i - comp * c.nv;
+    if (is_pinned(pin, vtx)) continue;
+    const double pi = p[i];
+    const double q = mass[vtx] * pi + dt2 * (double)acc_kp[i];
+    y[i] += alpha * pi;
+    const double ri = r[i] - alpha * q;
+    r[i] = ri;
+    const double z = ri * dinv[i];
+    rz += ri * z;
+    rr += ri * ri;
+  }
+  block_sum2(rz, rr);
+  if (threadIdx.x == 0) {
+    part_out[2 * blockIdx.x] = rz;
+    part_out[2 * blockIdx.x + 1] = rr;
+  }
+}
+
+// beta = rz_new / rz; p = z + beta p; clear the K p accumulator; decide
+// whether the next iteration runs.
+template <typename T>
+__global__ void __launch_bounds__(kVecThreads)
+cg_pupdate_kernel(StepConst c, int s, const double* __restrict__ r, const double* __restrict__ dinv, double* p,
+                  T* pe, T* acc_kp, CgScalars* sc, const double* part) {
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  if (!sc->active[s] || sc->status != EBB_OK) {
+    if (lead) sc->active[s ^ 1] = 0;
+    return;
+  }
+  double rz_new, rr;
+  reduce_partials(part, rz_new, rr);
+  const double beta = rz_new / sc->rz[s];
+  const int n = 3 * c.nv;
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
+    const double pi = r[i] * dinv[i] + beta * p[i];
+    p[i] = pi;
+    if (pe) pe[i] = (T)pi;
+    acc_kp[i] = T(0);
+  }
+  if (lead) {
+    const int it = sc->iter + 1;
+    sc->iter = it;
+    sc->rz[s ^ 1] = rz_new;
+    sc->rr = rr;
+    sc->active[s ^ 1] = (it < c.max_iters && sqrt(rr) > c.rtol * sqrt(sc->bb)) ? 1 : 0;
+  }
+}
+
+// v += dv; u += dt v.
+__global__ void step_finish_kernel(int n, double dt, const double* __restrict__ y, double* u, double* v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double vi = v[i] + y[i];
+    v[i] = vi;
+    u[i] += dt * vi;
+  }
+}
+
+}  // namespace
+
+struct StepScratch {
+  int nv = 0;
+  void* acc[4] = {nullptr, nullptr, nullptr, nullptr};   // f, Kv, diag, Kp in element precision
+  void* ue = nullptr;                                    // element-precision displacement
+  void* pe = nullptr;                                    // element-precision v, then p
+  double *r = nullptr, *p = nullptr, *y = nullptr, *dinv = nullptr, *mass = nullptr;
+  double* part = nullptr;   // 2 sets of kVecBlocks pairs
+  CgScalars* sc = nullptr;
+  CgScalars* h_sc = nullptr;
+  double rho = -1.0;
+};
+
+void free_step_scratch(ebb_rel_s* rel) {
+  StepScratch* s = rel->step;
+  if (!s) return;
+  for (void* a : s->acc) cudaFree(a);
+  cudaFree(s->ue);
+  cudaFree(s->pe);
+  cudaFree(s->r);
+  cudaFree(s->p);
+  cudaFree(s->y);
+  cudaFree(s->dinv);
+  cudaFree(s->mass);
+  cudaFree(s->part);
+  cudaFree(s->sc);
+  if (s->h_sc) cudaFreeHost(s->h_sc);
+  delete s;
+  rel->step = nullptr;
+}
+
+namespace {
+
+ebb_status_t ensure_scratch(ebb_ctx_s* ctx, ebb_rel_s* tets) {
+  const int nv = (int)tets->verts->size;
+  if (tets->step && tets->step->nv == nv) return EBB_OK;
+  free_step_scratch(tets);
+  StepScratch* s = new StepScratch();
+  tets->step = s;
+  s->nv = nv;
+  const size_t n = (size_t)3 * nv;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(&s->acc[i], n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->ue, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->pe, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->r, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->p, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->y, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->dinv, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->mass, (size_t)nv * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->part, 4 * kVecBlocks * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->sc, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&s->h_sc, sizeof(CgScalars));
+  if (e != cudaSuccess) {
+    free_step_scratch(tets);
+    cudaGetLastError();
+    return set_error(ctx, EBB_ERR_NOMEM, "device allocation for implicit-step scratch failed");
+  }
+  return EBB_OK;
+}
+
+template <typename T, typename PT>
+ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const PT* pin,
+                       const ebb_step_params_t* prm, ebb_cg_report_t* rep) {
+  const bool mixed = sizeof(T) == 4;
+  StepScratch* s = tets->step;
+  const int nv = s->nv;
+  const int n = 3 * nv;
+  const int nt = (int)tets->size;
+  cudaStream_t st = ctx->stream;
+  T* acc_f = (T*)s->acc[0];
+  T* acc_kv = (T*)s->acc[1];
+  T* acc_d = (T*)s->acc[2];
+  T* acc_kp = (T*)s->acc[3];
+  T* ue = (T*)s->ue;
+  T* pe = (T*)s->pe;
+  cudaError_t e = cudaSuccess;
+
+  if (s->rho != prm->rho) {
+    e = cudaMemsetAsync(s->mass, 0, (size_t)nv * sizeof(double), st);
+    if (e == cudaSuccess && nt > 0) {
+      mass_kernel<<<(nt + 255) / 256, 256, 0, st>>>(nt, tets->keys, tets->s64.V, prm->rho, s->mass);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_check(ctx, e, "lumped mass");
+    s->rho = prm->rho;
+  }
+
+  StepConst c;
+  c.nv = nv;
+  c.dt = prm->dt;
+  c.g[0] = prm->gravity[0];
+  c.g[1] = prm->gravity[1];
+  c.g[2] = prm->gravity[2];
+  c.rtol = prm->rtol;
+  c.max_iters = prm->max_iters;
+
+  const int vgrid = 4 * 152;
+  step_prep_kernel<T><<<vgrid, 256, 0, st>>>(n, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "step prep");
+
+  const T mu0 = (T)prm->mu, lam0 = (T)prm->lambda;
+  MapIO<T> io;
+  io.u = mixed ? ue : (const T*)u;
+  io.w = mixed ? pe : (const T*)v;
+  io.f = acc_f;
+  io.Kw = acc_kv;
+  io.d = acc_d;
+  e = launch_tet_map<T>(tets, prm->model, OP_FORCE | OP_KV | OP_DIAG, prm->reduce, mu0, lam0, io, nullptr, st);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "force/Kv/diag map");
+
+  double* part_a = s->part;
+  double* part_b = s->part + 2 * kVecBlocks;
+  cg_init_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, pin, s->mass, acc_f, acc_kv, acc_d, s->r, s->p,
+                                                             s->y, s->dinv, mixed ? pe : nullptr, part_a);
+  cg_start_kernel<<<1, kVecThreads, 0, st>>>(c, part_a, s->sc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "CG init");
+
+  MapIO<T> kio;
+  kio.u = io.u;
+  kio.w = mixed ? pe : (const T*)s->p;
+  kio.Kw = acc_kp;
+
+  int launched = 0;
+  ebb_status_t status = EBB_OK;
+  while (true) {
+    for (int k = 0; k < kChunk; ++k) {
+      const int par = k & 1;
+      e = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
+      if (e != cudaSuccess) break;
+      cg_pq_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->sc, part_a);
+      cg_update_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->dinv,
+                                                                   s->r, s->y, s->sc, part_a, part_b);
+      cg_pupdate_kernel<T><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, s->r, s->dinv, s->p, mixed ? pe : nullptr,
+                                                               acc_kp, s->sc, part_b);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) return cuda_check(ctx, e, "CG iteration launch");
+    launched += kChunk;
+    e = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "CG status read");
+    const CgScalars& h = *s->h_sc;
+    if (h.status != EBB_OK) {
+      status = h.status;
+      break;
+    }
+    if (!h.active[h.iter & 1] || h.iter >= prm->max_iters) break;
+    if (launched > prm->max_iters + 2 * kChunk) break;  // defensive bound
+  }
+
+  step_finish_kernel<<<vgrid, 256, 0, st>>>(n, prm->dt, s->y, u, v);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "step finish");
+  const CgScalars& h = *s->h_sc;
+  const double rel = h.bb > 0.0 ? std::sqrt(h.rr / h.bb) : 0.0;
+  if (rep) {
+    rep->iters = h.iter;
+    rep->rel_residual = rel;
+  }
+  // Device-raised errors (inverted elements) take precedence.
+  cudaError_t ce = cudaMemcpyAsync(ctx->h_err, ctx->d_err, ERRW_WORDS * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_check(ctx, ce, "status read");
+  if (ctx->h_err[ERRW_CODE] != 0) {
+    const int code = ctx->h_err[ERRW_CODE], idx = ctx->h_err[ERRW_INDEX];
+    cudaMemsetAsync(ctx->d_err, 0, ERRW_WORDS * sizeof(int), st);
+    cudaStreamSynchronize(st);
+    char buf[128];
+    snprintf(buf, sizeof buf, "device error %d (inverted element?) at tet row %d", code, idx);
+    status = set_error(ctx, code, buf);
+  } else if (status == EBB_ERR_CG_BREAKDOWN) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "PCG breakdown (p^T A p <= 0) at iteration %d", h.iter);
+    set_error(ctx, status, buf);
+  } else if (prm->fail_on_max_iters && h.iter >= prm->max_iters && rel > prm->rtol) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "PCG not converged after %d iterations (rel residual %.3e)", h.iter, rel);
+    status = set_error(ctx, EBB_ERR_NOT_CONVERGED, buf);
+  }
+  if (rep) rep->status = status;
+  return status;
+}
+
+}  // namespace
+
+ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const void* pinned,
+                               ebb_dtype_t pinned_dtype, const ebb_step_params_t* p, ebb_cg_report_t* rep) {
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
+  if (tets->verts->size == 0) {
+    if (rep) rep->status = EBB_OK;
+    return EBB_OK;
+  }
+  ebb_status_t s = ensure_scratch(ctx, tets);
+  if (s) return s;
+  const bool f64 = p->precision == EBB_PREC_F64;
+  if (pinned_dtype == EBB_I32) {
+    return f64 ? step_impl<double, int>(ctx, tets, u, v, (const int*)pinned, p, rep)
+               : step_impl<float, int>(ctx, tets, u, v, (const int*)pinned, p, rep);
+  }
+  return f64 ? step_impl<double, unsigned char>(ctx, tets, u, v, (const unsigned char*)pinned, p, rep)
+             : step_impl<float, unsigned char>(ctx, tets, u, v, (const unsigned char*)pinned, p, rep);
+}
+
+}  // namespace ebb

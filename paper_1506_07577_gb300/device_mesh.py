@@ -1,0 +1,83 @@
+"""Device-resident tet mesh: torch-owned field storage bound to the C ABI.
+
+PyTorch supplies device memory and the stream; every computation runs in
+``libebb_gb300.so`` through the calls in ``abi``.  Vertex fields are stored
+as column stores shaped (3, N_v) (one contiguous plane per component,
+Section 6.1), the tet key-field ``v`` as (4, N_t) int32.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import abi
+
+
+class DeviceTetMesh:
+    """Relations ``verts``/``tets`` on one CUDA device with the rest shape,
+    keys and optional per-tet Lame fields bound, finalized on construction."""
+
+    def __init__(self, X, tets, mu=None, lam=None, device=0, stream=None, colour=False):
+        self.device = torch.device("cuda", device)
+        self.ctx = abi.ebb_ctx_create(device, stream)
+        self.n_verts = int(X.shape[0])
+        self.n_tets = int(tets.shape[0])
+        self.verts = abi.ebb_relation_create(self.ctx, "verts", self.n_verts)
+        self.tets = abi.ebb_relation_create(self.ctx, "tets", self.n_tets)
+        self._tensors = {}
+        self.X = self._put("X", np.ascontiguousarray(np.asarray(X, np.float64).T), self.verts)
+        keys = np.ascontiguousarray(np.asarray(tets, np.int32).T)
+        self.keys = torch.from_numpy(keys).to(self.device)
+        abi.ebb_field_bind(self.ctx, self.tets, "v", self.keys, key_target=self.verts)
+        if (mu is None) != (lam is None):
+            raise ValueError("give both per-tet mu and lam, or neither")
+        if mu is not None and np.ndim(mu) > 0:
+            self._put("mu", np.asarray(mu, np.float64), self.tets)
+            self._put("lambda", np.asarray(lam, np.float64), self.tets)
+        # uploads ran on torch's current stream; the library may use another
+        torch.cuda.synchronize(self.device)
+        abi.ebb_relation_finalize(self.ctx, self.tets, abi.EBB_FINALIZE_COLOR if colour else 0)
+
+    def _put(self, name, arr, rel):
+        t = torch.from_numpy(np.ascontiguousarray(arr)).to(self.device)
+        abi.ebb_field_bind(self.ctx, rel, name, t)
+        self._tensors[name] = t
+        return t
+
+    def vertex_field(self, name, dtype=torch.float64, ncomp=3, value=None):
+        """Allocate (or upload) a vertex field of shape (ncomp, N_v), bind it
+        under ``name`` and return the tensor.  ``value`` may be an (N_v, ncomp)
+        numpy array."""
+        if value is not None:
+            arr = np.asarray(value)
+            arr = arr.T if arr.ndim == 2 else arr
+            t = torch.from_numpy(np.ascontiguousarray(arr)).to(self.device, dtype)
+        else:
+            shape = (ncomp, self.n_verts) if ncomp > 1 else (self.n_verts,)
+            t = torch.zeros(shape, dtype=dtype, device=self.device)
+        torch.cuda.synchronize(self.device)
+        abi.ebb_field_bind(self.ctx, self.verts, name, t)
+        self._tensors[name] = t
+        return t
+
+    def bind(self, name, tensor):
+        abi.ebb_field_bind(self.ctx, self.verts, name, tensor)
+        self._tensors[name] = tensor
+        return tensor
+
+    def close(self):
+        if self.ctx is not None:
+            abi.ebb_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
