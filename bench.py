@@ -189,12 +189,12 @@ def run_ours(args, rank, world, local_rank):
 
     m, mu, lam, u, w = workload()
     stream = torch.cuda.Stream(device=dev)
-    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream)
+    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream, colour=True)
     u32 = dm.vertex_field("u32", torch.float32, value=u)
     w32 = dm.vertex_field("w32", torch.float32, value=w)
     f = dm.vertex_field("f", torch.float32)
     Kw = dm.vertex_field("Kw", torch.float32)
-    opts = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_ATOMIC)
+    opts = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     nt = m.n_tets
 
@@ -281,6 +281,26 @@ def run_ours(args, rank, world, local_rank):
         err = max(float(np.max(np.abs(fg - fo)) / np.max(np.abs(fo))),
                   float(np.max(np.abs(kg - ko)) / np.max(np.abs(ko))))
 
+    # ---- reduction variants of the fused map (kernel time only) ----------
+    variants = {}
+    for name, red in (("atomic", abi.EBB_REDUCE_ATOMIC), ("colour", abi.EBB_REDUCE_COLOR),
+                      ("tiled", abi.EBB_REDUCE_TILED)):
+        o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=red)
+        ts = []
+        with torch.cuda.stream(stream):
+            for k in range(args.warmup + 5):
+                flush.fill_(float(k))
+                f.zero_()
+                Kw.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", o)
+                b.record(stream)
+                b.synchronize()
+                if k >= args.warmup:
+                    ts.append(a.elapsed_time(b) * 1e3)
+        variants[name] = {"us": statistics.median(ts), "tets_per_s": nt / (statistics.median(ts) * 1e-6)}
+
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
 
@@ -290,7 +310,7 @@ def run_ours(args, rank, world, local_rank):
     kern_avg = sum(kern_ms) / len(kern_ms) / 1e3
     achieved = bpt * nt / kern_avg / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic>",
+            "traffic": None, "kernel": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV>",
             "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
 
     dm.close()
@@ -300,10 +320,11 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64^3 cube grid, 5 tets/cube (274,625 verts, 1,310,720 tets), NH, "
-                                   "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, atomic scatter",
+                                   "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, tiled scatter",
                        "n_tets": nt, "n_verts": m.n_verts, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
+            "reduction_variants": variants,
             "e2e": {"value": nt * args.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,

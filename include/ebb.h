@@ -76,12 +76,24 @@ typedef enum { EBB_STVK = 0, EBB_NEOHOOKEAN = 1 } ebb_model_t;
  * ebb_cg_implicit_step the CG vectors, dot products and updates stay FP64. */
 typedef enum { EBB_PREC_F64 = 0, EBB_PREC_F32 = 1 } ebb_precision_t;
 
-/* Scatter (+= reduction) strategy.  ATOMIC: hardware atomic adds (Section
- * 6.2 "Reductions").  COLOR: tets grouped by a vertex-conflict colouring, one
- * colour at a time with plain read-modify-write; deterministic run to run
- * (the colouring approach of Liszt discussed in Section 7.4).  AUTO: the
- * library's tuned choice. */
-typedef enum { EBB_REDUCE_ATOMIC = 0, EBB_REDUCE_COLOR = 1, EBB_REDUCE_AUTO = 2 } ebb_reduce_t;
+/* Scatter (+= reduction) strategy.
+ *   ATOMIC: one thread per tet, hardware atomic adds into the vertex fields
+ *           (the field reductions of Section 6.2 "Reductions").
+ *   COLOR:  tets grouped by a vertex-conflict colouring, one colour at a time
+ *           with plain read-modify-write; bitwise reproducible run to run
+ *           (the colouring approach of Liszt discussed in Section 7.4).
+ *           Needs EBB_FINALIZE_COLOR.
+ *   TILED:  tets in Morton order cut into tiles; each tile gathers its
+ *           distinct vertices into shared memory once, pre-reduces the
+ *           per-corner results there and issues one atomic add per distinct
+ *           vertex and component.
+ *   AUTO:   the library's tuned choice (currently TILED). */
+typedef enum {
+  EBB_REDUCE_ATOMIC = 0,
+  EBB_REDUCE_COLOR = 1,
+  EBB_REDUCE_AUTO = 2,
+  EBB_REDUCE_TILED = 3
+} ebb_reduce_t;
 
 /* ebb_relation_finalize flags */
 #define EBB_FINALIZE_COLOR    1u  /* build the vertex-conflict colouring of tets */

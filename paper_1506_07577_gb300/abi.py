@@ -38,7 +38,7 @@ STATUS_NAMES = {v: k for k, v in dict(globals()).items() if k.startswith("EBB_ER
 EBB_F32, EBB_F64, EBB_I32, EBB_U8 = 1, 2, 3, 4
 EBB_STVK, EBB_NEOHOOKEAN = 0, 1
 EBB_PREC_F64, EBB_PREC_F32 = 0, 1
-EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO = 0, 1, 2
+EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED = 0, 1, 2, 3
 EBB_FINALIZE_COLOR = 1
 EBB_MAP_ZERO_OUT = 1
 
@@ -163,7 +163,7 @@ def ebb_relation_finalize(ctx, rel, flags=0):
     return _check(ctx, _lib.ebb_relation_finalize(rel, int(flags)))
 
 
-def map_opts(model, mu=0.0, lam=0.0, precision=EBB_PREC_F64, reduce=EBB_REDUCE_ATOMIC, flags=0):
+def map_opts(model, mu=0.0, lam=0.0, precision=EBB_PREC_F64, reduce=EBB_REDUCE_AUTO, flags=0):
     return ebb_map_opts_t(int(model), float(mu), float(lam), int(precision), int(reduce), int(flags))
 
 
@@ -184,7 +184,7 @@ def ebb_map_tet_diagK(ctx, tets, u, d_out, opts):
 
 
 def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,
-                reduce=EBB_REDUCE_ATOMIC, max_iters=1000, rtol=1e-8, fail_on_max_iters=False):
+                reduce=EBB_REDUCE_AUTO, max_iters=1000, rtol=1e-8, fail_on_max_iters=False):
     g = (C.c_double * 3)(*[float(x) for x in gravity])
     return ebb_step_params_t(int(model), float(mu), float(lam), int(precision), int(reduce), float(dt), g,
                              float(rho), int(max_iters), float(rtol), int(bool(fail_on_max_iters)))

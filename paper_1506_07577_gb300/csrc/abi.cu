@@ -44,8 +44,9 @@ size_t dtype_size(ebb_dtype_t d) {
 
 // Rest-shape precomputation: B = Dm^-1 and V = det(Dm)/6 in FP64, plus FP32
 // copies.  Dm = [X1-X0, X2-X0, X3-X0] with X read through the keys.
-__global__ void rest_shape_kernel(int nt, int nv, const int4* __restrict__ keys, const double* __restrict__ X,
-                                  double* B64, double* V64, float* B32, float* V32, int* err) {
+__global__ void rest_shape_kernel(int nt, int nv, const int4* __restrict__ keys, const int* __restrict__ perm,
+                                  const double* __restrict__ X, double* B64, double* V64, float* B32, float* V32,
+                                  int* err) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const int4 k = keys[t];
@@ -60,7 +61,7 @@ __global__ void rest_shape_kernel(int nt, int nv, const int4* __restrict__ keys,
   const double c02 = D[3] * D[7] - D[4] * D[6];
   const double det = D[0] * c00 + D[1] * c01 + D[2] * c02;
   if (!(det > 0.0)) {
-    if (atomicCAS(err + ERRW_CODE, 0, EBB_ERR_INVERTED) == 0) err[ERRW_INDEX] = t;
+    if (atomicCAS(err + ERRW_CODE, 0, EBB_ERR_INVERTED) == 0) err[ERRW_INDEX] = perm[t];
   }
   const double id = 1.0 / det;
   // inverse = adj / det, adj = cof^T
@@ -82,11 +83,14 @@ __global__ void rest_shape_kernel(int nt, int nv, const int4* __restrict__ keys,
   V32[t] = (float)(det / 6.0);
 }
 
-__global__ void copy_material_kernel(int nt, const double* __restrict__ mu, const double* __restrict__ lam,
-                                     double* mu64, double* lam64, float* mu32, float* lam32) {
+// Per-tet Lame parameters gathered into the internal tet order.
+__global__ void copy_material_kernel(int nt, const int* __restrict__ perm, const double* __restrict__ mu,
+                                     const double* __restrict__ lam, double* mu64, double* lam64, float* mu32,
+                                     float* lam32) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
-  const double m = mu[t], l = lam[t];
+  const int o = perm[t];
+  const double m = mu[o], l = lam[o];
   mu64[t] = m;
   lam64[t] = l;
   mu32[t] = (float)m;
@@ -107,6 +111,7 @@ void free_tet_data(ebb_rel_s* r) {
   r->s64 = TetStreams<double>();
   r->s32 = TetStreams<float>();
   free_colouring(r);
+  free_layout(r);
   free_step_scratch(r);
   r->finalized = false;
 }
@@ -175,8 +180,8 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
   if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   ebb_reduce_t reduce = opts->reduce;
-  if (reduce == EBB_REDUCE_AUTO) reduce = EBB_REDUCE_ATOMIC;
-  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR)
+  if (reduce == EBB_REDUCE_AUTO) reduce = EBB_REDUCE_TILED;
+  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
@@ -381,6 +386,20 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
         }
     packed[t] = make_int4(k[0], k[1], k[2], k[3]);
   }
+  // Rest positions on the host for the Morton order of the tets.
+  std::vector<double> hX((size_t)3 * nv);
+  s = cuda_check(ctx, cudaMemcpyAsync(hX.data(), X->ptr, hX.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream),
+                 "copying rest positions");
+  if (s) return s;
+  s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "copying rest positions");
+  if (s) return s;
+  std::vector<int> perm;
+  std::vector<int4> sorted;
+  s = build_layout(ctx, tets, packed, hX, perm, sorted);
+  if (s) return s;
+  packed.swap(sorted);
+
   cudaError_t e = cudaMalloc(&tets->keys, sizeof(int4) * nt);
   if (e == cudaSuccess) e = cudaMalloc(&tets->s64.B, sizeof(double) * 9 * nt);
   if (e == cudaSuccess) e = cudaMalloc(&tets->s64.V, sizeof(double) * nt);
@@ -400,11 +419,12 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   e = cudaMemcpyAsync(tets->keys, packed.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
     const int th = 256, gr = (nt + th - 1) / th;
-    rest_shape_kernel<<<gr, th, 0, ctx->stream>>>(nt, nv, tets->keys, (const double*)X->ptr, tets->s64.B,
+    rest_shape_kernel<<<gr, th, 0, ctx->stream>>>(nt, nv, tets->keys, tets->tet_perm, (const double*)X->ptr, tets->s64.B,
                                                   tets->s64.V, tets->s32.B, tets->s32.V, ctx->d_err);
     if (fmu)
-      copy_material_kernel<<<gr, th, 0, ctx->stream>>>(nt, (const double*)fmu->ptr, (const double*)flam->ptr,
-                                                       tets->s64.mu, tets->s64.lam, tets->s32.mu, tets->s32.lam);
+      copy_material_kernel<<<gr, th, 0, ctx->stream>>>(nt, tets->tet_perm, (const double*)fmu->ptr,
+                                                       (const double*)flam->ptr, tets->s64.mu, tets->s64.lam,
+                                                       tets->s32.mu, tets->s32.lam);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -489,7 +509,9 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
-  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_ATOMIC : params->reduce;
+  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
+  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+    return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
   void *pu = nullptr, *pv = nullptr;

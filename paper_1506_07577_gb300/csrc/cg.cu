@@ -105,16 +105,16 @@ __global__ void step_prep_kernel(int n, const double* __restrict__ u, const doub
   }
 }
 
-__global__ void mass_kernel(int nt, const int4* __restrict__ keys, const double* __restrict__ V, double rho,
-                            double* m) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
-  const int4 k = keys[t];
-  const double q = 0.25 * rho * V[t];
-  atomicAdd(m + k.x, q);
-  atomicAdd(m + k.y, q);
-  atomicAdd(m + k.z, q);
-  atomicAdd(m + k.w, q);
+// Lumped mass m_v = sum over (tet, corner) entries of v of rho V_t / 4,
+// gathered through the vertex -> (tet, corner) index in a fixed order so the
+// result does not depend on thread scheduling.
+__global__ void mass_kernel(int nv, const int* __restrict__ off, const int* __restrict__ ent,
+                            const double* __restrict__ V, double rho, double* m) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int e = off[v]; e < off[v + 1]; ++e) s += V[ent[e] >> 2];
+  m[v] = 0.25 * rho * s;
 }
 
 struct StepConst {
@@ -353,11 +353,9 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   cudaError_t e = cudaSuccess;
 
   if (s->rho != prm->rho) {
-    e = cudaMemsetAsync(s->mass, 0, (size_t)nv * sizeof(double), st);
-    if (e == cudaSuccess && nt > 0) {
-      mass_kernel<<<(nt + 255) / 256, 256, 0, st>>>(nt, tets->keys, tets->s64.V, prm->rho, s->mass);
-      e = cudaGetLastError();
-    }
+    mass_kernel<<<(nv + 255) / 256, 256, 0, st>>>(nv, tets->vindex.off, tets->vindex.ent, tets->s64.V, prm->rho,
+                                                   s->mass);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(ctx, e, "lumped mass");
     s->rho = prm->rho;
   }

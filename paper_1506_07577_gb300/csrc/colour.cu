@@ -48,6 +48,7 @@ cudaError_t gather_copy(int n, int planes, const int* perm, const T* src, T** ds
 void free_colouring(ebb_rel_s* tets) {
   Colouring& c = tets->colour;
   cudaFree(c.keys);
+  cudaFree(c.perm);
   cudaFree(c.s64.B);
   cudaFree(c.s64.V);
   cudaFree(c.s64.mu);
@@ -101,6 +102,7 @@ ebb_status_t build_colouring(ebb_ctx_s* ctx, ebb_rel_s* tets) {
     gather_keys_kernel<<<(nt + 255) / 256, 256, 0, st>>>(nt, dperm, tets->keys, col.keys);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = gather_copy(nt, 1, dperm, tets->tet_perm, &col.perm, st);
   if (e == cudaSuccess) e = gather_copy(nt, 9, dperm, tets->s64.B, &col.s64.B, st);
   if (e == cudaSuccess) e = gather_copy(nt, 1, dperm, tets->s64.V, &col.s64.V, st);
   if (e == cudaSuccess) e = gather_copy(nt, 1, dperm, tets->s64.mu, &col.s64.mu, st);

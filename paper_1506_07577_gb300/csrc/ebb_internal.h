@@ -38,8 +38,33 @@ struct Colouring {
   int ncolours = 0;
   std::vector<int> offsets;
   int4* keys = nullptr;
+  int* perm = nullptr;   // colour-ordered row -> caller's row
   TetStreams<double> s64;
   TetStreams<float> s32;
+};
+
+// Tiles of consecutive (Morton-ordered) tets for the shared-memory
+// pre-reduced maps.  Tile i covers internal tet rows [tet_off[i],
+// tet_off[i+1]) and the distinct vertices vtx[vtx_off[i] .. vtx_off[i+1]);
+// slots[t] holds the tile-local index of each of tet t's four vertices.
+constexpr int kTileTets = 256;   // tets per tile (= threads per CTA)
+constexpr int kTileSlots = 256;  // distinct vertices per tile (u8 slots)
+
+struct Tiles {
+  int ntiles = 0;
+  int* tet_off = nullptr;
+  int* vtx_off = nullptr;
+  int* vtx = nullptr;
+  uchar4* slots = nullptr;
+  int total_vtx = 0;
+};
+
+// Inverse of the key-field (Section 6.1 GroupBy): for vertex v the entries
+// ent[off[v] .. off[v+1]) are 4*t + a for every internal tet row t whose
+// corner a is v, in increasing order.
+struct VertexIndex {
+  int* off = nullptr;
+  int* ent = nullptr;
 };
 
 struct StepScratch;  // defined in cg.cu
@@ -66,11 +91,14 @@ struct ebb_rel_s {
   // ---- finalized tet data (tets relation only) ----
   bool finalized = false;
   ebb_rel_s* verts = nullptr;
-  int4* keys = nullptr;                 // internal keys, one int4 per tet
+  int4* keys = nullptr;                 // internal keys, one int4 per tet (Morton order)
+  int* tet_perm = nullptr;              // internal row -> caller's row
   ebb::TetStreams<double> s64;
   ebb::TetStreams<float> s32;
   ebb::Colouring colour;
   bool has_colour = false;
+  ebb::Tiles tiles;
+  ebb::VertexIndex vindex;
 
   // ---- implicit-step scratch ----
   ebb::StepScratch* step = nullptr;
@@ -109,6 +137,15 @@ void free_step_scratch(ebb_rel_s* rel);
 ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v,
                                const void* pinned, ebb_dtype_t pinned_dtype,
                                const ebb_step_params_t* p, ebb_cg_report_t* rep);
+
+// Morton order, tiles and vertex index from host keys (layout.cu).  `keys`
+// and `X` are the caller's order (X as 3 planes of nv); on return
+// `perm[i]` is the caller's row of internal row i and the device-side
+// tiles / vertex index of `tets` are built for the internal order.
+ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
+                          const std::vector<double>& X, std::vector<int>& perm,
+                          std::vector<int4>& sorted_keys);
+void free_layout(ebb_rel_s* tets);
 
 // Build the colouring (colour.cu).
 ebb_status_t build_colouring(ebb_ctx_s* ctx, ebb_rel_s* tets);

@@ -46,13 +46,13 @@ def _run_maps(dm, u, w, model, prec, reduce, mu, lam):
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["atomic", "colour"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled"])
 @pytest.mark.parametrize("per_tet", [True, False])
 def test_maps_match_oracle(model, prec, reduce, per_tet):
     abi = _abi()
     m, mu, lam, u, w = problem(6 if per_tet else 7, model, seed=13, per_tet=per_tet)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
-    red = abi.EBB_REDUCE_ATOMIC if reduce == "atomic" else abi.EBB_REDUCE_COLOR
+    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED}[reduce]
     with _mesh(m, mu, lam) as dm:
         got = _run_maps(dm, u, w, model, prec, red, mu, lam)
     tol = TOL[prec]
@@ -71,9 +71,10 @@ def test_small_strain_fp32_relative_accuracy():
         m, mu, lam, u, w = problem(6, model, seed=5, amp=1e-4, smooth=1e-5)
         f, Kw, _ = oracle_maps(m, mu, lam, u, w, model)
         with _mesh(m, mu, lam, colour=False) as dm:
-            got = _run_maps(dm, u, w, model, "f32", abi.EBB_REDUCE_ATOMIC, mu, lam)
-        assert rel_err(got["f"], f) < 1e-5
-        assert rel_err(got["Kw"], Kw) < 1e-5
+            for red in (abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_TILED):
+                got = _run_maps(dm, u, w, model, "f32", red, mu, lam)
+                assert rel_err(got["f"], f) < 1e-5
+                assert rel_err(got["Kw"], Kw) < 1e-5
 
 
 def test_colour_variant_is_bitwise_deterministic():
@@ -91,8 +92,9 @@ def test_permuted_ids_match_oracle():
     m, mu, lam, u, w = problem(5, "stvk", seed=8, permute=True)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, "stvk")
     with _mesh(m, mu, lam) as dm:
-        got = _run_maps(dm, u, w, "stvk", "f32", abi.EBB_REDUCE_ATOMIC, mu, lam)
-    assert rel_err(got["f"], f) < 1e-5 and rel_err(got["Kw"], Kw) < 1e-5
+        for red in (abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_COLOR):
+            got = _run_maps(dm, u, w, "stvk", "f32", red, mu, lam)
+            assert rel_err(got["f"], f) < 1e-5 and rel_err(got["Kw"], Kw) < 1e-5
 
 
 @pytest.mark.parametrize("n,model,prec", [(64, "nh", "f32"), (128, "stvk", "f32"), (32, "stvk", "f64")])
@@ -114,7 +116,7 @@ def test_full_size_sampled_vertices(n, model, prec):
     f = fem.tet_forces(x, sub, B, V, mu_s, lam_s, mdl)[sample]
     Kw = fem.tet_Kv(x, w, sub, B, V, mu_s, lam_s, mdl)[sample]
     with _mesh(m, mu, lam, colour=False) as dm:
-        got = _run_maps(dm, u, w, model, prec, abi.EBB_REDUCE_ATOMIC, mu, lam)
+        got = _run_maps(dm, u, w, model, prec, abi.EBB_REDUCE_TILED, mu, lam)
     tol = TOL[prec]
     assert rel_err(got["f"][sample], f) < tol
     assert rel_err(got["Kw"][sample], Kw) < tol

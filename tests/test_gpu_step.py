@@ -41,7 +41,7 @@ def _oracle_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, u0=None, v
     return u, v, infos
 
 
-def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, reduce="atomic",
+def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, reduce="tiled",
                pin_dtype=torch.uint8, u0=None, v0=None, fail_on_max=False):
     abi = _abi()
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
@@ -54,7 +54,8 @@ def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, re
         prm = abi.step_params(abi.EBB_STVK if model == "stvk" else abi.EBB_NEOHOOKEAN, dt, rho,
                               0.0 if per_tet else mu, 0.0 if per_tet else lam, G,
                               abi.EBB_PREC_F64 if precision == "f64" else abi.EBB_PREC_F32,
-                              abi.EBB_REDUCE_ATOMIC if reduce == "atomic" else abi.EBB_REDUCE_COLOR,
+                              {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR,
+                               "tiled": abi.EBB_REDUCE_TILED}[reduce],
                               max_iters, rtol, fail_on_max)
         reps = []
         for _ in range(steps):
@@ -64,7 +65,7 @@ def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, re
     return u, v, reps
 
 
-@pytest.mark.parametrize("reduce", ["atomic", "colour"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled"])
 def test_stvk_fp64_step_n8_matches_oracle(reduce):
     """8x8x8 StVK FP64 workload: one step, dt = 1e-3, 50 CG iterations
     (early stop at 1e-14 relative residual)."""
