@@ -349,10 +349,18 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
 
   free_tet_data(tets);
+  if (cudaError_t pe = prepare_map_kernels()) return cuda_check(ctx, pe, "configuring map kernels");
   tets->verts = verts;
   const int nt = (int)tets->size;
   const int nv = (int)verts->size;
   if (nt == 0) {
+    // Still build the (empty) vertex index: the lumped mass reads it.
+    std::vector<int4> none, sorted;
+    std::vector<int> perm;
+    std::vector<unsigned char> prefix;
+    ebb_status_t ls =
+        build_layout(ctx, tets, none, std::vector<double>((size_t)3 * nv, 0.0), perm, sorted, prefix);
+    if (ls) return ls;
     tets->finalized = true;
     return EBB_OK;
   }
@@ -396,7 +404,8 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   if (s) return s;
   std::vector<int> perm;
   std::vector<int4> sorted;
-  s = build_layout(ctx, tets, packed, hX, perm, sorted);
+  std::vector<unsigned char> prefix;
+  s = build_layout(ctx, tets, packed, hX, perm, sorted, prefix);
   if (s) return s;
   packed.swap(sorted);
 
@@ -433,6 +442,11 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     return cuda_check(ctx, e, "rest-shape precomputation");
   }
   s = read_device_error(ctx);
+  if (s) {
+    free_tet_data(tets);
+    return s;
+  }
+  s = build_tile_blobs(ctx, tets, prefix);
   if (s) {
     free_tet_data(tets);
     return s;

@@ -18,6 +18,7 @@
 // both precisions; the element maps run in the element precision T.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <string>
 
 #include "ebb_internal.h"
@@ -275,8 +276,23 @@ __global__ void step_finish_kernel(int n, double dt, const double* __restrict__ 
 
 }  // namespace
 
+// Everything a captured CG chunk bakes into its kernel arguments; a change
+// of any field re-captures the graph.
+struct ChunkKey {
+  int elem_bytes, pin_bytes, model, reduce;
+  double mu0, lam0;
+  StepConst c;
+  const void* pin;
+  const void* u;
+};
+
 struct StepScratch {
   int nv = 0;
+  cudaStream_t stream = nullptr;        // internal stream (capturable)
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t chunk = nullptr;      // kChunk captured CG iterations
+  ChunkKey key;
+  bool have_key = false;
   void* acc[4] = {nullptr, nullptr, nullptr, nullptr};   // f, Kv, diag, Kp in element precision
   void* ue = nullptr;                                    // element-precision displacement
   void* pe = nullptr;                                    // element-precision v, then p
@@ -301,6 +317,9 @@ void free_step_scratch(ebb_rel_s* rel) {
   cudaFree(s->part);
   cudaFree(s->sc);
   if (s->h_sc) cudaFreeHost(s->h_sc);
+  if (s->chunk) cudaGraphExecDestroy(s->chunk);
+  if (s->ev) cudaEventDestroy(s->ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
   rel->step = nullptr;
 }
@@ -327,6 +346,8 @@ ebb_status_t ensure_scratch(ebb_ctx_s* ctx, ebb_rel_s* tets) {
   if (e == cudaSuccess) e = cudaMalloc(&s->part, 4 * kVecBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->sc, sizeof(CgScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&s->h_sc, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     free_step_scratch(tets);
     cudaGetLastError();
@@ -342,16 +363,20 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   StepScratch* s = tets->step;
   const int nv = s->nv;
   const int n = 3 * nv;
-  const int nt = (int)tets->size;
-  cudaStream_t st = ctx->stream;
+  // All step work runs on the library's own stream, ordered after the
+  // caller's stream; the call is synchronous.
+  cudaStream_t st = s->stream;
+  cudaError_t e = cudaEventRecord(s->ev, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->ev, 0);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "ordering after the caller's stream");
   T* acc_f = (T*)s->acc[0];
   T* acc_kv = (T*)s->acc[1];
   T* acc_d = (T*)s->acc[2];
   T* acc_kp = (T*)s->acc[3];
   T* ue = (T*)s->ue;
   T* pe = (T*)s->pe;
-  cudaError_t e = cudaSuccess;
 
+  if (tets->vindex.off == nullptr) return set_error(ctx, EBB_ERR_STATE, "relation has no vertex index");
   if (s->rho != prm->rho) {
     mass_kernel<<<(nv + 255) / 256, 256, 0, st>>>(nv, tets->vindex.off, tets->vindex.ent, tets->s64.V, prm->rho,
                                                    s->mass);
@@ -361,6 +386,7 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   }
 
   StepConst c;
+  memset(&c, 0, sizeof c);
   c.nv = nv;
   c.dt = prm->dt;
   c.g[0] = prm->gravity[0];
@@ -397,26 +423,60 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   kio.w = mixed ? pe : (const T*)s->p;
   kio.Kw = acc_kp;
 
-  int launched = 0;
-  ebb_status_t status = EBB_OK;
-  while (true) {
-    for (int k = 0; k < kChunk; ++k) {
+  // kChunk CG iterations (plus the status read-back) are captured once as a
+  // CUDA graph and relaunched until the device reports convergence.
+  ChunkKey key;
+  memset(&key, 0, sizeof key);
+  key.elem_bytes = (int)sizeof(T);
+  key.pin_bytes = (int)sizeof(PT);
+  key.model = prm->model;
+  key.reduce = prm->reduce;
+  key.mu0 = prm->mu;
+  key.lam0 = prm->lambda;
+  key.c = c;
+  key.pin = pin;
+  key.u = kio.u;
+  if (!s->chunk || !s->have_key || memcmp(&key, &s->key, sizeof key) != 0) {
+    if (s->chunk) cudaGraphExecDestroy(s->chunk);
+    s->chunk = nullptr;
+    s->have_key = false;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "CG chunk capture");
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kChunk && le == cudaSuccess; ++k) {
       const int par = k & 1;
-      e = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
-      if (e != cudaSuccess) break;
+      le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
       cg_pq_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->sc, part_a);
       cg_update_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->dinv,
                                                                    s->r, s->y, s->sc, part_a, part_b);
       cg_pupdate_kernel<T><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, s->r, s->dinv, s->p, mixed ? pe : nullptr,
                                                                acc_kp, s->sc, part_b);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) break;
+      if (le == cudaSuccess) le = cudaGetLastError();
     }
-    if (e != cudaSuccess) return cuda_check(ctx, e, "CG iteration launch");
-    launched += kChunk;
-    e = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
+    if (le == cudaSuccess) le = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_check(ctx, le != cudaSuccess ? le : e, "CG chunk capture");
+    }
+    e = cudaGraphInstantiate(&s->chunk, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      s->chunk = nullptr;
+      return cuda_check(ctx, e, "CG chunk instantiate");
+    }
+    s->key = key;
+    s->have_key = true;
+  }
+
+  int launched = 0;
+  ebb_status_t status = EBB_OK;
+  while (true) {
+    e = cudaGraphLaunch(s->chunk, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "CG status read");
+    if (e != cudaSuccess) return cuda_check(ctx, e, "CG chunk");
+    launched += kChunk;
     const CgScalars& h = *s->h_sc;
     if (h.status != EBB_OK) {
       status = h.status;

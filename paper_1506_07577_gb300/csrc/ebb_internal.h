@@ -43,20 +43,42 @@ struct Colouring {
   TetStreams<float> s32;
 };
 
-// Tiles of consecutive (Morton-ordered) tets for the shared-memory
-// pre-reduced maps.  Tile i covers internal tet rows [tet_off[i],
-// tet_off[i+1]) and the distinct vertices vtx[vtx_off[i] .. vtx_off[i+1]);
-// slots[t] holds the tile-local index of each of tet t's four vertices.
+// Tiles of consecutive (Morton-ordered) tets for the shared-memory maps.
+// A tile holds up to kTileTets tets touching at most kTileSlots distinct
+// vertices ("slots").  Everything a tile needs except the vertex fields is
+// packed into one contiguous blob (one bulk copy per tile):
+//   header  int4 {ntets, nslots, first internal tet row, 0}
+//   slots   uchar4[kTileTets]        tile-local slot of each tet corner
+//   ent     u16[4*kTileTets]         per slot, its (corner, tet) entries a*256+t
+//   eoff    u16[kTileSlots + 8]      slot j's entries are ent[eoff[j] .. eoff[j+1])
+//                                    (low 15 bits); bit 15 marks a vertex that no
+//                                    other tile touches
+//   vtx     int[kTileSlots]          vertex id of each slot
+//   B       T[9][kTileTets]          Dm^-1, entry (r,c) in plane 3r+c
+//   V       T[kTileTets]             rest volume
+//   mu,lam  T[kTileTets] each        per-tet Lame parameters (if bound)
+// Unused tail entries are zero.
 constexpr int kTileTets = 256;   // tets per tile (= threads per CTA)
 constexpr int kTileSlots = 256;  // distinct vertices per tile (u8 slots)
+constexpr unsigned short kOwnedBit = 0x8000;
+constexpr int kBlobSlots = 16;
+constexpr int kBlobEnt = kBlobSlots + 4 * kTileTets;
+constexpr int kBlobEoff = kBlobEnt + 2 * 4 * kTileTets;
+constexpr int kBlobVtx = kBlobEoff + 2 * (kTileSlots + 8);
+constexpr int kBlobPrefix = kBlobVtx + 4 * kTileSlots;
+static_assert(kBlobPrefix % 16 == 0, "blob prefix must keep 16-byte alignment");
+
+struct BlobLayout {
+  int bytes = 0;           // per tile (multiple of 128)
+  int B = 0, V = 0;        // byte offsets of the element-precision arrays
+  int mu = -1, lam = -1;   // -1: uniform material
+};
 
 struct Tiles {
   int ntiles = 0;
-  int* tet_off = nullptr;
-  int* vtx_off = nullptr;
-  int* vtx = nullptr;
-  uchar4* slots = nullptr;
-  int total_vtx = 0;
+  unsigned char* blob32 = nullptr;
+  unsigned char* blob64 = nullptr;
+  BlobLayout L32, L64;
 };
 
 // Inverse of the key-field (Section 6.1 GroupBy): for vertex v the entries
@@ -130,6 +152,10 @@ cudaError_t launch_tet_map(ebb_rel_s* rel, int model, int ops, ebb_reduce_t redu
                            T mu0, T lam0, const MapIO<T>& io, const int* active,
                            cudaStream_t stream);
 
+// Set the tiled kernels' shared-memory attributes on the current device
+// (tet_maps.cu).
+cudaError_t prepare_map_kernels();
+
 // Free the per-relation step scratch (cg.cu).
 void free_step_scratch(ebb_rel_s* rel);
 
@@ -140,11 +166,16 @@ ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, doubl
 
 // Morton order, tiles and vertex index from host keys (layout.cu).  `keys`
 // and `X` are the caller's order (X as 3 planes of nv); on return
-// `perm[i]` is the caller's row of internal row i and the device-side
-// tiles / vertex index of `tets` are built for the internal order.
+// `perm[i]` is the caller's row of internal row i, the vertex index and
+// tet_perm of `tets` are on the device, and `prefix` holds the integer part
+// of every tile blob (kBlobPrefix bytes per tile).
 ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
                           const std::vector<double>& X, std::vector<int>& perm,
-                          std::vector<int4>& sorted_keys);
+                          std::vector<int4>& sorted_keys, std::vector<unsigned char>& prefix);
+
+// Pack the tile blobs (both precisions) from the host prefix and the
+// device-side per-tet streams (layout.cu).
+ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix);
 void free_layout(ebb_rel_s* tets);
 
 // Build the colouring (colour.cu).

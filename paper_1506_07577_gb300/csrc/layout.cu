@@ -1,19 +1,19 @@
-// Internal layout of a finalized tets relation (host-side construction).
+// Internal layout of a finalized tets relation.
 //
 // Keys are opaque (Section 5.1, and its footnote: the runtime is free to
 // reorder relations), so the library stores tets in its own order:
 //   1. Morton order of the tet centroids over the rest shape, which keeps
 //      tets that share vertices next to each other;
 //   2. tiles of up to kTileTets consecutive tets touching at most kTileSlots
-//      distinct vertices, with a tile-local u8 slot per tet corner (the tiled
-//      map gathers and pre-reduces through shared memory);
+//      distinct vertices; each tile's data is packed into one contiguous blob
+//      (see ebb_internal.h) that the tiled map fetches with one bulk copy;
 //   3. the inverse of the key-field, vertex -> (tet, corner) entries in CSR
 //      form: Section 6.1 groups a relation by a key-field by sorting it and
 //      adding a [begin, end) index to the target, which is exactly this.
 #include <algorithm>
 #include <cstdint>
 #include <cstdio>
-#include <numeric>
+#include <cstring>
 #include <vector>
 
 #include "ebb_internal.h"
@@ -44,13 +44,53 @@ cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   return cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st);
 }
 
+BlobLayout make_layout(size_t elem, bool material) {
+  BlobLayout L;
+  L.B = kBlobPrefix;
+  L.V = L.B + (int)(9 * kTileTets * elem);
+  int end = L.V + (int)(kTileTets * elem);
+  if (material) {
+    L.mu = end;
+    L.lam = L.mu + (int)(kTileTets * elem);
+    end = L.lam + (int)(kTileTets * elem);
+  }
+  L.bytes = (end + 127) / 128 * 128;
+  return L;
+}
+
+// One CTA per tile: copy the integer prefix, then gather the tile's per-tet
+// element-precision values from the planar streams (zero past the tile end).
+template <typename T>
+__global__ void pack_blob_kernel(int nt, const unsigned char* __restrict__ prefix, TetStreams<T> s, BlobLayout L,
+                                 unsigned char* blob) {
+  const int tile = blockIdx.x;
+  unsigned char* b = blob + (size_t)tile * L.bytes;
+  const int4* src = reinterpret_cast<const int4*>(prefix + (size_t)tile * kBlobPrefix);
+  int4* dst = reinterpret_cast<int4*>(b);
+  for (int i = threadIdx.x; i < kBlobPrefix / 16; i += blockDim.x) dst[i] = src[i];
+  const int4 hdr = src[0];
+  const int ntets = hdr.x, tb = hdr.z;
+  T* B = reinterpret_cast<T*>(b + L.B);
+  T* V = reinterpret_cast<T*>(b + L.V);
+  T* mu = L.mu >= 0 ? reinterpret_cast<T*>(b + L.mu) : nullptr;
+  T* lam = L.lam >= 0 ? reinterpret_cast<T*>(b + L.lam) : nullptr;
+  for (int i = threadIdx.x; i < kTileTets; i += blockDim.x) {
+    const bool in = i < ntets;
+    const int t = tb + i;
+    for (int k = 0; k < 9; ++k) B[k * kTileTets + i] = in ? s.B[(size_t)k * nt + t] : T(0);
+    V[i] = in ? s.V[t] : T(0);
+    if (mu) {
+      mu[i] = in ? s.mu[t] : T(0);
+      lam[i] = in ? s.lam[t] : T(0);
+    }
+  }
+}
+
 }  // namespace
 
 void free_layout(ebb_rel_s* tets) {
-  cudaFree(tets->tiles.tet_off);
-  cudaFree(tets->tiles.vtx_off);
-  cudaFree(tets->tiles.vtx);
-  cudaFree(tets->tiles.slots);
+  cudaFree(tets->tiles.blob32);
+  cudaFree(tets->tiles.blob64);
   tets->tiles = Tiles();
   cudaFree(tets->vindex.off);
   cudaFree(tets->vindex.ent);
@@ -60,7 +100,8 @@ void free_layout(ebb_rel_s* tets) {
 }
 
 ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
-                          const std::vector<double>& X, std::vector<int>& perm, std::vector<int4>& sorted) {
+                          const std::vector<double>& X, std::vector<int>& perm, std::vector<int4>& sorted,
+                          std::vector<unsigned char>& prefix) {
   const int nt = (int)keys.size();
   const int nv = (int)(X.size() / 3);
   cudaStream_t st = ctx->stream;
@@ -97,42 +138,7 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     sorted[i] = keys[perm[i]];
   }
 
-  // 2. Tiles.
-  std::vector<int> tet_off{0}, vtx_off{0}, vtx;
-  std::vector<uchar4> slots(nt);
-  std::vector<int> stamp(nv, -1), slot_of(nv, 0);
-  int tile = 0, tile_tets = 0, tile_vtx = 0;
-  for (int i = 0; i < nt; ++i) {
-    const int k[4] = {sorted[i].x, sorted[i].y, sorted[i].z, sorted[i].w};
-    int fresh = 0;
-    for (int a = 0; a < 4; ++a) fresh += stamp[k[a]] != tile;
-    if (tile_tets == kTileTets || tile_vtx + fresh > kTileSlots) {
-      tet_off.push_back(i);
-      vtx_off.push_back((int)vtx.size());
-      ++tile;
-      tile_tets = 0;
-      tile_vtx = 0;
-    }
-    unsigned char s[4];
-    for (int a = 0; a < 4; ++a) {
-      const int v = k[a];
-      if (stamp[v] != tile) {
-        stamp[v] = tile;
-        slot_of[v] = tile_vtx++;
-        vtx.push_back(v);
-      }
-      s[a] = (unsigned char)slot_of[v];
-    }
-    slots[i] = make_uchar4(s[0], s[1], s[2], s[3]);
-    ++tile_tets;
-  }
-  if (tile_tets > 0) {
-    tet_off.push_back(nt);
-    vtx_off.push_back((int)vtx.size());
-  }
-  const int ntiles = (int)tet_off.size() - 1;
-
-  // 3. Vertex -> (tet, corner) index in internal order.
+  // 2. Vertex -> (tet, corner) index in internal order.
   std::vector<int> voff(nv + 1, 0), vent((size_t)4 * nt);
   for (int i = 0; i < nt; ++i) {
     voff[sorted[i].x + 1]++;
@@ -149,11 +155,95 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     }
   }
 
-  cudaError_t e = upload(&tets->tiles.tet_off, tet_off, st);
-  if (e == cudaSuccess) e = upload(&tets->tiles.vtx_off, vtx_off, st);
-  if (e == cudaSuccess) e = upload(&tets->tiles.vtx, vtx, st);
-  if (e == cudaSuccess) e = upload(&tets->tiles.slots, slots, st);
-  if (e == cudaSuccess) e = upload(&tets->vindex.off, voff, st);
+  // 3. Tiles: greedy cut of the Morton order, then the blob prefix per tile.
+  std::vector<int> tet_off{0};
+  {
+    std::vector<int> stamp(nv, -1);
+    int tile = 0, tile_tets = 0, tile_vtx = 0;
+    for (int i = 0; i < nt; ++i) {
+      const int k[4] = {sorted[i].x, sorted[i].y, sorted[i].z, sorted[i].w};
+      int fresh = 0;
+      for (int a = 0; a < 4; ++a) fresh += stamp[k[a]] != tile;
+      if (tile_tets == kTileTets || tile_vtx + fresh > kTileSlots) {
+        tet_off.push_back(i);
+        ++tile;
+        tile_tets = 0;
+        tile_vtx = 0;
+        fresh = 4;
+      }
+      for (int a = 0; a < 4; ++a)
+        if (stamp[k[a]] != tile) {
+          stamp[k[a]] = tile;
+          ++tile_vtx;
+        }
+      ++tile_tets;
+    }
+    if (tile_tets > 0) tet_off.push_back(nt);
+  }
+  const int ntiles = (int)tet_off.size() - 1;
+  prefix.assign((size_t)ntiles * kBlobPrefix, 0);
+  {
+    std::vector<int> slot_of(nv, -1);
+    std::vector<int> vtx;
+    std::vector<int> cnt(kTileSlots + 1);
+    for (int ti = 0; ti < ntiles; ++ti) {
+      unsigned char* b = prefix.data() + (size_t)ti * kBlobPrefix;
+      uchar4* slots = reinterpret_cast<uchar4*>(b + kBlobSlots);
+      unsigned short* ent = reinterpret_cast<unsigned short*>(b + kBlobEnt);
+      unsigned short* eoff = reinterpret_cast<unsigned short*>(b + kBlobEoff);
+      int* bvtx = reinterpret_cast<int*>(b + kBlobVtx);
+      const int tb = tet_off[ti], te = tet_off[ti + 1];
+      // Distinct vertices of the tile, numbered by decreasing entry count so
+      // that the threads of one warp sum similar numbers of entries.
+      vtx.clear();
+      for (int t = tb; t < te; ++t) {
+        const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
+        for (int a = 0; a < 4; ++a) {
+          if (slot_of[k[a]] < 0) {
+            slot_of[k[a]] = 0;
+            vtx.push_back(k[a]);
+          }
+          slot_of[k[a]]++;
+        }
+      }
+      std::stable_sort(vtx.begin(), vtx.end(), [&](int a, int b) { return slot_of[a] > slot_of[b]; });
+      for (size_t j = 0; j < vtx.size(); ++j) slot_of[vtx[j]] = (int)j;
+      for (int t = tb; t < te; ++t) {
+        const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
+        slots[t - tb] = make_uchar4((unsigned char)slot_of[k[0]], (unsigned char)slot_of[k[1]],
+                                    (unsigned char)slot_of[k[2]], (unsigned char)slot_of[k[3]]);
+      }
+      const int nvu = (int)vtx.size();
+      std::fill(cnt.begin(), cnt.end(), 0);
+      for (int t = tb; t < te; ++t) {
+        const uchar4 s4 = slots[t - tb];
+        cnt[s4.x + 1]++;
+        cnt[s4.y + 1]++;
+        cnt[s4.z + 1]++;
+        cnt[s4.w + 1]++;
+      }
+      for (int j = 0; j < nvu; ++j) cnt[j + 1] += cnt[j];
+      for (int j = 0; j <= nvu; ++j) eoff[j] = (unsigned short)cnt[j];
+      for (int j = 0; j < nvu; ++j) {
+        const int v = vtx[j];
+        bvtx[j] = v;
+        if (voff[v + 1] - voff[v] == cnt[j + 1] - cnt[j]) eoff[j] |= kOwnedBit;
+        slot_of[v] = -1;
+      }
+      for (int t = tb; t < te; ++t) {
+        const uchar4 s4 = slots[t - tb];
+        const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
+        for (int a = 0; a < 4; ++a) ent[cnt[sl[a]]++] = (unsigned short)(a * 256 + (t - tb));
+      }
+      int* hdr = reinterpret_cast<int*>(b);
+      hdr[0] = te - tb;
+      hdr[1] = nvu;
+      hdr[2] = tb;
+      hdr[3] = 0;
+    }
+  }
+
+  cudaError_t e = upload(&tets->vindex.off, voff, st);
   if (e == cudaSuccess) e = upload(&tets->vindex.ent, vent, st);
   if (e == cudaSuccess) e = upload(&tets->tet_perm, perm, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -163,7 +253,33 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     return set_error(ctx, EBB_ERR_NOMEM, std::string("building the tet layout: ") + cudaGetErrorString(e));
   }
   tets->tiles.ntiles = ntiles;
-  tets->tiles.total_vtx = (int)vtx.size();
+  return EBB_OK;
+}
+
+ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix) {
+  Tiles& tl = tets->tiles;
+  const int ntiles = tl.ntiles;
+  if (ntiles == 0) return EBB_OK;
+  cudaStream_t st = ctx->stream;
+  const bool material = tets->s64.mu != nullptr;
+  tl.L32 = make_layout(sizeof(float), material);
+  tl.L64 = make_layout(sizeof(double), material);
+  unsigned char* dprefix = nullptr;
+  cudaError_t e = upload(&dprefix, prefix, st);
+  if (e == cudaSuccess) e = cudaMalloc(&tl.blob32, (size_t)ntiles * tl.L32.bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&tl.blob64, (size_t)ntiles * tl.L64.bytes);
+  if (e == cudaSuccess) {
+    const int nt = (int)tets->size;
+    pack_blob_kernel<float><<<ntiles, 256, 0, st>>>(nt, dprefix, tets->s32, tl.L32, tl.blob32);
+    pack_blob_kernel<double><<<ntiles, 256, 0, st>>>(nt, dprefix, tets->s64, tl.L64, tl.blob64);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dprefix);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ctx, EBB_ERR_NOMEM, std::string("packing tile blobs: ") + cudaGetErrorString(e));
+  }
   return EBB_OK;
 }
 
