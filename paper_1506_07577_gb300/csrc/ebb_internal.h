@@ -46,27 +46,33 @@ struct Colouring {
 // Tiles of consecutive (Morton-ordered) tets for the shared-memory maps.
 // A tile holds up to kTileTets tets touching at most kTileSlots distinct
 // vertices ("slots").  Everything a tile needs except the vertex fields is
-// packed into one contiguous blob (one bulk copy per tile):
-//   header  int4 {ntets, nslots, first internal tet row, 0}
+// packed into one contiguous blob:
+//   header  int4 {ntets, nslots, first internal tet row, nunits}
 //   slots   uchar4[kTileTets]        tile-local slot of each tet corner
-//   ent     u16[4*kTileTets]         per slot, its (corner, tet) entries a*256+t
-//   eoff    u16[kTileSlots + 8]      slot j's entries are ent[eoff[j] .. eoff[j+1])
-//                                    (low 15 bits); bit 15 marks a vertex that no
-//                                    other tile touches
+//   ent     u16[kTileTets][kUnitEntries]  entries (corner, tet) = a*256+t summed
+//                                    by thread i, padded with a*256+kTileTets
+//                                    (a row that is always zero)
+//   units   u32[kTileTets]           reduction work of thread i: bit 0 has a
+//                                    unit, 14-21 slot, 22-25 lanes after this
+//                                    one in the same slot and warp, 26 first
+//                                    lane of that run (adds the sum into the
+//                                    field)
 //   vtx     int[kTileSlots]          vertex id of each slot
 //   B       T[9][kTileTets]          Dm^-1, entry (r,c) in plane 3r+c
 //   V       T[kTileTets]             rest volume
 //   mu,lam  T[kTileTets] each        per-tet Lame parameters (if bound)
 // Unused tail entries are zero.
-constexpr int kTileTets = 256;   // tets per tile (= threads per CTA)
-constexpr int kTileSlots = 256;  // distinct vertices per tile (u8 slots)
-constexpr unsigned short kOwnedBit = 0x8000;
+constexpr int kTileTets = 128;   // tets per tile (= threads per CTA)
+constexpr int kTileSlots = 128;  // distinct vertices per tile (u8 slots)
+constexpr int kUnitEntries = 8;  // entries summed by one thread
+constexpr int kUnitMaxRun = 16;  // units of one slot (4-bit lane count)
 constexpr int kBlobSlots = 16;
 constexpr int kBlobEnt = kBlobSlots + 4 * kTileTets;
-constexpr int kBlobEoff = kBlobEnt + 2 * 4 * kTileTets;
-constexpr int kBlobVtx = kBlobEoff + 2 * (kTileSlots + 8);
+constexpr int kBlobUnits = kBlobEnt + 2 * kUnitEntries * kTileTets;
+constexpr int kBlobVtx = kBlobUnits + 4 * kTileTets;
 constexpr int kBlobPrefix = kBlobVtx + 4 * kTileSlots;
 static_assert(kBlobPrefix % 16 == 0, "blob prefix must keep 16-byte alignment");
+static_assert(kTileTets < 256 && kTileSlots <= 256, "entry code and unit descriptor field widths");
 
 struct BlobLayout {
   int bytes = 0;           // per tile (multiple of 128)

@@ -155,32 +155,47 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     }
   }
 
-  // 3. Tiles: greedy cut of the Morton order, then the blob prefix per tile.
+  // 3. Tiles: greedy cut of the Morton order.  A tile closes before it would
+  // exceed kTileTets tets, kTileSlots distinct vertices, kTileTets reduction
+  // units (ceil(entries / kUnitEntries) summed over its vertices) or
+  // kUnitMaxRun units for one vertex.
   std::vector<int> tet_off{0};
   {
-    std::vector<int> stamp(nv, -1);
-    int tile = 0, tile_tets = 0, tile_vtx = 0;
+    std::vector<int> stamp(nv, -1), count(nv, 0);
+    int tile = 0, tile_tets = 0, tile_vtx = 0, tile_units = 0;
     for (int i = 0; i < nt; ++i) {
       const int k[4] = {sorted[i].x, sorted[i].y, sorted[i].z, sorted[i].w};
-      int fresh = 0;
-      for (int a = 0; a < 4; ++a) fresh += stamp[k[a]] != tile;
-      if (tile_tets == kTileTets || tile_vtx + fresh > kTileSlots) {
+      int fresh = 0, more_units = 0;
+      bool run_ok = true;
+      for (int a = 0; a < 4; ++a) {
+        const int c = stamp[k[a]] == tile ? count[k[a]] : 0;
+        fresh += c == 0;
+        more_units += c % kUnitEntries == 0;
+        run_ok = run_ok && (c + 1 + kUnitEntries - 1) / kUnitEntries <= kUnitMaxRun;
+      }
+      if (tile_tets == kTileTets || tile_vtx + fresh > kTileSlots || tile_units + more_units > kTileTets ||
+          !run_ok) {
         tet_off.push_back(i);
         ++tile;
-        tile_tets = 0;
-        tile_vtx = 0;
-        fresh = 4;
+        tile_tets = tile_vtx = tile_units = 0;
       }
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 4; ++a) {
         if (stamp[k[a]] != tile) {
           stamp[k[a]] = tile;
+          count[k[a]] = 0;
           ++tile_vtx;
         }
+        if (count[k[a]] % kUnitEntries == 0) ++tile_units;
+        ++count[k[a]];
+      }
       ++tile_tets;
     }
     if (tile_tets > 0) tet_off.push_back(nt);
   }
   const int ntiles = (int)tet_off.size() - 1;
+
+  // 4. Blob prefix per tile: slots (numbered by decreasing entry count), the
+  // entries grouped by slot, the reduction units and the vertex ids.
   prefix.assign((size_t)ntiles * kBlobPrefix, 0);
   {
     std::vector<int> slot_of(nv, -1);
@@ -190,11 +205,9 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
       unsigned char* b = prefix.data() + (size_t)ti * kBlobPrefix;
       uchar4* slots = reinterpret_cast<uchar4*>(b + kBlobSlots);
       unsigned short* ent = reinterpret_cast<unsigned short*>(b + kBlobEnt);
-      unsigned short* eoff = reinterpret_cast<unsigned short*>(b + kBlobEoff);
+      uint32_t* units = reinterpret_cast<uint32_t*>(b + kBlobUnits);
       int* bvtx = reinterpret_cast<int*>(b + kBlobVtx);
       const int tb = tet_off[ti], te = tet_off[ti + 1];
-      // Distinct vertices of the tile, numbered by decreasing entry count so
-      // that the threads of one warp sum similar numbers of entries.
       vtx.clear();
       for (int t = tb; t < te; ++t) {
         const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
@@ -206,7 +219,7 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
           slot_of[k[a]]++;
         }
       }
-      std::stable_sort(vtx.begin(), vtx.end(), [&](int a, int b) { return slot_of[a] > slot_of[b]; });
+      std::stable_sort(vtx.begin(), vtx.end(), [&](int x, int y) { return slot_of[x] > slot_of[y]; });
       for (size_t j = 0; j < vtx.size(); ++j) slot_of[vtx[j]] = (int)j;
       for (int t = tb; t < te; ++t) {
         const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
@@ -223,23 +236,46 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
         cnt[s4.w + 1]++;
       }
       for (int j = 0; j < nvu; ++j) cnt[j + 1] += cnt[j];
-      for (int j = 0; j <= nvu; ++j) eoff[j] = (unsigned short)cnt[j];
-      for (int j = 0; j < nvu; ++j) {
-        const int v = vtx[j];
-        bvtx[j] = v;
-        if (voff[v + 1] - voff[v] == cnt[j + 1] - cnt[j]) eoff[j] |= kOwnedBit;
-        slot_of[v] = -1;
+      // Units: thread i sums a run of <= kUnitEntries entries of one slot
+      // (padded to kUnitEntries with the zero row).  Consecutive units of a
+      // slot inside one warp form a segment combined by shuffles; its first
+      // lane adds the sum into the field.
+      std::vector<unsigned short> grouped(cnt[nvu]);
+      {
+        std::vector<int> fill(cnt.begin(), cnt.begin() + nvu);
+        for (int t = tb; t < te; ++t) {
+          const uchar4 s4 = slots[t - tb];
+          const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
+          for (int a = 0; a < 4; ++a) grouped[fill[sl[a]]++] = (unsigned short)(a * 256 + (t - tb));
+        }
       }
-      for (int t = tb; t < te; ++t) {
-        const uchar4 s4 = slots[t - tb];
-        const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
-        for (int a = 0; a < 4; ++a) ent[cnt[sl[a]]++] = (unsigned short)(a * 256 + (t - tb));
+      int nunits = 0;
+      std::vector<int> uslot;
+      for (int j = 0; j < nvu; ++j) {
+        for (int e = cnt[j]; e < cnt[j + 1]; e += kUnitEntries) {
+          const int n = std::min(kUnitEntries, cnt[j + 1] - e);
+          for (int q = 0; q < kUnitEntries; ++q)
+            ent[nunits * kUnitEntries + q] = q < n ? grouped[e + q] : (unsigned short)kTileTets;
+          units[nunits] = 1u | ((uint32_t)j << 14);
+          uslot.push_back(j);
+          ++nunits;
+        }
+      }
+      for (int i = 0; i < nunits; ++i) {
+        const bool head = i == 0 || uslot[i - 1] != uslot[i] || (i % 32) == 0;
+        int last = i;
+        while (last + 1 < nunits && uslot[last + 1] == uslot[i] && (last + 1) % 32 != 0) ++last;
+        units[i] |= ((uint32_t)(last - i) << 22) | ((uint32_t)head << 26);
+      }
+      for (int j = 0; j < nvu; ++j) {
+        bvtx[j] = vtx[j];
+        slot_of[vtx[j]] = -1;
       }
       int* hdr = reinterpret_cast<int*>(b);
       hdr[0] = te - tb;
       hdr[1] = nvu;
       hdr[2] = tb;
-      hdr[3] = 0;
+      hdr[3] = nunits;
     }
   }
 

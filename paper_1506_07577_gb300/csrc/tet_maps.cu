@@ -169,45 +169,135 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
   }
 }
 
-// ---- tiled: persistent CTAs, one tile blob per bulk copy ---------------------
-// Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...  Two blob
-// buffers alternate: while tile i is computed, the blob of tile i+G is in
-// flight (cp.async.bulk on an mbarrier) and the vertex values of tile i+G are
-// being loaded into registers.  Per tile:
-//   phase 1  one tet per thread: corner values from the slot arrays su/sw,
-//            per-corner outputs to so[NO][4][kTileTets] (conflict-free);
-//   phase 2  one slot per thread: sum the slot's (corner, tet) entries in a
-//            fixed order, then one atomic add per component into the vertex
-//            field (a fire-and-forget reduction: no load on the critical path).
-// Dynamic shared memory: blob[2] | slot values[2] (su[3][S], then sw[3][S] for
-// K w) | so[NO][4][TT] | mbarrier[2].  Slot values are double buffered so the
-// next tile's vertex values can be stored before the current tile's
-// reduction; two barriers per tile.
+// ---- tiled: persistent CTAs over tile blobs --------------------------------
+// Each CTA walks tiles blockIdx.x, blockIdx.x + G, ... (G = gridDim.x).  The
+// integer part of each tile blob (slots, entries, reduction units, vertex
+// ids) is fetched with one cp.async.bulk into a 3-deep shared ring, two
+// tiles ahead; the per-tet floats (Dm^-1, V, Lame) are read straight from
+// the blob in global memory with coalesced loads one tile ahead into
+// registers, and the next tile's vertex values are loaded into registers
+// while the current tile computes.  Per tile, with one CTA barrier:
+//   phase 1  one tet per thread: corner values from the slot vectors,
+//            element evaluation, per-corner outputs to shared memory (fields
+//            interleaved, conflict-free); then the prefetched vertex values
+//            of the next tile go to the other slot buffer;
+//                                    -- the one barrier per tile --
+//   phase 2  one reduction unit per thread: the sum of at most kUnitEntries
+//            entries of one vertex, in a fixed order; the units of one vertex
+//            on consecutive lanes are combined by a segmented shuffle tree and
+//            the run's first lane issues one atomic add per component (a
+//            fire-and-forget reduction).  Every thread does at most
+//            kUnitEntries steps, whatever the vertex degrees.
+// Slot vectors and per-corner outputs are double buffered, so phase 2 of one
+// tile overlaps phase 1 of the next.
+// Dynamic shared memory: prefix ring[3] | slot vectors[2] (u[S][4], then
+// w[S][4] for K w) | outputs[2][4][3][TT+1][NF] | mbarrier[3].
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+constexpr int kRing = 3;
 
 template <typename T, int OPS>
 struct TileSmem {
   static constexpr bool FO = (OPS & OP_FORCE) != 0;
   static constexpr bool KV = (OPS & OP_KV) != 0;
   static constexpr bool DG = (OPS & OP_DIAG) != 0;
-  static constexpr int NO = (FO ? 3 : 0) + (KV ? 3 : 0) + (DG ? 3 : 0);
+  static constexpr int NF = (FO ? 1 : 0) + (KV ? 1 : 0) + (DG ? 1 : 0);  // output fields
   static constexpr int S = kTileSlots;
   static constexpr int TT = kTileTets;
-  static constexpr size_t slot_elems = 3 * S * (KV ? 2 : 1);  // su (+ sw) for one tile
-  static constexpr size_t fixed = sizeof(T) * 2 * slot_elems + sizeof(T) * NO * 4 * TT + 2 * sizeof(uint64_t);
-  static size_t bytes(const BlobLayout& L) { return 2 * (size_t)L.bytes + fixed; }
+  static constexpr size_t slot_elems = (size_t)S * 4 * (KV ? 2 : 1);
+  static constexpr size_t out_elems = (size_t)4 * 3 * (TT + 1) * NF;  // row TT stays zero
+  static constexpr size_t ring_bytes = (size_t)kRing * kBlobPrefix;
+  static constexpr size_t bytes = ring_bytes + sizeof(T) * (2 * slot_elems + 2 * out_elems) + kRing * sizeof(uint64_t);
 };
 
+template <typename T>
+struct TetRegs {
+  T B[9];
+  T V, mu, lam;
+};
+
+// Coalesced loads of one tile's per-tet floats (the blob is zero padded, so
+// every thread may load).
+template <typename T>
+__device__ __forceinline__ void load_tet_regs(const unsigned char* blob, const BlobLayout& L, int tid, T mu0,
+                                              T lam0, TetRegs<T>& r) {
+  const T* B = reinterpret_cast<const T*>(blob + L.B);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) r.B[i] = B[i * kTileTets + tid];
+  r.V = reinterpret_cast<const T*>(blob + L.V)[tid];
+  r.mu = L.mu >= 0 ? reinterpret_cast<const T*>(blob + L.mu)[tid] : mu0;
+  r.lam = L.lam >= 0 ? reinterpret_cast<const T*>(blob + L.lam)[tid] : lam0;
+}
+
+// 3-vectors stored 4 wide in shared memory.
+__device__ __forceinline__ void ld3(const float* p, float* v) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+}
+__device__ __forceinline__ void ld3(const double* p, double* v) {
+  const double2 q = *reinterpret_cast<const double2*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = p[2];
+}
+__device__ __forceinline__ void st3(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], 0.f);
+}
+__device__ __forceinline__ void st3(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  p[2] = v[2];
+}
+
+// NF interleaved output values at p.
+template <typename T, int NF>
+__device__ __forceinline__ void st_out(T* p, const T* v) {
+  if (NF == 2) {
+    if (sizeof(T) == 4)
+      *reinterpret_cast<float2*>(p) = make_float2((float)v[0], (float)v[1]);
+    else
+      *reinterpret_cast<double2*>(p) = make_double2((double)v[0], (double)v[1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) p[i] = v[i];
+  }
+}
+template <typename T, int NF>
+__device__ __forceinline__ void add_out(const T* p, T* acc) {
+  if (NF == 2) {
+    if (sizeof(T) == 4) {
+      const float2 q = *reinterpret_cast<const float2*>(p);
+      acc[0] += (T)q.x;
+      acc[1] += (T)q.y;
+    } else {
+      const double2 q = *reinterpret_cast<const double2*>(p);
+      acc[0] += (T)q.x;
+      acc[1] += (T)q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) acc[i] += p[i];
+  }
+}
+
 template <typename T, int MODEL, int OPS>
-__global__ void __launch_bounds__(kTileTets)
+__global__ void __launch_bounds__(kTileTets, sizeof(T) == 4 ? 5 : 2)
 tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, BlobLayout L,
                 const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err) {
   using Z = TileSmem<T, OPS>;
-  constexpr int S = Z::S, TT = Z::TT, NO = Z::NO;
+  constexpr int TT = Z::TT, NF = Z::NF;
   extern __shared__ __align__(128) unsigned char smem[];
-  T* slotv = reinterpret_cast<T*>(smem + 2 * (size_t)L.bytes);
+  unsigned char* ring = smem;
+  T* slotv = reinterpret_cast<T*>(smem + Z::ring_bytes);
   T* so = slotv + 2 * Z::slot_elems;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(so + NO * 4 * TT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(so + 2 * Z::out_elems);
+  T* out_field[3];
+  {
+    int f = 0;
+    if (Z::FO) out_field[f++] = io.f;
+    if (Z::KV) out_field[f++] = io.Kw;
+    if (Z::DG) out_field[f++] = io.d;
+  }
 
   if (active != nullptr && *active == 0) return;
   const int tid = threadIdx.x;
@@ -215,30 +305,46 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
   int tile = blockIdx.x;
   if (tile >= ntiles) return;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+#pragma unroll
+    for (int r = 0; r < kRing; ++r) mbar_init(&bar[r], 1);
     fence_mbar_init();
   }
-  __syncthreads();
-  // Per-buffer state, kept in scalars (no local-memory arrays).
-  bool pend0 = true, pend1 = tile + G < ntiles;
-  unsigned par0 = 0u, par1 = 0u;
-  if (tid == 0) {
-    bulk_load(smem, blobs + (size_t)tile * L.bytes, L.bytes, &bar[0]);
-    if (pend1) bulk_load(smem + L.bytes, blobs + (size_t)(tile + G) * L.bytes, L.bytes, &bar[1]);
+  // Zero rows (tet index TT) read by padded reduction entries.
+  for (int i = tid; i < 2 * 12 * NF; i += TT) {
+    const int buf = i / (12 * NF), ac = (i / NF) % 12, f = i % NF;
+    so[buf * Z::out_elems + ((size_t)ac * (TT + 1) + TT) * NF + f] = T(0);
   }
-  bool bad = !mbar_wait(&bar[0], par0, kWaitCycles);
-  if (__syncthreads_or(bad)) goto drain;
-  pend0 = false;
-  par0 ^= 1u;
-  {
-    const int4 h = *reinterpret_cast<const int4*>(smem);
-    if (tid < h.y) {
-      const int v = reinterpret_cast<const int*>(smem + kBlobVtx)[tid];
+  __syncthreads();
+  // Ring state, identical in every thread unless a wait times out: bit r of
+  // `pend` = a copy into ring slot r is in flight; bit r of `parity` = the
+  // phase parity to wait for next.
+  unsigned pend = 0u, parity = 0u;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        slotv[c * S + tid] = io.u[(size_t)c * nv + v];
-        if (Z::KV) slotv[(3 + c) * S + tid] = io.w[(size_t)c * nv + v];
+  for (int r = 0; r < kRing - 1; ++r) {
+    const int t = tile + r * G;
+    if (t < ntiles) {
+      if (tid == 0) bulk_load(ring + r * kBlobPrefix, blobs + (size_t)t * L.bytes, kBlobPrefix, &bar[r]);
+      pend |= 1u << r;
+    }
+  }
+  TetRegs<T> tr;
+  load_tet_regs(blobs + (size_t)tile * L.bytes, L, tid, mu0, lam0, tr);
+  bool bad = !mbar_wait(&bar[0], 0u, kWaitCycles);
+  if (__syncthreads_or(bad)) goto drain;
+  pend &= ~1u;
+  parity ^= 1u;
+  {
+    const int4 h = *reinterpret_cast<const int4*>(ring);
+    for (int j = tid; j < h.y; j += TT) {
+      const int v = reinterpret_cast<const int*>(ring + kBlobVtx)[j];
+      T x[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) x[c] = io.u[(size_t)c * nv + v];
+      st3(slotv + 4 * j, x);
+      if (Z::KV) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[c] = io.w[(size_t)c * nv + v];
+        st3(slotv + 4 * (Z::S + j), x);
       }
     }
   }
@@ -246,28 +352,33 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
 
   for (int k = 0;; ++k) {
     const int b = k & 1;
+    const int rc = k % kRing, rn = (k + 1) % kRing;
+    const unsigned char* pre = ring + rc * kBlobPrefix;
+    const unsigned char* pren = ring + rn * kBlobPrefix;
     const T* su = slotv + (b ? Z::slot_elems : 0);
-    const T* sw = su + 3 * S;
+    const T* sw = su + 4 * Z::S;
     T* su_next = slotv + (b ? 0 : Z::slot_elems);
-    unsigned char* cur = b ? smem + L.bytes : smem;
-    unsigned char* nxt = b ? smem : smem + L.bytes;
+    T* sob = so + (b ? Z::out_elems : 0);
     const int next = tile + G;
-    // Next tile: wait for its blob, start loading its vertex values.
+
+    // Next tile: wait for its prefix, start loading its vertex values.  No
+    // barrier here: a thread whose wait timed out skips the loads that depend
+    // on the copy and reports at the tile's barrier below.
     T pu[3], pw[3];
+    TetRegs<T> tn;
     int nvu_next = 0;
+    bad = false;
     if (next < ntiles) {
-      bad = !mbar_wait(&bar[b ^ 1], b ? par0 : par1, kWaitCycles);
-      if (__syncthreads_or(bad)) goto drain;
-      if (b) {
-        pend0 = false;
-        par0 ^= 1u;
+      load_tet_regs(blobs + (size_t)next * L.bytes, L, tid, mu0, lam0, tn);
+      if (mbar_wait(&bar[rn], (parity >> rn) & 1u, kWaitCycles)) {
+        pend &= ~(1u << rn);
+        parity ^= 1u << rn;
+        nvu_next = reinterpret_cast<const int4*>(pren)->y;
       } else {
-        pend1 = false;
-        par1 ^= 1u;
+        bad = true;
       }
-      nvu_next = reinterpret_cast<const int4*>(nxt)->y;
       if (tid < nvu_next) {
-        const int v = reinterpret_cast<const int*>(nxt + kBlobVtx)[tid];
+        const int v = reinterpret_cast<const int*>(pren + kBlobVtx)[tid];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           pu[c] = io.u[(size_t)c * nv + v];
@@ -275,101 +386,103 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
         }
       }
     }
-    const int4 h = *reinterpret_cast<const int4*>(cur);
+    const int4 h = *reinterpret_cast<const int4*>(pre);
 
     // Phase 1: one tet per thread.
     if (tid < h.x) {
-      const uchar4 sl4 = reinterpret_cast<const uchar4*>(cur + kBlobSlots)[tid];
+      const uchar4 sl4 = reinterpret_cast<const uchar4*>(pre + kBlobSlots)[tid];
       const int sl[4] = {sl4.x, sl4.y, sl4.z, sl4.w};
-      const T* Bs = reinterpret_cast<const T*>(cur + L.B);
-      T B[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) B[i] = Bs[i * TT + tid];
-      const T V = reinterpret_cast<const T*>(cur + L.V)[tid];
-      const T mu = L.mu >= 0 ? reinterpret_cast<const T*>(cur + L.mu)[tid] : mu0;
-      const T lam = L.lam >= 0 ? reinterpret_cast<const T*>(cur + L.lam)[tid] : lam0;
       T Du[9], Dw[9];
+      {
+        T x0[3], xa[3];
+        ld3(su + 4 * sl[0], x0);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T u0 = su[c * S + sl[0]];
+        for (int j = 0; j < 3; ++j) {
+          ld3(su + 4 * sl[j + 1], xa);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Du[c * 3 + j] = su[c * S + sl[j + 1]] - u0;
+          for (int c = 0; c < 3; ++c) Du[c * 3 + j] = xa[c] - x0[c];
+        }
         if (Z::KV) {
-          const T w0 = sw[c * S + sl[0]];
+          ld3(sw + 4 * sl[0], x0);
 #pragma unroll
-          for (int j = 0; j < 3; ++j) Dw[c * 3 + j] = sw[c * S + sl[j + 1]] - w0;
+          for (int j = 0; j < 3; ++j) {
+            ld3(sw + 4 * sl[j + 1], xa);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Dw[c * 3 + j] = xa[c] - x0[c];
+          }
         }
       }
       T fo[4][3], ko[4][3], dgo[4][3];
-      const bool ok = element_eval<T, MODEL, OPS>(B, V, mu, lam, Du, Dw, fo, ko, dgo);
+      const bool ok = element_eval<T, MODEL, OPS>(tr.B, tr.V, tr.mu, tr.lam, Du, Dw, fo, ko, dgo);
       if (!ok) raise_error(err, EBB_ERR_INVERTED, perm[h.z + tid]);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          int o = 0;
-          if (Z::FO) so[((o + c) * 4 + a) * TT + tid] = ok ? fo[a][c] : T(0);
-          if (Z::FO) o += 3;
-          if (Z::KV) so[((o + c) * 4 + a) * TT + tid] = ok ? ko[a][c] : T(0);
-          if (Z::KV) o += 3;
-          if (Z::DG) so[((o + c) * 4 + a) * TT + tid] = ok ? dgo[a][c] : T(0);
+          T v[NF > 0 ? NF : 1];
+          int f = 0;
+          if (Z::FO) v[f++] = ok ? fo[a][c] : T(0);
+          if (Z::KV) v[f++] = ok ? ko[a][c] : T(0);
+          if (Z::DG) v[f++] = ok ? dgo[a][c] : T(0);
+          st_out<T, NF>(sob + ((size_t)(a * 3 + c) * (TT + 1) + tid) * NF, v);
         }
       }
     }
     if (tid < nvu_next) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        su_next[c * S + tid] = pu[c];
-        if (Z::KV) su_next[(3 + c) * S + tid] = pw[c];
-      }
+      st3(su_next + 4 * tid, pu);
+      if (Z::KV) st3(su_next + 4 * (Z::S + tid), pw);
     }
-    __syncthreads();
+    if (__syncthreads_or(bad)) goto drain;
 
-    // Phase 2: one distinct vertex per thread.
-    if (tid < h.y) {
-      const unsigned short* eoff = reinterpret_cast<const unsigned short*>(cur + kBlobEoff);
-      const unsigned short* ent = reinterpret_cast<const unsigned short*>(cur + kBlobEnt);
-      const int e0 = eoff[tid] & 0x7fff, e1 = eoff[tid + 1] & 0x7fff;
-      T acc[NO];
-#pragma unroll
-      for (int o = 0; o < NO; ++o) acc[o] = T(0);
-      for (int e = e0; e < e1; ++e) {
-        const int code = ent[e];
-        const int idx = (code >> 8) * TT + (code & 255);
-#pragma unroll
-        for (int o = 0; o < NO; ++o) acc[o] += so[o * 4 * TT + idx];
-      }
-      const int v = reinterpret_cast<const int*>(cur + kBlobVtx)[tid];
-#pragma unroll
-      for (int o = 0; o < NO; ++o) {
-        T* field;
-        int c;
-        if (Z::FO && o < 3) {
-          field = io.f;
-          c = o;
-        } else if (Z::KV && o < (Z::FO ? 6 : 3)) {
-          field = io.Kw;
-          c = o - (Z::FO ? 3 : 0);
-        } else {
-          field = io.d;
-          c = o - (Z::FO ? 3 : 0) - (Z::KV ? 3 : 0);
+    // Ring slot of tile k-1 is free (its phase 2 finished before the barrier):
+    // refill it with the tile kRing-1 ahead.
+    {
+      const int tf = tile + (kRing - 1) * G;
+      if (tf < ntiles) {
+        const int rf = (k + kRing - 1) % kRing;
+        if (tid == 0) {
+          fence_proxy_async_smem();
+          bulk_load(ring + rf * kBlobPrefix, blobs + (size_t)tf * L.bytes, kBlobPrefix, &bar[rf]);
         }
-        atomicAdd(field + (size_t)c * nv + v, acc[o]);
+        pend |= 1u << rf;
       }
     }
-    __syncthreads();
 
-    // The current buffer is free: refill it with the tile after next.
-    if (next + G < ntiles) {
-      if (tid == 0) {
-        fence_proxy_async_smem();
-        bulk_load(cur, blobs + (size_t)(next + G) * L.bytes, L.bytes, &bar[b]);
+    // Phase 2: one reduction unit per thread: kUnitEntries independent loads.
+    {
+      const uint32_t d = reinterpret_cast<const uint32_t*>(pre + kBlobUnits)[tid];
+      const unsigned rem = (d >> 22) & 0xfu;
+      T acc[3 * NF];
+#pragma unroll
+      for (int o = 0; o < 3 * NF; ++o) acc[o] = T(0);
+      if (d & 1u) {
+        const uint4 codes = reinterpret_cast<const uint4*>(pre + kBlobEnt)[tid];
+        const unsigned cw[4] = {codes.x, codes.y, codes.z, codes.w};
+#pragma unroll
+        for (int q = 0; q < kUnitEntries; ++q) {
+          const unsigned code = (cw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+          const int base = (int)(code >> 8) * 3 * (TT + 1) + (int)(code & 255u);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) add_out<T, NF>(sob + ((size_t)base + c * (TT + 1)) * NF, acc + c * NF);
+        }
       }
-      if (b)
-        pend1 = true;
-      else
-        pend0 = true;
+      const unsigned maxrem = __reduce_max_sync(0xffffffffu, rem);
+      for (unsigned st = 1; st <= maxrem; st <<= 1) {
+#pragma unroll
+        for (int o = 0; o < 3 * NF; ++o) {
+          const T x = __shfl_down_sync(0xffffffffu, acc[o], st);
+          if (rem >= st) acc[o] += x;
+        }
+      }
+      if ((d >> 26) & 1u) {
+        const int v = reinterpret_cast<const int*>(pre + kBlobVtx)[(d >> 14) & 0xffu];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int f = 0; f < NF; ++f) atomicAdd(out_field[f] + (size_t)c * nv + v, acc[c * NF + f]);
+      }
     }
+    tr = tn;
     if (next >= ntiles) break;
     tile = next;
   }
@@ -379,8 +492,9 @@ drain:
   // A copy did not complete in time: report it and wait (bounded) for the
   // copies still in flight before the CTA's shared memory goes away.
   if (tid == 0) raise_error(err, EBB_ERR_TIMEOUT, blockIdx.x);
-  if (pend0) mbar_wait(&bar[0], par0, kWaitCycles);
-  if (pend1) mbar_wait(&bar[1], par1, kWaitCycles);
+#pragma unroll
+  for (int r = 0; r < kRing; ++r)
+    if ((pend >> r) & 1u) mbar_wait(&bar[r], (parity >> r) & 1u, kWaitCycles);
 }
 
 template <typename T, int MODEL, int OPS>
@@ -442,7 +556,7 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
   const Tiles& tl = rel->tiles;
   if (tl.ntiles == 0) return cudaSuccess;
   const BlobLayout& L = layout_of<T>(tl);
-  const size_t smem = TileSmem<T, OPS>::bytes(L);
+  const size_t smem = TileSmem<T, OPS>::bytes;
   using Cfg = TileLaunchCfg<T, MODEL, OPS>;
   if (Cfg::smem != smem) {
     int per_sm = 0;
