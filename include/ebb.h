@@ -229,6 +229,42 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                   const ebb_step_params_t* params,
                                   ebb_cg_report_t* report);
 
+/* ---- implicit step without device allocation ---------------------------- */
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory -- code running where cudaMalloc is not
+ * allowed or not wanted (a host framework that owns every device byte and
+ * hands out fixed arenas, real-time loops that must not hit the allocator, or
+ * contexts created before any allocator is set up).  Contexts, relations and
+ * finalize all allocate, so this call takes plain device arrays instead:
+ *   keys    I32, 4 planes of n_tets (tets.v[4]; each key in [0, n_verts))
+ *   X       F64, 3 planes of n_verts: rest positions
+ *   u, v    F64, 3 planes of n_verts: displacement and velocity, updated in
+ *           place exactly as ebb_cg_implicit_step updates them
+ *   pinned  U8, n_verts (nonzero = pinned), or NULL
+ * on the current CUDA device, enqueued on `cuda_stream` (NULL = legacy
+ * default stream); the call is synchronous.  Only params->precision ==
+ * EBB_PREC_F64 and uniform material (params->mu, params->lambda) are
+ * supported, and the scatter is always the atomic one.
+ * Its working memory is one fixed array in the library's device image
+ * (about 2.8 MB, held on every device that loads the library until the
+ * process exits), so sizes are capped: n_verts <=
+ * EBB_NOALLOC_MAX_VERTS and n_tets <= EBB_NOALLOC_MAX_TETS, else EBB_ERR_ARG
+ * before any work is enqueued.  The call neither allocates nor frees device
+ * memory.  The first call on a device looks up the array's device address
+ * (make it before any stream capture).  Every call reuses the same array, so
+ * two calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and corrupt each other; the call clears what must start at zero.
+ * Errors: EBB_ERR_ARG, EBB_ERR_KEY, EBB_ERR_INVERTED, EBB_ERR_CG_BREAKDOWN,
+ * EBB_ERR_NOT_CONVERGED (if requested), EBB_ERR_CUDA.  There is no context,
+ * so no message: only the status code. */
+#define EBB_NOALLOC_MAX_VERTS 4096
+#define EBB_NOALLOC_MAX_TETS 24576
+ebb_status_t ebb_cg_implicit_step_noalloc(void* cuda_stream, int32_t n_verts, int32_t n_tets,
+                                          const int32_t* keys, const double* X, double* u,
+                                          double* v, const uint8_t* pinned,
+                                          const ebb_step_params_t* params,
+                                          ebb_cg_report_t* report);
+
 #ifdef __cplusplus
 }
 #endif

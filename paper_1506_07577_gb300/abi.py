@@ -41,6 +41,8 @@ EBB_PREC_F64, EBB_PREC_F32 = 0, 1
 EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED = 0, 1, 2, 3
 EBB_FINALIZE_COLOR = 1
 EBB_MAP_ZERO_OUT = 1
+EBB_NOALLOC_MAX_VERTS = 4096
+EBB_NOALLOC_MAX_TETS = 24576
 
 ebb_ctx_t = C.c_void_p
 ebb_rel_t = C.c_void_p
@@ -79,6 +81,9 @@ _SIGS = {
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
+    "ebb_cg_implicit_step_noalloc": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.POINTER(ebb_step_params_t),
+                                      C.POINTER(ebb_cg_report_t)], ebb_status_t),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -193,4 +198,19 @@ def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), prec
 def ebb_cg_implicit_step(ctx, tets, u, v, pinned, params):
     rep = ebb_cg_report_t()
     _check(ctx, _lib.ebb_cg_implicit_step(ctx, tets, _b(u), _b(v), _b(pinned), C.byref(params), C.byref(rep)))
+    return rep
+
+
+def ebb_cg_implicit_step_noalloc(stream, n_verts, n_tets, keys, X, u, v, pinned, params):
+    """The allocation-free implicit step.  ``keys`` (4, n_tets) int32, ``X``,
+    ``u``, ``v`` (3, n_verts) float64 and ``pinned`` (n_verts,) uint8 or None
+    are CUDA tensors; u and v are updated in place.  Raises EbbError on a
+    non-zero status (this call has no context, so no message)."""
+    def ptr(t):
+        return None if t is None else C.c_void_p(t.data_ptr())
+    rep = ebb_cg_report_t()
+    st = _lib.ebb_cg_implicit_step_noalloc(_stream_handle(stream), int(n_verts), int(n_tets), ptr(keys), ptr(X),
+                                           ptr(u), ptr(v), ptr(pinned), C.byref(params), C.byref(rep))
+    if st != EBB_OK:
+        raise EbbError(st, "ebb_cg_implicit_step_noalloc failed")
     return rep
