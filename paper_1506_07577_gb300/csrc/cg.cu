@@ -10,9 +10,9 @@
 //
 // Global reductions (dot products) follow the two-pass scheme of Section 6.2
 // "Reductions": the first pass is fused into the kernel producing the values
-// (per-block partial sums), the second pass runs at the start of the kernel
-// that consumes the scalar -- every block re-reduces the partials in the same
-// order, so all blocks see the same bits and the result is deterministic.
+// (per-block partial sums); the second pass is done by the last block of the
+// same kernel to finish, which sums the partials in block order (so the
+// result is deterministic) and updates the CG scalars on the device.
 // Scalars never leave the device inside the loop; the host reads one status
 // word per batch of iterations.  CG vectors, dots and updates are FP64 in
 // both precisions; the element maps run in the element precision T.
@@ -28,16 +28,20 @@ namespace ebb {
 namespace {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecBlocks = 304;   // 2 blocks per SM on a 152-SM GB300
-constexpr int kChunk = 8;         // CG iterations launched between host status reads (even)
+constexpr int kVecBlocks = 4 * 152;   // 4 blocks per SM on a 152-SM GB300
+constexpr int kChunk = 8;             // CG iterations launched between host status reads (even)
 
+// Device-side CG state.  `count` are the arrival counters of the three
+// reduction sites (init, p.Ap, r.z); the last block of a kernel resets its own.
 struct CgScalars {
   double rz[2];      // r.z, indexed by iteration parity
   double rr;         // r.r after the last update
   double bb;         // b.b
+  double alpha, beta;
   int active[2];     // iteration with parity s runs iff active[s]
   int iter;          // iterations completed
   int status;        // EBB_OK or EBB_ERR_CG_BREAKDOWN
+  unsigned count[3];
 };
 
 template <typename PT>
@@ -71,23 +75,38 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __syncthreads();
 }
 
-// Second pass: sum kVecBlocks partial pairs in a fixed order; every thread of
-// the block gets the result.
-__device__ __forceinline__ void reduce_partials(const double* part, double& a, double& b) {
+// Two-pass global sum of (a, b) (Section 6.2 "Reductions"): every block
+// writes its partial; the last block to arrive sums all partials in block
+// order -- the same order every time, so the result is deterministic -- and
+// returns true with the totals in (a, b) for all of its threads.
+__device__ __forceinline__ bool reduce_last(double& a, double& b, double* part, unsigned* counter) {
+  __shared__ unsigned s_last;
   __shared__ double ra, rb;
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+    __threadfence();
+    s_last = atomicAdd(counter, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
   double x = 0.0, y = 0.0;
-  for (int i = threadIdx.x; i < kVecBlocks; i += kVecThreads) {
-    x += part[2 * i];
-    y += part[2 * i + 1];
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kVecThreads) {
+    x += __ldcg(part + 2 * i);
+    y += __ldcg(part + 2 * i + 1);
   }
   block_sum2(x, y);
   if (threadIdx.x == 0) {
     ra = x;
     rb = y;
+    *counter = 0u;
   }
   __syncthreads();
   a = ra;
   b = rb;
+  return true;
 }
 
 // u32 = u, w32 = v (mixed precision), accumulators zeroed.
@@ -127,14 +146,15 @@ struct StepConst {
 };
 
 // b = dt (f + m g - dt K v) (0 on pinned rows); r = b; z = r / diag(A);
-// p = z; y = 0.  Partials: (r.z, r.r).
+// p = z; y = 0; then r.z and r.r, and the CG state for iteration 0.
 template <typename T, typename PT>
 __global__ void __launch_bounds__(kVecThreads)
 cg_init_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict__ mass,
                const T* __restrict__ acc_f, const T* __restrict__ acc_kv, const T* __restrict__ acc_d,
-               double* r, double* p, double* y, double* dinv, T* pe, double* part) {
+               double* r, double* p, double* y, double* dinv, T* pe, double* part, CgScalars* sc) {
   const int n = 3 * c.nv;
   double rz = 0.0, rr = 0.0;
+#pragma unroll 4
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
     const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
     const int vtx = i - comp * c.nv;
@@ -153,21 +173,12 @@ cg_init_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict
     rz += b * z;
     rr += b * b;
   }
-  block_sum2(rz, rr);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = rz;
-    part[2 * blockIdx.x + 1] = rr;
-  }
-}
-
-__global__ void __launch_bounds__(kVecThreads) cg_start_kernel(StepConst c, const double* part, CgScalars* sc) {
-  double rz, rr;
-  reduce_partials(part, rz, rr);
-  if (threadIdx.x == 0) {
+  if (reduce_last(rz, rr, part, &sc->count[0]) && threadIdx.x == 0) {
     sc->rz[0] = rz;
     sc->rz[1] = 0.0;
     sc->rr = rr;
     sc->bb = rr;
+    sc->alpha = sc->beta = 0.0;
     sc->iter = 0;
     sc->status = EBB_OK;
     sc->active[0] = (c.max_iters > 0 && sqrt(rr) > c.rtol * sqrt(rr)) ? 1 : 0;
@@ -175,15 +186,16 @@ __global__ void __launch_bounds__(kVecThreads) cg_start_kernel(StepConst c, cons
   }
 }
 
-// q = A p on free rows; partial p.q.
+// p.Ap over free rows (Ap = M p + dt^2 K p); alpha = r.z / p.Ap.
 template <typename T, typename PT>
 __global__ void __launch_bounds__(kVecThreads)
 cg_pq_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
-             const double* __restrict__ p, const T* __restrict__ acc_kp, const CgScalars* sc, double* part) {
+             const double* __restrict__ p, const T* __restrict__ acc_kp, double* part, CgScalars* sc) {
   if (!sc->active[s]) return;
   const int n = 3 * c.nv;
   const double dt2 = c.dt * c.dt;
   double pq = 0.0, zero = 0.0;
+#pragma unroll 4
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
     const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
     const int vtx = i - comp * c.nv;
@@ -191,30 +203,29 @@ cg_pq_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __res
     const double pi = p[i];
     pq += pi * (mass[vtx] * pi + dt2 * (double)acc_kp[i]);
   }
-  block_sum2(pq, zero);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = pq;
-    part[2 * blockIdx.x + 1] = 0.0;
+  if (reduce_last(pq, zero, part, &sc->count[1]) && threadIdx.x == 0) {
+    if (pq > 0.0) {
+      sc->alpha = sc->rz[s] / pq;
+    } else {
+      sc->alpha = 0.0;
+      sc->status = EBB_ERR_CG_BREAKDOWN;
+    }
   }
 }
 
-// alpha = rz / pq; y += alpha p; r -= alpha q; partials (r.z, r.r).
+// y += alpha p; r -= alpha Ap; then r.z and r.r, beta, and whether the next
+// iteration runs.
 template <typename T, typename PT>
 __global__ void __launch_bounds__(kVecThreads)
 cg_update_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
                  const double* __restrict__ p, const T* __restrict__ acc_kp, const double* __restrict__ dinv,
-                 double* r, double* y, CgScalars* sc, const double* part_in, double* part_out) {
-  if (!sc->active[s]) return;
-  double pq, unused;
-  reduce_partials(part_in, pq, unused);
-  if (!(pq > 0.0)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->status = EBB_ERR_CG_BREAKDOWN;
-    return;
-  }
-  const double alpha = sc->rz[s] / pq;
+                 double* r, double* y, double* part, CgScalars* sc) {
+  if (!sc->active[s] || sc->status != EBB_OK) return;
+  const double alpha = sc->alpha;
   const int n = 3 * c.nv;
   const double dt2 = c.dt * c.dt;
   double rz = 0.0, rr = 0.0;
+#pragma unroll 4
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
     const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
     const int vtx = i - comp * c.nv;
@@ -224,44 +235,37 @@ cg_update_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* _
     y[i] += alpha * pi;
     const double ri = r[i] - alpha * q;
     r[i] = ri;
-    const double z = ri * dinv[i];
-    rz += ri * z;
+    rz += ri * (ri * dinv[i]);
     rr += ri * ri;
   }
-  block_sum2(rz, rr);
-  if (threadIdx.x == 0) {
-    part_out[2 * blockIdx.x] = rz;
-    part_out[2 * blockIdx.x + 1] = rr;
+  if (reduce_last(rz, rr, part, &sc->count[2]) && threadIdx.x == 0) {
+    const int it = sc->iter + 1;
+    sc->iter = it;
+    sc->beta = rz / sc->rz[s];
+    sc->rz[s ^ 1] = rz;
+    sc->rr = rr;
+    sc->active[s ^ 1] = (it < c.max_iters && sqrt(rr) > c.rtol * sqrt(sc->bb)) ? 1 : 0;
   }
 }
 
-// beta = rz_new / rz; p = z + beta p; clear the K p accumulator; decide
-// whether the next iteration runs.
+// p = z + beta p (z = r / diag A); clear the K p accumulator.  Propagates
+// "inactive" to the next parity when this iteration did not run.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads)
 cg_pupdate_kernel(StepConst c, int s, const double* __restrict__ r, const double* __restrict__ dinv, double* p,
-                  T* pe, T* acc_kp, CgScalars* sc, const double* part) {
-  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+                  T* pe, T* acc_kp, CgScalars* sc) {
   if (!sc->active[s] || sc->status != EBB_OK) {
-    if (lead) sc->active[s ^ 1] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->active[s ^ 1] = 0;
     return;
   }
-  double rz_new, rr;
-  reduce_partials(part, rz_new, rr);
-  const double beta = rz_new / sc->rz[s];
+  const double beta = sc->beta;
   const int n = 3 * c.nv;
+#pragma unroll 4
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
     const double pi = r[i] * dinv[i] + beta * p[i];
     p[i] = pi;
     if (pe) pe[i] = (T)pi;
     acc_kp[i] = T(0);
-  }
-  if (lead) {
-    const int it = sc->iter + 1;
-    sc->iter = it;
-    sc->rz[s ^ 1] = rz_new;
-    sc->rr = rr;
-    sc->active[s ^ 1] = (it < c.max_iters && sqrt(rr) > c.rtol * sqrt(sc->bb)) ? 1 : 0;
   }
 }
 
@@ -396,6 +400,9 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   c.max_iters = prm->max_iters;
 
   const int vgrid = 4 * 152;
+  // Arrival counters of the last-block reductions start at zero.
+  e = cudaMemsetAsync(s->sc, 0, sizeof(CgScalars), st);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "CG state reset");
   step_prep_kernel<T><<<vgrid, 256, 0, st>>>(n, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "step prep");
@@ -413,8 +420,7 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   double* part_a = s->part;
   double* part_b = s->part + 2 * kVecBlocks;
   cg_init_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, pin, s->mass, acc_f, acc_kv, acc_d, s->r, s->p,
-                                                             s->y, s->dinv, mixed ? pe : nullptr, part_a);
-  cg_start_kernel<<<1, kVecThreads, 0, st>>>(c, part_a, s->sc);
+                                                             s->y, s->dinv, mixed ? pe : nullptr, part_a, s->sc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "CG init");
 
@@ -446,11 +452,11 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
     for (int k = 0; k < kChunk && le == cudaSuccess; ++k) {
       const int par = k & 1;
       le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
-      cg_pq_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->sc, part_a);
+      cg_pq_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, part_a, s->sc);
       cg_update_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->dinv,
-                                                                   s->r, s->y, s->sc, part_a, part_b);
+                                                                   s->r, s->y, part_b, s->sc);
       cg_pupdate_kernel<T><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, s->r, s->dinv, s->p, mixed ? pe : nullptr,
-                                                               acc_kp, s->sc, part_b);
+                                                               acc_kp, s->sc);
       if (le == cudaSuccess) le = cudaGetLastError();
     }
     if (le == cudaSuccess) le = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
