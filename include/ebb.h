@@ -229,6 +229,25 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                   const ebb_step_params_t* params,
                                   ebb_cg_report_t* report);
 
+/* Batched form: one implicit step for each of many independent meshes
+ * stored in one verts/tets relation pair (the batched meshes of the
+ * spec workload list; the per-mesh step is exactly the one above).
+ * `batch` names an I32 one-component vertex field giving each vertex its mesh
+ * id in [0, nbatch); ids must be non-decreasing along verts (each mesh's
+ * vertices contiguous) and every id must occur.  Bind the field as
+ * "batch" before ebb_relation_finalize so tets are ordered mesh by mesh and
+ * a tet joining two meshes is rejected (EBB_ERR_KEY).  Every element map
+ * runs as one launch over all meshes; CG scalars, convergence and iteration
+ * counts are per mesh (a converged mesh stops updating while others go on).
+ * `pinned` must be a U8 field or NULL.  reports (may be NULL) receives nbatch
+ * entries.  Synchronous.  Returns the first failing mesh's status (its
+ * message names the mesh), else EBB_OK. */
+ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                          const char* v, const char* pinned,
+                                          const char* batch, int32_t nbatch,
+                                          const ebb_step_params_t* params,
+                                          ebb_cg_report_t* reports);
+
 /* ---- implicit step without device allocation ---------------------------- */
 /* The paper has no counterpart to this call; it exists for callers that
  * cannot allocate device memory -- code running where cudaMalloc is not

@@ -209,6 +209,49 @@ def batched_sizes(count: int, n_lo: int, n_hi: int, seed: int) -> np.ndarray:
     return np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(np.int64)
 
 
+@dataclasses.dataclass
+class MeshBatch:
+    """Independent meshes concatenated into one vertex / tet relation pair.
+
+    X, tets, pinned : as in TetMesh, for all meshes (tets offset per mesh)
+    batch           : (N_v,) int32 mesh id of each vertex (non-decreasing)
+    sides           : cube count per side of each mesh
+    vert_off, tet_off : (count+1,) row offsets of each mesh
+    """
+    X: np.ndarray
+    tets: np.ndarray
+    pinned: np.ndarray
+    batch: np.ndarray
+    sides: np.ndarray
+    vert_off: np.ndarray
+    tet_off: np.ndarray
+
+    def mesh(self, m):
+        """(X, tets, pinned) of mesh m alone, keys rebased to its vertices."""
+        a, b = self.vert_off[m], self.vert_off[m + 1]
+        ta, tb = self.tet_off[m], self.tet_off[m + 1]
+        return self.X[a:b], self.tets[ta:tb] - a, self.pinned[a:b]
+
+
+def cube_grid_batch(sides, jitter: float = 0.01, seed: int = 0) -> MeshBatch:
+    """Concatenate one cube grid per entry of ``sides`` (mesh m jittered
+    with seed ``seed + m``)."""
+    Xs, Ts, Ps, Bs = [], [], [], []
+    voff, toff = [0], [0]
+    for m, n in enumerate(sides):
+        g = cube_grid(int(n), jitter=jitter, seed=seed + m)
+        Ts.append(g.tets.astype(np.int64) + voff[-1])
+        Xs.append(g.X)
+        Ps.append(g.pinned)
+        Bs.append(np.full(g.n_verts, m, dtype=np.int32))
+        voff.append(voff[-1] + g.n_verts)
+        toff.append(toff[-1] + g.n_tets)
+    return MeshBatch(X=np.ascontiguousarray(np.concatenate(Xs)),
+                     tets=np.ascontiguousarray(np.concatenate(Ts).astype(np.int32)),
+                     pinned=np.concatenate(Ps), batch=np.concatenate(Bs), sides=np.asarray(sides),
+                     vert_off=np.asarray(voff), tet_off=np.asarray(toff))
+
+
 # Workload recipes.  They stand in for the paper's FEM workloads (Section 7.2,
 # Vega: StVK, implicit backward Euler, Jacobi PCG on tet meshes; Section 7.3,
 # FreeFem++: neo-Hookean, implicit CG), whose meshes are not available: cube

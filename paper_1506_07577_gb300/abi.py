@@ -81,6 +81,8 @@ _SIGS = {
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
+    "ebb_cg_implicit_step_batched": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.c_int32,
+                                      C.POINTER(ebb_step_params_t), C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_noalloc": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.POINTER(ebb_step_params_t),
                                       C.POINTER(ebb_cg_report_t)], ebb_status_t),
@@ -199,6 +201,14 @@ def ebb_cg_implicit_step(ctx, tets, u, v, pinned, params):
     rep = ebb_cg_report_t()
     _check(ctx, _lib.ebb_cg_implicit_step(ctx, tets, _b(u), _b(v), _b(pinned), C.byref(params), C.byref(rep)))
     return rep
+
+
+def ebb_cg_implicit_step_batched(ctx, tets, u, v, pinned, batch, nbatch, params):
+    """One implicit step per mesh of a batch; returns the list of reports."""
+    reps = (ebb_cg_report_t * int(nbatch))()
+    _check(ctx, _lib.ebb_cg_implicit_step_batched(ctx, tets, _b(u), _b(v), _b(pinned), _b(batch), int(nbatch),
+                                                  C.byref(params), reps))
+    return list(reps)
 
 
 def ebb_cg_implicit_step_noalloc(stream, n_verts, n_tets, keys, X, u, v, pinned, params):

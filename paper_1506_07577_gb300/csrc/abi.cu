@@ -113,6 +113,7 @@ void free_tet_data(ebb_rel_s* r) {
   free_colouring(r);
   free_layout(r);
   free_step_scratch(r);
+  free_batch_scratch(r);
   r->finalized = false;
 }
 
@@ -359,7 +360,7 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     std::vector<int> perm;
     std::vector<unsigned char> prefix;
     ebb_status_t ls =
-        build_layout(ctx, tets, none, std::vector<double>((size_t)3 * nv, 0.0), perm, sorted, prefix);
+        build_layout(ctx, tets, none, std::vector<double>((size_t)3 * nv, 0.0), nullptr, perm, sorted, prefix);
     if (ls) return ls;
     tets->finalized = true;
     return EBB_OK;
@@ -402,10 +403,32 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   if (s) return s;
   s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "copying rest positions");
   if (s) return s;
+  // Optional per-vertex group ids ("batch", I32): tets are then ordered by
+  // group first, and a tet may not join vertices of two groups.
+  std::vector<int> hbatch;
+  if (const Field* fb = find_field(verts, "batch")) {
+    if (fb->dtype != EBB_I32 || fb->ncomp != 1)
+      return set_error(ctx, EBB_ERR_ARG, "verts.batch must be I32 with 1 component");
+    hbatch.resize(nv);
+    s = cuda_check(ctx, cudaMemcpyAsync(hbatch.data(), fb->ptr, (size_t)nv * sizeof(int), cudaMemcpyDeviceToHost,
+                                        ctx->stream),
+                   "copying batch ids");
+    if (s) return s;
+    s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "copying batch ids");
+    if (s) return s;
+    for (int t = 0; t < nt; ++t) {
+      const int b = hbatch[packed[t].x];
+      if (b < 0 || hbatch[packed[t].y] != b || hbatch[packed[t].z] != b || hbatch[packed[t].w] != b) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "tet row %d joins vertices of different batches (or a negative batch id)", t);
+        return set_error(ctx, EBB_ERR_KEY, buf);
+      }
+    }
+  }
   std::vector<int> perm;
   std::vector<int4> sorted;
   std::vector<unsigned char> prefix;
-  s = build_layout(ctx, tets, packed, hX, perm, sorted, prefix);
+  s = build_layout(ctx, tets, packed, hX, hbatch.empty() ? nullptr : &hbatch, perm, sorted, prefix);
   if (s) return s;
   packed.swap(sorted);
 
@@ -548,6 +571,49 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
   ebb_step_params_t p = *params;
   p.reduce = reduce;
   return run_implicit_step(ctx, tets, (double*)pu, (double*)pv, pp, pdt, &p, report);
+}
+
+ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,
+                                          const char* pinned, const char* batch, int32_t nbatch,
+                                          const ebb_step_params_t* params, ebb_cg_report_t* reports) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (reports)
+    for (int32_t m = 0; m < nbatch; ++m) reports[m] = ebb_cg_report_t{0, 0.0, EBB_ERR_ARG};
+  if (!tets || !params || !u || !v || !batch || nbatch < 1) return set_error(ctx, EBB_ERR_ARG, "null argument");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (params->model != EBB_STVK && params->model != EBB_NEOHOOKEAN)
+    return set_error(ctx, EBB_ERR_ARG, "unknown material model");
+  if (params->precision != EBB_PREC_F64 && params->precision != EBB_PREC_F32)
+    return set_error(ctx, EBB_ERR_ARG, "unknown precision");
+  if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
+    return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
+  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
+  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+    return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
+  if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
+    return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
+  if (tets->verts->size == 0) return set_error(ctx, EBB_ERR_ARG, "empty vertex relation");
+  void *pu = nullptr, *pv = nullptr, *pb = nullptr;
+  ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
+  if (s) return s;
+  s = vertex_field(ctx, tets, v, EBB_F64, 3, &pv);
+  if (s) return s;
+  s = vertex_field(ctx, tets, batch, EBB_I32, 1, &pb);
+  if (s) return s;
+  const size_t bytes = (size_t)tets->verts->size * 3 * 8;
+  if (ranges_overlap(pu, bytes, pv, bytes)) return set_error(ctx, EBB_ERR_PHASE, "u and v overlap");
+  const void* pp = nullptr;
+  if (pinned) {
+    const Field* f = find_field(tets->verts, pinned);
+    if (!f || f->ncomp != 1 || f->dtype != EBB_U8)
+      return set_error(ctx, EBB_ERR_ARG, "pinned must name a U8 vertex field with 1 component");
+    pp = f->ptr;
+  }
+  ebb_step_params_t p = *params;
+  p.reduce = reduce;
+  return run_batched_step(ctx, tets, (double*)pu, (double*)pv, pp, (const int*)pb, nbatch, &p, reports);
 }
 
 }  // extern "C"

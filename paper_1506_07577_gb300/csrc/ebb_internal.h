@@ -95,7 +95,8 @@ struct VertexIndex {
   int* ent = nullptr;
 };
 
-struct StepScratch;  // defined in cg.cu
+struct StepScratch;   // defined in cg.cu
+struct BatchScratch;  // defined in batched.cu
 
 struct ebb_rel_impl;
 
@@ -130,6 +131,7 @@ struct ebb_rel_s {
 
   // ---- implicit-step scratch ----
   ebb::StepScratch* step = nullptr;
+  ebb::BatchScratch* batch = nullptr;
 };
 
 namespace ebb {
@@ -171,18 +173,25 @@ ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, doubl
                                const ebb_step_params_t* p, ebb_cg_report_t* rep);
 
 // Morton order, tiles and vertex index from host keys (layout.cu).  `keys`
-// and `X` are the caller's order (X as 3 planes of nv); on return
+// and `X` are the caller's order (X as 3 planes of nv); `batch` (may be null)
+// gives each vertex a group id that orders tets before the Morton code; on return
 // `perm[i]` is the caller's row of internal row i, the vertex index and
 // tet_perm of `tets` are on the device, and `prefix` holds the integer part
 // of every tile blob (kBlobPrefix bytes per tile).
 ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
-                          const std::vector<double>& X, std::vector<int>& perm,
-                          std::vector<int4>& sorted_keys, std::vector<unsigned char>& prefix);
+                          const std::vector<double>& X, const std::vector<int>* batch,
+                          std::vector<int>& perm, std::vector<int4>& sorted_keys,
+                          std::vector<unsigned char>& prefix);
 
 // Pack the tile blobs (both precisions) from the host prefix and the
 // device-side per-tet streams (layout.cu).
 ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix);
 void free_layout(ebb_rel_s* tets);
+
+// Batched implicit step (batched.cu).
+ebb_status_t run_batched_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const void* pinned,
+                              const int* batch, int nmesh, const ebb_step_params_t* p, ebb_cg_report_t* reps);
+void free_batch_scratch(ebb_rel_s* rel);
 
 // Build the colouring (colour.cu).
 ebb_status_t build_colouring(ebb_ctx_s* ctx, ebb_rel_s* tets);

@@ -3,7 +3,8 @@
 // Keys are opaque (Section 5.1, and its footnote: the runtime is free to
 // reorder relations), so the library stores tets in its own order:
 //   1. Morton order of the tet centroids over the rest shape, which keeps
-//      tets that share vertices next to each other;
+//      tets that share vertices next to each other (grouped first by the
+//      optional per-vertex batch id, so independent meshes stay apart);
 //   2. tiles of up to kTileTets consecutive tets touching at most kTileSlots
 //      distinct vertices; each tile's data is packed into one contiguous blob
 //      (see ebb_internal.h) that the tiled map fetches with one bulk copy;
@@ -14,6 +15,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <tuple>
 #include <vector>
 
 #include "ebb_internal.h"
@@ -100,8 +102,8 @@ void free_layout(ebb_rel_s* tets) {
 }
 
 ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
-                          const std::vector<double>& X, std::vector<int>& perm, std::vector<int4>& sorted,
-                          std::vector<unsigned char>& prefix) {
+                          const std::vector<double>& X, const std::vector<int>* batch, std::vector<int>& perm,
+                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix) {
   const int nt = (int)keys.size();
   const int nv = (int)(X.size() / 3);
   cudaStream_t st = ctx->stream;
@@ -116,7 +118,8 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     }
     if (!(hi[c] > lo[c])) hi[c] = lo[c] + 1.0;
   }
-  std::vector<std::pair<uint64_t, int>> code(nt);
+  // Sort key: (group id, Morton code of the centroid, row).
+  std::vector<std::tuple<int, uint64_t, int>> code(nt);
   const double q = (double)((1u << 21) - 1);
   for (int t = 0; t < nt; ++t) {
     const int k[4] = {keys[t].x, keys[t].y, keys[t].z, keys[t].w};
@@ -128,13 +131,13 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
       r = r < 0 ? 0 : (r > 1 ? 1 : r);
       m |= spread3((uint64_t)(r * q)) << c;
     }
-    code[t] = {m, t};
+    code[t] = std::make_tuple(batch ? (*batch)[k[0]] : 0, m, t);
   }
   std::sort(code.begin(), code.end());
   perm.resize(nt);
   sorted.resize(nt);
   for (int i = 0; i < nt; ++i) {
-    perm[i] = code[i].second;
+    perm[i] = std::get<2>(code[i]);
     sorted[i] = keys[perm[i]];
   }
 

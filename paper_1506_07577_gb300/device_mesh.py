@@ -15,9 +15,10 @@ from . import abi
 
 class DeviceTetMesh:
     """Relations ``verts``/``tets`` on one CUDA device with the rest shape,
-    keys and optional per-tet Lame fields bound, finalized on construction."""
+    keys, optional per-tet Lame fields and optional per-vertex batch ids
+    bound, finalized on construction."""
 
-    def __init__(self, X, tets, mu=None, lam=None, device=0, stream=None, colour=False):
+    def __init__(self, X, tets, mu=None, lam=None, device=0, stream=None, colour=False, batch=None):
         self.device = torch.device("cuda", device)
         self.ctx = abi.ebb_ctx_create(device, stream)
         self.n_verts = int(X.shape[0])
@@ -34,6 +35,8 @@ class DeviceTetMesh:
         if mu is not None and np.ndim(mu) > 0:
             self._put("mu", np.asarray(mu, np.float64), self.tets)
             self._put("lambda", np.asarray(lam, np.float64), self.tets)
+        if batch is not None:
+            self.batch = self._put("batch", np.asarray(batch, np.int32), self.verts)
         # uploads ran on torch's current stream; the library may use another
         torch.cuda.synchronize(self.device)
         abi.ebb_relation_finalize(self.ctx, self.tets, abi.EBB_FINALIZE_COLOR if colour else 0)
