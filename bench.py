@@ -320,6 +320,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
+    bat = batched_steps(abi, torch, local_rank, args) if args.batch_meshes > 0 else None
 
     # ---- roofline of the dominant kernel ----------------------------------
     peak, peak_kind = _peaks()
@@ -349,7 +350,8 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": args.steps,
             "clocks": clk,
             "parity_max_rel_err_sampled": err,
-            "implicit_step": imp}
+            "implicit_step": imp,
+            "batched_step": bat}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, m, mu, lam, u, w)
     print(json.dumps(line), flush=True)
@@ -384,6 +386,62 @@ def implicit_steps(dm, m, abi, torch, stream, args):
             "v_rel_diff_mixed_vs_fp64_form": du}
 
 
+def batched_steps(abi, torch, local_rank, args):
+    """256 independent cube grids, n log-uniform in [4, 24] (neo-Hookean,
+    E = 1e5, nu = 0.45), one implicit step each: the batched call (mixed and
+    FP64 forms) against one regular call per mesh (mixed)."""
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    sides = meshgen.batched_sizes(args.batch_meshes, 4, 24, seed=4)
+    b = meshgen.cube_grid_batch(sides, jitter=0.01, seed=400)
+    mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+    nt = int(b.tets.shape[0])
+    out = {"meshes": int(len(sides)), "n_tets": nt, "n_verts": int(b.X.shape[0]),
+           "sides_min": int(sides.min()), "sides_max": int(sides.max())}
+    with DeviceTetMesh(b.X, b.tets, batch=b.batch, device=local_rank) as dm:
+        uu = dm.vertex_field("u", torch.float64)
+        vv = dm.vertex_field("v", torch.float64)
+        dm.bind("pinned", torch.from_numpy(b.pinned.astype(np.uint8)).to(uu.device))
+        for name, prec in (("mixed", abi.EBB_PREC_F32), ("fp64", abi.EBB_PREC_F64)):
+            prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, mu, lam, precision=prec, rtol=1e-8)
+            ts = []
+            for rep in range(3):
+                uu.zero_()
+                vv.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                reps = abi.ebb_cg_implicit_step_batched(dm.ctx, dm.tets, "u", "v", "pinned", "batch", len(sides),
+                                                        prm)
+                ts.append(time.perf_counter() - t0)
+            out[f"{name}_ms"] = 1e3 * min(ts[1:])
+            its = [r.iters for r in reps]
+            out[f"{name}_cg_iters_min_max"] = [min(its), max(its)]
+        out["speedup_vs_fp64_form"] = out["fp64_ms"] / out["mixed_ms"]
+    # one regular call per mesh (mixed), meshes resident, same workload
+    meshes = []
+    for m in range(len(sides)):
+        X, tets, pinned = b.mesh(m)
+        dm = DeviceTetMesh(X, tets, device=local_rank)
+        dm.vertex_field("u", torch.float64)
+        dm.vertex_field("v", torch.float64)
+        dm.bind("pinned", torch.from_numpy(pinned.astype(np.uint8)).to(torch.device("cuda", local_rank)))
+        meshes.append(dm)
+    prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, mu, lam, precision=abi.EBB_PREC_F32, rtol=1e-8)
+    for dm in meshes:   # warm-up (graph capture per mesh)
+        abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm)
+    for dm in meshes:
+        dm._tensors["u"].zero_()
+        dm._tensors["v"].zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for dm in meshes:
+        abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm)
+    out["per_mesh_calls_mixed_ms"] = 1e3 * (time.perf_counter() - t0)
+    out["batched_speedup_vs_per_mesh_calls"] = out["per_mesh_calls_mixed_ms"] / out["mixed_ms"]
+    for dm in meshes:
+        dm.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +451,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--implicit-steps", type=int, default=10)
+    ap.add_argument("--batch-meshes", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -229,6 +229,28 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                   const ebb_step_params_t* params,
                                   ebb_cg_report_t* report);
 
+/* Vector-Jacobian product of one implicit step (the adjoint; St.
+ * Venant-Kirchhoff, FP64 only).  `u`, `v` name the state at the START of the
+ * step (read only; the step is re-solved internally from it).  `gu`, `gv`
+ * name F64 vertex fields holding dL/du', dL/dv' of a scalar loss L with
+ * respect to the step's outputs; on return they hold dL/du, dL/dv.
+ * `gmu`, `glam` name F64 one-component fields bound on the tets relation (in
+ * the caller's tet order) into which dL/dmu and dL/dlambda of each tet are
+ * ADDED; either may be NULL.  With x = X + u, A = M + dt^2 K(x) and v' the
+ * step's new velocity:
+ *   A lam = dL/dv' + dt dL/du'  (pinned rows zero; same PCG, same operator)
+ *   dL/du = dL/du' - dt K lam - dt^2 d/dx[lam^T K(x) v']
+ *   dL/dv = dL/dv' + dt dL/du' - dt^2 K lam
+ *   dL/dtheta += dt d/dtheta[lam^T f] - dt^2 d/dtheta[lam^T K v']  per tet.
+ * The report describes the adjoint solve.  Synchronous.  Errors as for
+ * ebb_cg_implicit_step, plus EBB_ERR_ARG for another model or precision and
+ * EBB_ERR_PHASE if u, v, gu, gv overlap. */
+ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                      const char* v, const char* pinned, const char* gu,
+                                      const char* gv, const char* gmu, const char* glam,
+                                      const ebb_step_params_t* params,
+                                      ebb_cg_report_t* report);
+
 /* Batched form: one implicit step for each of many independent meshes
  * stored in one verts/tets relation pair (the batched meshes of the
  * spec workload list; the per-mesh step is exactly the one above).

@@ -81,6 +81,8 @@ _SIGS = {
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
+    "ebb_cg_implicit_step_vjp": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ebb_step_params_t),
+                                  C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_batched": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.c_int32,
                                       C.POINTER(ebb_step_params_t), C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_noalloc": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -200,6 +202,15 @@ def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), prec
 def ebb_cg_implicit_step(ctx, tets, u, v, pinned, params):
     rep = ebb_cg_report_t()
     _check(ctx, _lib.ebb_cg_implicit_step(ctx, tets, _b(u), _b(v), _b(pinned), C.byref(params), C.byref(rep)))
+    return rep
+
+
+def ebb_cg_implicit_step_vjp(ctx, tets, u, v, pinned, gu, gv, gmu, glam, params):
+    """Adjoint of one step: gu, gv (in dL/du', dL/dv'; out dL/du, dL/dv),
+    per-tet dL/dmu, dL/dlambda added into the tets fields gmu, glam."""
+    rep = ebb_cg_report_t()
+    _check(ctx, _lib.ebb_cg_implicit_step_vjp(ctx, tets, _b(u), _b(v), _b(pinned), _b(gu), _b(gv), _b(gmu),
+                                              _b(glam), C.byref(params), C.byref(rep)))
     return rep
 
 

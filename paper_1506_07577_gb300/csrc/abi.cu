@@ -573,6 +573,61 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
   return run_implicit_step(ctx, tets, (double*)pu, (double*)pv, pp, pdt, &p, report);
 }
 
+ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,
+                                      const char* pinned, const char* gu, const char* gv, const char* gmu,
+                                      const char* glam, const ebb_step_params_t* params, ebb_cg_report_t* report) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (report) *report = ebb_cg_report_t{0, 0.0, EBB_ERR_ARG};
+  if (!tets || !params || !u || !v || !gu || !gv) return set_error(ctx, EBB_ERR_ARG, "null argument");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (params->model != EBB_STVK || params->precision != EBB_PREC_F64)
+    return set_error(ctx, EBB_ERR_ARG, "the step VJP supports StVK in FP64 only");
+  if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
+    return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
+  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
+  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+    return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
+  if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
+    return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
+  void *pu = nullptr, *pv = nullptr, *pgu = nullptr, *pgv = nullptr;
+  ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
+  if (!s) s = vertex_field(ctx, tets, v, EBB_F64, 3, &pv);
+  if (!s) s = vertex_field(ctx, tets, gu, EBB_F64, 3, &pgu);
+  if (!s) s = vertex_field(ctx, tets, gv, EBB_F64, 3, &pgv);
+  if (s) return s;
+  const size_t bytes = (size_t)tets->verts->size * 3 * 8;
+  const void* all[4] = {pu, pv, pgu, pgv};
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (ranges_overlap(all[i], bytes, all[j], bytes))
+        return set_error(ctx, EBB_ERR_PHASE, "u, v, gu and gv must be four distinct fields");
+  double* per_tet[2] = {nullptr, nullptr};
+  const char* names[2] = {gmu, glam};
+  for (int i = 0; i < 2; ++i) {
+    if (!names[i]) continue;
+    const Field* f = find_field(tets, names[i]);
+    if (!f || f->dtype != EBB_F64 || f->ncomp != 1)
+      return set_error(ctx, EBB_ERR_ARG, std::string("per-tet gradient field '") + names[i] +
+                                             "' must be bound on tets as F64 with 1 component");
+    per_tet[i] = (double*)f->ptr;
+  }
+  const void* pp = nullptr;
+  ebb_dtype_t pdt = EBB_U8;
+  if (pinned) {
+    const Field* f = find_field(tets->verts, pinned);
+    if (!f || f->ncomp != 1 || (f->dtype != EBB_U8 && f->dtype != EBB_I32))
+      return set_error(ctx, EBB_ERR_ARG, "pinned must name a U8 or I32 vertex field with 1 component");
+    pp = f->ptr;
+    pdt = f->dtype;
+  }
+  ebb_step_params_t p = *params;
+  p.reduce = reduce;
+  return run_step_vjp(ctx, tets, (const double*)pu, (const double*)pv, pp, pdt, (double*)pgu, (double*)pgv,
+                      per_tet[0], per_tet[1], &p, report);
+}
+
 ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,
                                           const char* pinned, const char* batch, int32_t nbatch,
                                           const ebb_step_params_t* params, ebb_cg_report_t* reports) {

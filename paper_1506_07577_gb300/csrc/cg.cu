@@ -269,6 +269,61 @@ cg_pupdate_kernel(StepConst c, int s, const double* __restrict__ r, const double
   }
 }
 
+// Adjoint solve set-up: b = dL/dv' + dt dL/du' (0 on pinned rows); r = b;
+// z = r / diag(A) (diag from the forward solve at the same state); p = z;
+// y = 0; r.z, r.r and the CG state for iteration 0.
+template <typename PT>
+__global__ void __launch_bounds__(kVecThreads)
+cg_init_rhs_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict__ gu,
+                   const double* __restrict__ gv, const double* __restrict__ dinv, double* r, double* p, double* y,
+                   double* part, CgScalars* sc) {
+  const int n = 3 * c.nv;
+  double rz = 0.0, rr = 0.0;
+#pragma unroll 4
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
+    const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
+    const int vtx = i - comp * c.nv;
+    const double b = is_pinned(pin, vtx) ? 0.0 : gv[i] + c.dt * gu[i];
+    const double z = b * dinv[i];
+    r[i] = b;
+    p[i] = z;
+    y[i] = 0.0;
+    rz += b * z;
+    rr += b * b;
+  }
+  if (reduce_last(rz, rr, part, &sc->count[0]) && threadIdx.x == 0) {
+    sc->rz[0] = rz;
+    sc->rz[1] = 0.0;
+    sc->rr = rr;
+    sc->bb = rr;
+    sc->alpha = sc->beta = 0.0;
+    sc->iter = 0;
+    sc->status = EBB_OK;
+    sc->active[0] = (c.max_iters > 0 && sqrt(rr) > c.rtol * sqrt(rr)) ? 1 : 0;
+    sc->active[1] = 0;
+  }
+}
+
+// w = v' = v + dv; adjoint accumulators zeroed.
+__global__ void vjp_prep_kernel(int n, const double* __restrict__ v, const double* __restrict__ dv, double* w,
+                                double* acc_kl, double* acc_xq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    w[i] = v[i] + dv[i];
+    acc_kl[i] = 0.0;
+    acc_xq[i] = 0.0;
+  }
+}
+
+// dL/du = gu - dt K lam - dt^2 d/dx[lam^T K v'];  dL/dv = gv + dt gu - dt^2 K lam.
+__global__ void vjp_finish_kernel(int n, double dt, const double* __restrict__ acc_kl,
+                                  const double* __restrict__ acc_xq, double* gu, double* gv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double g = gu[i], kl = acc_kl[i];
+    gu[i] = g - dt * kl - dt * dt * acc_xq[i];
+    gv[i] = gv[i] + dt * g - dt * dt * kl;
+  }
+}
+
 // v += dv; u += dt v.
 __global__ void step_finish_kernel(int n, double dt, const double* __restrict__ y, double* u, double* v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -305,6 +360,7 @@ struct StepScratch {
   CgScalars* sc = nullptr;
   CgScalars* h_sc = nullptr;
   double rho = -1.0;
+  double *vjp_w = nullptr, *vjp_kl = nullptr, *vjp_xq = nullptr;   // adjoint-only buffers
 };
 
 void free_step_scratch(ebb_rel_s* rel) {
@@ -321,6 +377,9 @@ void free_step_scratch(ebb_rel_s* rel) {
   cudaFree(s->part);
   cudaFree(s->sc);
   if (s->h_sc) cudaFreeHost(s->h_sc);
+  cudaFree(s->vjp_w);
+  cudaFree(s->vjp_kl);
+  cudaFree(s->vjp_xq);
   if (s->chunk) cudaGraphExecDestroy(s->chunk);
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -329,6 +388,13 @@ void free_step_scratch(ebb_rel_s* rel) {
 }
 
 namespace {
+
+struct VjpArgs {
+  double* gu;     // in: dL/du', out: dL/du
+  double* gv;     // in: dL/dv', out: dL/dv
+  double* gmu;    // per-tet dL/dmu (+=), caller's tet order, may be null
+  double* glam;   // per-tet dL/dlambda (+=), may be null
+};
 
 ebb_status_t ensure_scratch(ebb_ctx_s* ctx, ebb_rel_s* tets) {
   const int nv = (int)tets->verts->size;
@@ -362,7 +428,7 @@ ebb_status_t ensure_scratch(ebb_ctx_s* ctx, ebb_rel_s* tets) {
 
 template <typename T, typename PT>
 ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const PT* pin,
-                       const ebb_step_params_t* prm, ebb_cg_report_t* rep) {
+                       const ebb_step_params_t* prm, ebb_cg_report_t* rep, const VjpArgs* vjp = nullptr) {
   const bool mixed = sizeof(T) == 4;
   StepScratch* s = tets->step;
   const int nv = s->nv;
@@ -476,23 +542,47 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
     s->have_key = true;
   }
 
-  int launched = 0;
   ebb_status_t status = EBB_OK;
-  while (true) {
-    e = cudaGraphLaunch(s->chunk, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_check(ctx, e, "CG chunk");
-    launched += kChunk;
-    const CgScalars& h = *s->h_sc;
-    if (h.status != EBB_OK) {
-      status = h.status;
-      break;
+  auto run_chunks = [&]() -> cudaError_t {
+    int launched = 0;
+    while (true) {
+      cudaError_t ce2 = cudaGraphLaunch(s->chunk, st);
+      if (ce2 == cudaSuccess) ce2 = cudaStreamSynchronize(st);
+      if (ce2 != cudaSuccess) return ce2;
+      launched += kChunk;
+      const CgScalars& h = *s->h_sc;
+      if (h.status != EBB_OK) {
+        status = h.status;
+        return cudaSuccess;
+      }
+      if (!h.active[h.iter & 1] || h.iter >= prm->max_iters) return cudaSuccess;
+      if (launched > prm->max_iters + 2 * kChunk) return cudaSuccess;  // defensive bound
     }
-    if (!h.active[h.iter & 1] || h.iter >= prm->max_iters) break;
-    if (launched > prm->max_iters + 2 * kChunk) break;  // defensive bound
-  }
+  };
+  e = run_chunks();
+  if (e != cudaSuccess) return cuda_check(ctx, e, "CG chunk");
 
-  step_finish_kernel<<<vgrid, 256, 0, st>>>(n, prm->dt, s->y, u, v);
+  if (vjp != nullptr) {
+    // Adjoint of the step just solved (FP64, StVK): v' = v + dv, then the
+    // adjoint solve A lam = gv + dt gu with the same operator (the captured
+    // iterations act on p, K p and the forward state), then the adjoint map.
+    if (status != EBB_OK) return set_error(ctx, status, "forward solve failed inside the step VJP");
+    vjp_prep_kernel<<<vgrid, 256, 0, st>>>(n, v, s->y, s->vjp_w, s->vjp_kl, s->vjp_xq);
+    cg_init_rhs_kernel<PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, pin, vjp->gu, vjp->gv, s->dinv, s->r, s->p, s->y,
+                                                              part_a, s->sc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_chunks();
+    if (e != cudaSuccess) return cuda_check(ctx, e, "adjoint solve");
+    e = launch_adjoint_map(tets, prm->mu, prm->lambda, u, s->y, s->vjp_w, s->vjp_kl, s->vjp_xq, vjp->gmu, vjp->glam,
+                           prm->dt, st);
+    if (e == cudaSuccess) {
+      vjp_finish_kernel<<<vgrid, 256, 0, st>>>(n, prm->dt, s->vjp_kl, s->vjp_xq, vjp->gu, vjp->gv);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_check(ctx, e, "adjoint map");
+  } else {
+    step_finish_kernel<<<vgrid, 256, 0, st>>>(n, prm->dt, s->y, u, v);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -545,6 +635,41 @@ ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, doubl
   }
   return f64 ? step_impl<double, unsigned char>(ctx, tets, u, v, (const unsigned char*)pinned, p, rep)
              : step_impl<float, unsigned char>(ctx, tets, u, v, (const unsigned char*)pinned, p, rep);
+}
+
+ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const void* pinned,
+                          ebb_dtype_t pinned_dtype, double* gu, double* gv, double* gmu, double* glam,
+                          const ebb_step_params_t* p, ebb_cg_report_t* rep) {
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
+  if (tets->verts->size == 0) {
+    if (rep) rep->status = EBB_OK;
+    return EBB_OK;
+  }
+  ebb_status_t s = ensure_scratch(ctx, tets);
+  if (s) return s;
+  StepScratch* sc = tets->step;
+  if (!sc->vjp_w) {
+    const size_t n = (size_t)3 * sc->nv * sizeof(double);
+    cudaError_t e = cudaMalloc(&sc->vjp_w, n);
+    if (e == cudaSuccess) e = cudaMalloc(&sc->vjp_kl, n);
+    if (e == cudaSuccess) e = cudaMalloc(&sc->vjp_xq, n);
+    if (e != cudaSuccess) {
+      cudaFree(sc->vjp_w);
+      cudaFree(sc->vjp_kl);
+      cudaFree(sc->vjp_xq);
+      sc->vjp_w = sc->vjp_kl = sc->vjp_xq = nullptr;
+      cudaGetLastError();
+      return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the step VJP failed");
+    }
+  }
+  VjpArgs a{gu, gv, gmu, glam};
+  // The forward solve reads u and v only; the finish step is replaced by the
+  // adjoint, so neither is written.
+  if (pinned_dtype == EBB_I32)
+    return step_impl<double, int>(ctx, tets, const_cast<double*>(u), const_cast<double*>(v), (const int*)pinned, p,
+                                  rep, &a);
+  return step_impl<double, unsigned char>(ctx, tets, const_cast<double*>(u), const_cast<double*>(v),
+                                          (const unsigned char*)pinned, p, rep, &a);
 }
 
 }  // namespace ebb

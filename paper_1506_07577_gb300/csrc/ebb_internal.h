@@ -188,6 +188,14 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
 ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix);
 void free_layout(ebb_rel_s* tets);
 
+// Step VJP (cg.cu) and its adjoint element map (adjoint.cu).
+ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const void* pinned,
+                          ebb_dtype_t pinned_dtype, double* gu, double* gv, double* gmu, double* glam,
+                          const ebb_step_params_t* p, ebb_cg_report_t* rep);
+cudaError_t launch_adjoint_map(ebb_rel_s* rel, double mu0, double lam0, const double* u, const double* lv,
+                               const double* w, double* acc_kl, double* acc_xq, double* gmu, double* glam, double dt,
+                               cudaStream_t st);
+
 // Batched implicit step (batched.cu).
 ebb_status_t run_batched_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const void* pinned,
                               const int* batch, int nmesh, const ebb_step_params_t* p, ebb_cg_report_t* reps);

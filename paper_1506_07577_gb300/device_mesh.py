@@ -64,7 +64,14 @@ class DeviceTetMesh:
         return t
 
     def bind(self, name, tensor):
+        """Bind an existing CUDA tensor as a vertex field."""
         abi.ebb_field_bind(self.ctx, self.verts, name, tensor)
+        self._tensors[name] = tensor
+        return tensor
+
+    def bind_tets(self, name, tensor):
+        """Bind an existing CUDA tensor as a field of the tets relation."""
+        abi.ebb_field_bind(self.ctx, self.tets, name, tensor)
         self._tensors[name] = tensor
         return tensor
 
