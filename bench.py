@@ -321,6 +321,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
     bat = batched_steps(abi, torch, local_rank, args) if args.batch_meshes > 0 else None
+    adj = adjoint_rollout(abi, torch, local_rank, args) if not args.no_adjoint else None
+    perm = permuted_sweep(abi, torch, local_rank, args, _peaks()[0]) if args.permuted_n > 0 else None
 
     # ---- roofline of the dominant kernel ----------------------------------
     peak, peak_kind = _peaks()
@@ -351,7 +353,9 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "parity_max_rel_err_sampled": err,
             "implicit_step": imp,
-            "batched_step": bat}
+            "batched_step": bat,
+            "adjoint_rollout": adj,
+            "permuted_128": perm}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, m, mu, lam, u, w)
     print(json.dumps(line), flush=True)
@@ -442,6 +446,124 @@ def batched_steps(abi, torch, local_rank, args):
     return out
 
 
+def adjoint_rollout(abi, torch, local_rank, args):
+    """32^3 StVK rollout (per-tet Lame parameters within +-20% of E = 1e5,
+    nu = 0.45), 20 implicit steps, loss = sum of squared final displacements,
+    gradient w.r.t. (u0, v0, mu, lambda) with checkpoints every 5 steps;
+    timed against the plain FP64 forward rollout, and checked against a
+    central difference (h = 1e-6) along one random direction."""
+    from paper_1506_07577_gb300.autograd import rollout
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    n, steps, every, dt = 32, 20, 5, 1e-3
+    m = meshgen.cube_grid(n, jitter=0.01, seed=3)
+    mu, lam = meshgen.material_perturbed_lame(m.n_tets, 1e5, 0.45, 0.2, seed=3)
+    dev = torch.device("cuda", local_rank)
+    prm = abi.step_params(abi.EBB_STVK, dt, 1000.0, precision=abi.EBB_PREC_F64, max_iters=4000, rtol=1e-12)
+    pin = torch.from_numpy(m.pinned.astype(np.uint8)).to(dev)
+    v0 = 0.05 * meshgen.random_field(m.n_verts, seed=3)
+    v0[m.pinned] = 0.0
+
+    def make(mu_, lam_):
+        dm = DeviceTetMesh(m.X, m.tets, mu_, lam_, device=local_rank)
+        dm.bind("pinned", pin)
+        return dm
+
+    def forward_loss(dm, u0_, v0_):
+        uu = dm.vertex_field("fu", torch.float64, value=u0_)
+        dm.vertex_field("fv", torch.float64, value=v0_)
+        for _ in range(steps):
+            abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "fu", "fv", "pinned", prm)
+        return float((uu ** 2).sum())
+
+    out = {"n_tets": m.n_tets, "n_verts": m.n_verts, "steps": steps, "checkpoint_every": every, "dt": dt}
+    with make(mu, lam) as dm:
+        u0 = np.zeros_like(m.X)
+        forward_loss(dm, u0, v0)   # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        base = forward_loss(dm, u0, v0)
+        torch.cuda.synchronize()
+        out["fp64_forward_ms"] = 1e3 * (time.perf_counter() - t0)
+        tu0 = torch.zeros((3, m.n_verts), dtype=torch.float64, device=dev, requires_grad=True)
+        tv0 = torch.from_numpy(np.ascontiguousarray(v0.T)).to(dev).requires_grad_(True)
+        tmu = torch.from_numpy(mu).to(dev).requires_grad_(True)
+        tlam = torch.from_numpy(lam).to(dev).requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uT, _ = rollout(dm, tu0, tv0, tmu, tlam, steps, prm, checkpoint_every=every)
+        loss = (uT ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out["forward_with_checkpoints_ms"] = 1e3 * (t1 - t0)
+        out["backward_ms"] = 1e3 * (t2 - t1)
+        out["gradient_over_forward"] = (t2 - t0) / (out["fp64_forward_ms"] / 1e3)
+        out["loss"] = float(loss)
+        out["loss_rel_diff_vs_plain_forward"] = abs(float(loss) - base) / base
+        gu, gv = tu0.grad.cpu().numpy().T, tv0.grad.cpu().numpy().T
+        gmu, glam = tmu.grad.cpu().numpy(), tlam.grad.cpu().numpy()
+    rng = np.random.default_rng(0)
+    dv = rng.normal(size=v0.shape) * 1e-2
+    dv[m.pinned] = 0.0
+    dmu = rng.normal(size=mu.shape) * 1e3
+    dlam = rng.normal(size=lam.shape) * 1e3
+    h = 1e-6
+    vals = []
+    for sgn in (1.0, -1.0):
+        with make(mu + sgn * h * dmu, lam + sgn * h * dlam) as dmp:
+            vals.append(forward_loss(dmp, np.zeros_like(m.X), v0 + sgn * h * dv))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    an = float(np.sum(gv * dv) + np.sum(gmu * dmu) + np.sum(glam * dlam))
+    out["fd_directional_rel_err"] = abs(fd - an) / abs(an)
+    return out
+
+
+def permuted_sweep(abi, torch, local_rank, args, peak):
+    """128^3 StVK (FP32 element math), vertex and tet ids randomly permuted
+    (the library reorders tets internally): fused force + K*w per reduction
+    variant, L2 flushed before each timed launch."""
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    n = args.permuted_n
+    m = meshgen.cube_grid(n, jitter=0.01, seed=5, permute=True)
+    mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+    u = meshgen.random_displacement(m.X, n, amp=0.05, seed=5, smooth=0.01)
+    w = meshgen.random_field(m.n_verts, seed=5)
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    dm = DeviceTetMesh(m.X, m.tets, device=local_rank, colour=True)
+    setup_s = time.perf_counter() - t0
+    dm.vertex_field("u", torch.float32, value=u)
+    dm.vertex_field("w", torch.float32, value=w)
+    f = dm.vertex_field("f", torch.float32)
+    k = dm.vertex_field("k", torch.float32)
+    bpt = 16 + 36 + 4 + 4 * 12 * m.n_verts / m.n_tets
+    out = {"n_tets": m.n_tets, "n_verts": m.n_verts, "finalize_with_colouring_s": setup_s,
+           "algorithmic_bytes_per_tet": bpt}
+    for name, red in (("tiled", abi.EBB_REDUCE_TILED), ("atomic", abi.EBB_REDUCE_ATOMIC),
+                      ("colour", abi.EBB_REDUCE_COLOR)):
+        o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
+        ts = []
+        for it in range(3 + 5):
+            flush.fill_(float(it))
+            f.zero_()
+            k.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+            b.record()
+            b.synchronize()
+            if it >= 3:
+                ts.append(a.elapsed_time(b) * 1e-3)
+        t = statistics.median(ts)
+        gbs = bpt * m.n_tets / t / 1e9
+        out[name] = {"us": t * 1e6, "tets_per_s": m.n_tets / t, "algorithmic_GBps": gbs, "frac_of_peak": gbs / peak}
+    dm.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,6 +574,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--implicit-steps", type=int, default=10)
     ap.add_argument("--batch-meshes", type=int, default=256)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--permuted-n", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
