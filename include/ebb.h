@@ -97,6 +97,14 @@ typedef enum {
 
 /* ebb_relation_finalize flags */
 #define EBB_FINALIZE_COLOR    1u  /* build the vertex-conflict colouring of tets */
+#define EBB_FINALIZE_REORDER_VERTS 2u  /* number vertices internally in Morton order of
+                                          their rest positions (for meshes whose vertex
+                                          ids are scattered); vertex fields stay in the
+                                          caller's order: maps gather inputs into the
+                                          internal order and scatter outputs back, the
+                                          implicit step does so once per call.  Not
+                                          combinable with verts.batch; the batched step
+                                          and the step VJP refuse such relations. */
 
 /* map flags */
 #define EBB_MAP_ZERO_OUT      1u  /* zero the output fields before reducing into them */

@@ -40,6 +40,7 @@ EBB_STVK, EBB_NEOHOOKEAN = 0, 1
 EBB_PREC_F64, EBB_PREC_F32 = 0, 1
 EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED = 0, 1, 2, 3
 EBB_FINALIZE_COLOR = 1
+EBB_FINALIZE_REORDER_VERTS = 2
 EBB_MAP_ZERO_OUT = 1
 EBB_NOALLOC_MAX_VERTS = 4096
 EBB_NOALLOC_MAX_TETS = 24576

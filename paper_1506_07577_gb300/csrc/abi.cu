@@ -100,6 +100,12 @@ __global__ void copy_material_kernel(int nt, const int* __restrict__ perm, const
 void free_tet_data(ebb_rel_s* r) {
   cudaFree(r->keys);
   r->keys = nullptr;
+  cudaFree(r->vperm);
+  r->vperm = nullptr;
+  for (void*& p : r->vscratch) {
+    cudaFree(p);
+    p = nullptr;
+  }
   cudaFree(r->s64.B);
   cudaFree(r->s64.V);
   cudaFree(r->s64.mu);
@@ -217,6 +223,29 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
       if (s) return s;
     }
   }
+  // Reordered vertices: operands move into the internal order and back.
+  void* user_out[3] = {out[0], out[1], out[2]};
+  const int nv = (int)tets->verts->size;
+  if (tets->vperm) {
+    for (int i = 0; i < 5; ++i)   // sized for FP64 so either precision fits
+      if (!tets->vscratch[i] && cudaMalloc(&tets->vscratch[i], (size_t)nv * 3 * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, EBB_ERR_NOMEM, "device allocation for reordered map operands failed");
+      }
+    cudaError_t ge = cudaSuccess;
+    for (int i = 0; i < mc.nin && ge == cudaSuccess; ++i) {
+      ge = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)in[i], (double*)tets->vscratch[i],
+                                             ctx->stream)
+               : gather_vertex_field<float>(nv, tets->vperm, (const float*)in[i], (float*)tets->vscratch[i],
+                                            ctx->stream);
+      in[i] = tets->vscratch[i];
+    }
+    for (int i = 0; i < mc.nout && ge == cudaSuccess; ++i) {
+      out[i] = tets->vscratch[2 + i];
+      ge = cudaMemsetAsync(out[i], 0, bytes, ctx->stream);
+    }
+    if (ge != cudaSuccess) return cuda_check(ctx, ge, "reordering map operands");
+  }
   cudaError_t e;
   int oi = 0;
   if (f64) {
@@ -236,6 +265,13 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
     if (ops & OP_DIAG) io.d = (float*)out[oi++];
     e = launch_tet_map<float>(tets, opts->model, ops, reduce, (float)opts->mu, (float)opts->lambda, io, nullptr,
                               ctx->stream);
+  }
+  if (e == cudaSuccess && tets->vperm) {
+    for (int i = 0; i < mc.nout && e == cudaSuccess; ++i)
+      e = f64 ? scatter_add_vertex_field<double>(nv, tets->vperm, (const double*)out[i], (double*)user_out[i],
+                                                 ctx->stream)
+              : scatter_add_vertex_field<float>(nv, tets->vperm, (const float*)out[i], (float*)user_out[i],
+                                                ctx->stream);
   }
   return cuda_check(ctx, e, "launching tet map");
 }
@@ -425,11 +461,40 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
       }
     }
   }
+  // Optional vertex renumbering: keys, rest positions and everything built
+  // from them switch to the internal (Morton) vertex order.
+  double* X_int = nullptr;
+  if (flags & EBB_FINALIZE_REORDER_VERTS) {
+    if (!hbatch.empty())
+      return set_error(ctx, EBB_ERR_ARG, "EBB_FINALIZE_REORDER_VERTS cannot be combined with verts.batch");
+    std::vector<int> vp, vinv(nv);
+    vertex_morton_order(hX, vp);
+    for (int i = 0; i < nv; ++i) vinv[vp[i]] = i;
+    for (int t = 0; t < nt; ++t)
+      packed[t] = make_int4(vinv[packed[t].x], vinv[packed[t].y], vinv[packed[t].z], vinv[packed[t].w]);
+    std::vector<double> hXi(hX.size());
+    for (int c = 0; c < 3; ++c)
+      for (int i = 0; i < nv; ++i) hXi[(size_t)c * nv + i] = hX[(size_t)c * nv + vp[i]];
+    hX.swap(hXi);
+    cudaError_t ve = cudaMalloc(&tets->vperm, sizeof(int) * nv);
+    if (ve == cudaSuccess) ve = cudaMemcpy(tets->vperm, vp.data(), sizeof(int) * nv, cudaMemcpyHostToDevice);
+    if (ve == cudaSuccess) ve = cudaMalloc(&X_int, sizeof(double) * hX.size());
+    if (ve == cudaSuccess) ve = cudaMemcpy(X_int, hX.data(), sizeof(double) * hX.size(), cudaMemcpyHostToDevice);
+    if (ve != cudaSuccess) {
+      cudaFree(X_int);
+      free_tet_data(tets);
+      cudaGetLastError();
+      return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the vertex order failed");
+    }
+  }
   std::vector<int> perm;
   std::vector<int4> sorted;
   std::vector<unsigned char> prefix;
   s = build_layout(ctx, tets, packed, hX, hbatch.empty() ? nullptr : &hbatch, perm, sorted, prefix);
-  if (s) return s;
+  if (s) {
+    cudaFree(X_int);
+    return s;
+  }
   packed.swap(sorted);
 
   cudaError_t e = cudaMalloc(&tets->keys, sizeof(int4) * nt);
@@ -444,6 +509,7 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     if (e == cudaSuccess) e = cudaMalloc(&tets->s32.lam, sizeof(float) * nt);
   }
   if (e != cudaSuccess) {
+    cudaFree(X_int);
     free_tet_data(tets);
     cudaGetLastError();
     return set_error(ctx, EBB_ERR_NOMEM, "device allocation for tet data failed");
@@ -451,7 +517,8 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   e = cudaMemcpyAsync(tets->keys, packed.data(), sizeof(int4) * nt, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
     const int th = 256, gr = (nt + th - 1) / th;
-    rest_shape_kernel<<<gr, th, 0, ctx->stream>>>(nt, nv, tets->keys, tets->tet_perm, (const double*)X->ptr, tets->s64.B,
+    const double* Xk = X_int ? X_int : (const double*)X->ptr;
+    rest_shape_kernel<<<gr, th, 0, ctx->stream>>>(nt, nv, tets->keys, tets->tet_perm, Xk, tets->s64.B,
                                                   tets->s64.V, tets->s32.B, tets->s32.V, ctx->d_err);
     if (fmu)
       copy_material_kernel<<<gr, th, 0, ctx->stream>>>(nt, tets->tet_perm, (const double*)fmu->ptr,
@@ -460,6 +527,7 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(X_int);
   if (e != cudaSuccess) {
     free_tet_data(tets);
     return cuda_check(ctx, e, "rest-shape precomputation");
@@ -584,6 +652,7 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
   if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
   if (params->model != EBB_STVK || params->precision != EBB_PREC_F64)
     return set_error(ctx, EBB_ERR_ARG, "the step VJP supports StVK in FP64 only");
+  if (tets->vperm) return set_error(ctx, EBB_ERR_STATE, "the step VJP does not support EBB_FINALIZE_REORDER_VERTS");
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
   ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
@@ -650,6 +719,7 @@ ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const c
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
   if (tets->verts->size == 0) return set_error(ctx, EBB_ERR_ARG, "empty vertex relation");
+  if (tets->vperm) return set_error(ctx, EBB_ERR_STATE, "the batched step does not support EBB_FINALIZE_REORDER_VERTS");
   void *pu = nullptr, *pv = nullptr, *pb = nullptr;
   ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
   if (s) return s;

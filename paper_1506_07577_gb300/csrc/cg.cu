@@ -361,6 +361,8 @@ struct StepScratch {
   CgScalars* h_sc = nullptr;
   double rho = -1.0;
   double *vjp_w = nullptr, *vjp_kl = nullptr, *vjp_xq = nullptr;   // adjoint-only buffers
+  double *u_int = nullptr, *v_int = nullptr;                        // state in the internal vertex order
+  unsigned char* pin_int = nullptr;
 };
 
 void free_step_scratch(ebb_rel_s* rel) {
@@ -380,6 +382,9 @@ void free_step_scratch(ebb_rel_s* rel) {
   cudaFree(s->vjp_w);
   cudaFree(s->vjp_kl);
   cudaFree(s->vjp_xq);
+  cudaFree(s->u_int);
+  cudaFree(s->v_int);
+  cudaFree(s->pin_int);
   if (s->chunk) cudaGraphExecDestroy(s->chunk);
   if (s->ev) cudaEventDestroy(s->ev);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -629,6 +634,33 @@ ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, doubl
   ebb_status_t s = ensure_scratch(ctx, tets);
   if (s) return s;
   const bool f64 = p->precision == EBB_PREC_F64;
+  if (tets->vperm) {
+    // Reordered vertices: the step runs on the state in the internal order.
+    StepScratch* sc = tets->step;
+    const int nv = sc->nv;
+    cudaError_t e = cudaSuccess;
+    if (!sc->u_int) e = cudaMalloc(&sc->u_int, (size_t)3 * nv * sizeof(double));
+    if (e == cudaSuccess && !sc->v_int) e = cudaMalloc(&sc->v_int, (size_t)3 * nv * sizeof(double));
+    if (e == cudaSuccess && !sc->pin_int) e = cudaMalloc(&sc->pin_int, (size_t)nv);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the reordered state failed");
+    }
+    e = gather_vertex_field<double>(nv, tets->vperm, u, sc->u_int, ctx->stream);
+    if (e == cudaSuccess) e = gather_vertex_field<double>(nv, tets->vperm, v, sc->v_int, ctx->stream);
+    if (e == cudaSuccess)
+      e = pinned_dtype == EBB_I32
+              ? gather_pinned<int>(nv, tets->vperm, (const int*)pinned, sc->pin_int, ctx->stream)
+              : gather_pinned<unsigned char>(nv, tets->vperm, (const unsigned char*)pinned, sc->pin_int, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "reordering the state");
+    const ebb_status_t r = f64 ? step_impl<double, unsigned char>(ctx, tets, sc->u_int, sc->v_int, sc->pin_int, p, rep)
+                               : step_impl<float, unsigned char>(ctx, tets, sc->u_int, sc->v_int, sc->pin_int, p, rep);
+    e = scatter_vertex_field(nv, tets->vperm, sc->u_int, u, ctx->stream);
+    if (e == cudaSuccess) e = scatter_vertex_field(nv, tets->vperm, sc->v_int, v, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "restoring the state order");
+    return r;
+  }
   if (pinned_dtype == EBB_I32) {
     return f64 ? step_impl<double, int>(ctx, tets, u, v, (const int*)pinned, p, rep)
                : step_impl<float, int>(ctx, tets, u, v, (const int*)pinned, p, rep);

@@ -122,6 +122,8 @@ struct ebb_rel_s {
   ebb_rel_s* verts = nullptr;
   int4* keys = nullptr;                 // internal keys, one int4 per tet (Morton order)
   int* tet_perm = nullptr;              // internal row -> caller's row
+  int* vperm = nullptr;                 // internal vertex -> caller's vertex (null: same order)
+  void* vscratch[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // reordered map operands
   ebb::TetStreams<double> s64;
   ebb::TetStreams<float> s32;
   ebb::Colouring colour;
@@ -200,6 +202,18 @@ cudaError_t launch_adjoint_map(ebb_rel_s* rel, double mu0, double lam0, const do
 ebb_status_t run_batched_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const void* pinned,
                               const int* batch, int nmesh, const ebb_step_params_t* p, ebb_cg_report_t* reps);
 void free_batch_scratch(ebb_rel_s* rel);
+
+// Vertex reordering helpers (reorder.cu).  Gather: dst[c][i] = src[c][vperm[i]];
+// scatter-add: dst[c][vperm[i]] += src[c][i]; scatter: dst[c][vperm[i]] = src[c][i].
+template <typename T>
+cudaError_t gather_vertex_field(int nv, const int* vperm, const T* src, T* dst, cudaStream_t st);
+template <typename T>
+cudaError_t scatter_add_vertex_field(int nv, const int* vperm, const T* src, T* dst, cudaStream_t st);
+cudaError_t scatter_vertex_field(int nv, const int* vperm, const double* src, double* dst, cudaStream_t st);
+template <typename PT>
+cudaError_t gather_pinned(int nv, const int* vperm, const PT* src, unsigned char* dst, cudaStream_t st);
+// Morton order of vertex positions (X as 3 planes of nv): perm[i] = vertex at internal row i.
+void vertex_morton_order(const std::vector<double>& X, std::vector<int>& perm);
 
 // Build the colouring (colour.cu).
 ebb_status_t build_colouring(ebb_ctx_s* ctx, ebb_rel_s* tets);

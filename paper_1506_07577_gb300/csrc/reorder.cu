@@ -1,0 +1,126 @@
+// Vertex renumbering (EBB_FINALIZE_REORDER_VERTS).
+//
+// Keys are opaque (Section 5.1 and its footnote), so the library may number
+// vertices its own way: Morton order of the rest positions, which puts the
+// vertices of neighbouring tets next to each other in memory.  Caller-owned
+// vertex fields keep the caller's order; these kernels move values between
+// the two orders (the permutation is a bijection, so scatters never
+// collide).
+#include <algorithm>
+#include <cstdint>
+#include <tuple>
+#include <vector>
+
+#include "ebb_internal.h"
+
+namespace ebb {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void gather_kernel(int nv, const int* __restrict__ vperm, const T* __restrict__ src, T* dst) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  const int o = vperm[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dst[(size_t)c * nv + i] = src[(size_t)c * nv + o];
+}
+
+template <typename T>
+__global__ void scatter_add_kernel(int nv, const int* __restrict__ vperm, const T* __restrict__ src, T* dst) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  const int o = vperm[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dst[(size_t)c * nv + o] += src[(size_t)c * nv + i];
+}
+
+__global__ void scatter_kernel(int nv, const int* __restrict__ vperm, const double* __restrict__ src, double* dst) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  const int o = vperm[i];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dst[(size_t)c * nv + o] = src[(size_t)c * nv + i];
+}
+
+template <typename PT>
+__global__ void gather_pin_kernel(int nv, const int* __restrict__ vperm, const PT* __restrict__ src,
+                                  unsigned char* dst) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  dst[i] = src == nullptr ? 0 : (src[vperm[i]] != 0 ? 1 : 0);
+}
+
+uint64_t spread3(uint64_t x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t gather_vertex_field(int nv, const int* vperm, const T* src, T* dst, cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  gather_kernel<T><<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, src, dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scatter_add_vertex_field(int nv, const int* vperm, const T* src, T* dst, cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  scatter_add_kernel<T><<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t scatter_vertex_field(int nv, const int* vperm, const double* src, double* dst, cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  scatter_kernel<<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, src, dst);
+  return cudaGetLastError();
+}
+
+template <typename PT>
+cudaError_t gather_pinned(int nv, const int* vperm, const PT* src, unsigned char* dst, cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  gather_pin_kernel<PT><<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, src, dst);
+  return cudaGetLastError();
+}
+
+template cudaError_t gather_vertex_field<float>(int, const int*, const float*, float*, cudaStream_t);
+template cudaError_t gather_vertex_field<double>(int, const int*, const double*, double*, cudaStream_t);
+template cudaError_t scatter_add_vertex_field<float>(int, const int*, const float*, float*, cudaStream_t);
+template cudaError_t scatter_add_vertex_field<double>(int, const int*, const double*, double*, cudaStream_t);
+template cudaError_t gather_pinned<unsigned char>(int, const int*, const unsigned char*, unsigned char*,
+                                                  cudaStream_t);
+template cudaError_t gather_pinned<int>(int, const int*, const int*, unsigned char*, cudaStream_t);
+
+void vertex_morton_order(const std::vector<double>& X, std::vector<int>& perm) {
+  const int nv = (int)(X.size() / 3);
+  double lo[3], hi[3];
+  for (int c = 0; c < 3; ++c) {
+    lo[c] = nv ? *std::min_element(X.begin() + (size_t)c * nv, X.begin() + (size_t)(c + 1) * nv) : 0.0;
+    hi[c] = nv ? *std::max_element(X.begin() + (size_t)c * nv, X.begin() + (size_t)(c + 1) * nv) : 1.0;
+    if (!(hi[c] > lo[c])) hi[c] = lo[c] + 1.0;
+  }
+  const double q = (double)((1u << 21) - 1);
+  std::vector<std::pair<uint64_t, int>> code(nv);
+  for (int v = 0; v < nv; ++v) {
+    uint64_t m = 0;
+    for (int c = 0; c < 3; ++c) {
+      double r = (X[(size_t)c * nv + v] - lo[c]) / (hi[c] - lo[c]);
+      r = r < 0 ? 0 : (r > 1 ? 1 : r);
+      m |= spread3((uint64_t)(r * q)) << c;
+    }
+    code[v] = {m, v};
+  }
+  std::sort(code.begin(), code.end());
+  perm.resize(nv);
+  for (int i = 0; i < nv; ++i) perm[i] = code[i].second;
+}
+
+}  // namespace ebb

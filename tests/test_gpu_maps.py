@@ -97,8 +97,9 @@ def test_permuted_ids_match_oracle():
             assert rel_err(got["f"], f) < 1e-5 and rel_err(got["Kw"], Kw) < 1e-5
 
 
-@pytest.mark.parametrize("n,model,prec", [(64, "nh", "f32"), (128, "stvk", "f32"), (32, "stvk", "f64")])
-def test_full_size_sampled_vertices(n, model, prec):
+@pytest.mark.parametrize("n,model,prec,reorder", [(64, "nh", "f32", False), (128, "stvk", "f32", False),
+                                                  (128, "stvk", "f32", True), (32, "stvk", "f64", False)])
+def test_full_size_sampled_vertices(n, model, prec, reorder):
     """At the benchmark sizes the oracle checks sampled vertices: each is
     recomputed exactly from its incident tets only."""
     abi = _abi()
@@ -115,7 +116,9 @@ def test_full_size_sampled_vertices(n, model, prec):
     x = m.X + u
     f = fem.tet_forces(x, sub, B, V, mu_s, lam_s, mdl)[sample]
     Kw = fem.tet_Kv(x, w, sub, B, V, mu_s, lam_s, mdl)[sample]
-    with _mesh(m, mu, lam, colour=False) as dm:
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    with DeviceTetMesh(m.X, m.tets, mu if np.ndim(mu) else None, lam if np.ndim(lam) else None,
+                       reorder_verts=reorder) as dm:
         got = _run_maps(dm, u, w, model, prec, abi.EBB_REDUCE_TILED, mu, lam)
     tol = TOL[prec]
     assert rel_err(got["f"][sample], f) < tol
