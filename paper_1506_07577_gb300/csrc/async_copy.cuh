@@ -64,4 +64,53 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long l
   return true;
 }
 
+// Wait as above, but also give up as soon as *abort becomes non-zero (another
+// warp of the CTA gave up).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity, const volatile int* abort,
+                                                   long long limit) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort != 0 || clock64() - t0 > limit) return false;
+  }
+  return true;
+}
+
+// Plain arrive (release) on a barrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Element-wise asynchronous global->shared copies (4 or 8 bytes, naturally
+// aligned), cached in L1.
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// One arrival on `bar` once every cp.async this thread issued so far has
+// landed (the barrier's expected count includes this arrival).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Named barrier 1 over the first `nthreads` threads, OR-reducing `v`.
+template <int NTHREADS>
+__device__ __forceinline__ bool named_sync_or(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((unsigned)v), "n"(NTHREADS)
+      : "memory");
+  return r != 0;
+}
+
 }  // namespace ebb

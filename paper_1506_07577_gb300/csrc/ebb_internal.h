@@ -49,9 +49,14 @@ struct Colouring {
 // packed into one contiguous blob:
 //   header  int4 {ntets, nslots, first internal tet row, nunits}
 //   slots   uchar4[kTileTets]        tile-local slot of each tet corner
-//   ent     u16[kTileTets][kUnitEntries]  entries (corner, tet) = a*256+t summed
-//                                    by thread i, padded with a*256+kTileTets
-//                                    (a row that is always zero)
+//   ent     u16[kTileTets][kUnitEntries]  entries summed by thread i: entry
+//                                    (corner a, tet t) is coded as the row
+//                                    3a*(kTileTets+1) + t of the per-corner
+//                                    output array (rows 3a+c of kTileTets+1
+//                                    columns); an unused step holds
+//                                    kEntryNone.  The steps are ordered so
+//                                    that the 16 threads of a half-warp hit
+//                                    distinct bank pairs where possible
 //   units   u32[kTileTets]           reduction work of thread i: bit 0 has a
 //                                    unit, 14-21 slot, 22-25 lanes after this
 //                                    one in the same slot and warp, 26 first
@@ -66,6 +71,7 @@ constexpr int kTileTets = 128;   // tets per tile (= threads per CTA)
 constexpr int kTileSlots = 128;  // distinct vertices per tile (u8 slots)
 constexpr int kUnitEntries = 8;  // entries summed by one thread
 constexpr int kUnitMaxRun = 16;  // units of one slot (4-bit lane count)
+constexpr unsigned short kEntryNone = 0xffff;
 constexpr int kBlobSlots = 16;
 constexpr int kBlobEnt = kBlobSlots + 4 * kTileTets;
 constexpr int kBlobUnits = kBlobEnt + 2 * kUnitEntries * kTileTets;
@@ -76,6 +82,7 @@ static_assert(kTileTets < 256 && kTileSlots <= 256, "entry code and unit descrip
 
 struct BlobLayout {
   int bytes = 0;           // per tile (multiple of 128)
+  int copy = 0;            // bytes a kernel copies per tile (multiple of 16, <= bytes)
   int B = 0, V = 0;        // byte offsets of the element-precision arrays
   int mu = -1, lam = -1;   // -1: uniform material
 };

@@ -35,6 +35,76 @@ uint64_t spread3(uint64_t x) {
   return x;
 }
 
+// Order the entries of the reduction units of 16 consecutive threads (one
+// half-warp) over the kUnitEntries steps so that, at each step, the threads
+// read output rows in distinct shared-memory bank pairs.  The bank pair of
+// the row coded 3a*(kTileTets+1) + t is code mod 16 (kTileTets+1 = 1 mod 16).
+// This is an edge colouring of the bipartite multigraph threads x bank pairs
+// with one colour per step: with every degree at most kUnitEntries it exists
+// (Koenig's edge-colouring theorem) and the alternating-path method finds it.
+// A bank pair with more than kUnitEntries entries is first split into copies
+// of at most kUnitEntries each (entries of different copies may then share a
+// step: the unavoidable conflicts).  ent[l * kUnitEntries + q] receives the
+// entry thread l reads at step q, or kEntryNone.
+void schedule_half_warp(std::vector<std::vector<unsigned short>>& lanes, unsigned short* ent) {
+  constexpr int C = kUnitEntries;
+  const int nl = (int)lanes.size();
+  struct Edge {
+    int x, y, colour;
+    unsigned short code;
+  };
+  std::vector<Edge> edges;
+  int copies[16] = {0}, fill[16] = {0}, first_copy[16];
+  for (int l = 0; l < nl; ++l)
+    for (unsigned short code : lanes[l]) copies[code & 15]++;
+  int nright = 0;
+  for (int k = 0; k < 16; ++k) {
+    first_copy[k] = nright;
+    nright += (copies[k] + C - 1) / C;
+  }
+  for (int l = 0; l < nl; ++l)
+    for (unsigned short code : lanes[l]) {
+      const int k = code & 15;
+      edges.push_back({l, nl + first_copy[k] + fill[k]++ / C, -1, code});
+    }
+  const int nvert = nl + nright;
+  std::vector<int> at((size_t)nvert * C, -1);  // at[v*C + colour] = edge
+  auto free_colour = [&](int v) {
+    for (int c = 0; c < C; ++c)
+      if (at[(size_t)v * C + c] < 0) return c;
+    return -1;
+  };
+  for (int e = 0; e < (int)edges.size(); ++e) {
+    const int x = edges[e].x, y = edges[e].y;
+    const int a = free_colour(x), b = free_colour(y);
+    if (at[(size_t)y * C + a] >= 0) {
+      // Swap colours a and b along the path from y that alternates a, b.
+      std::vector<int> path;
+      int v = y, c = a;
+      while (at[(size_t)v * C + c] >= 0) {
+        const int f = at[(size_t)v * C + c];
+        path.push_back(f);
+        v = edges[f].x == v ? edges[f].y : edges[f].x;
+        c = c == a ? b : a;
+      }
+      for (int f : path) {
+        at[(size_t)edges[f].x * C + edges[f].colour] = -1;
+        at[(size_t)edges[f].y * C + edges[f].colour] = -1;
+      }
+      for (int f : path) {
+        edges[f].colour = edges[f].colour == a ? b : a;
+        at[(size_t)edges[f].x * C + edges[f].colour] = f;
+        at[(size_t)edges[f].y * C + edges[f].colour] = f;
+      }
+    }
+    edges[e].colour = a;
+    at[(size_t)x * C + a] = e;
+    at[(size_t)y * C + a] = e;
+  }
+  for (int i = 0; i < nl * C; ++i) ent[i] = kEntryNone;
+  for (const Edge& e : edges) ent[e.x * C + e.colour] = e.code;
+}
+
 template <typename T>
 cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   if (src.empty()) {
@@ -56,6 +126,7 @@ BlobLayout make_layout(size_t elem, bool material) {
     L.lam = L.mu + (int)(kTileTets * elem);
     end = L.lam + (int)(kTileTets * elem);
   }
+  L.copy = (end + 15) / 16 * 16;
   L.bytes = (end + 127) / 128 * 128;
   return L;
 }
@@ -239,30 +310,35 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
         cnt[s4.w + 1]++;
       }
       for (int j = 0; j < nvu; ++j) cnt[j + 1] += cnt[j];
-      // Units: thread i sums a run of <= kUnitEntries entries of one slot
-      // (padded to kUnitEntries with the zero row).  Consecutive units of a
-      // slot inside one warp form a segment combined by shuffles; its first
-      // lane adds the sum into the field.
+      // Units: thread i sums a run of <= kUnitEntries entries of one slot.
+      // Consecutive units of a slot inside one warp form a segment combined
+      // by shuffles; its first lane adds the sum into the field.
       std::vector<unsigned short> grouped(cnt[nvu]);
       {
         std::vector<int> fill(cnt.begin(), cnt.begin() + nvu);
         for (int t = tb; t < te; ++t) {
           const uchar4 s4 = slots[t - tb];
           const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
-          for (int a = 0; a < 4; ++a) grouped[fill[sl[a]]++] = (unsigned short)(a * 256 + (t - tb));
+          for (int a = 0; a < 4; ++a)
+            grouped[fill[sl[a]]++] = (unsigned short)(3 * a * (kTileTets + 1) + (t - tb));
         }
       }
       int nunits = 0;
       std::vector<int> uslot;
+      std::vector<std::vector<unsigned short>> unit_ent;
       for (int j = 0; j < nvu; ++j) {
         for (int e = cnt[j]; e < cnt[j + 1]; e += kUnitEntries) {
           const int n = std::min(kUnitEntries, cnt[j + 1] - e);
-          for (int q = 0; q < kUnitEntries; ++q)
-            ent[nunits * kUnitEntries + q] = q < n ? grouped[e + q] : (unsigned short)kTileTets;
+          unit_ent.emplace_back(grouped.begin() + e, grouped.begin() + e + n);
           units[nunits] = 1u | ((uint32_t)j << 14);
           uslot.push_back(j);
           ++nunits;
         }
+      }
+      for (int h0 = 0; h0 < nunits; h0 += 16) {
+        std::vector<std::vector<unsigned short>> half(unit_ent.begin() + h0,
+                                                      unit_ent.begin() + std::min(nunits, h0 + 16));
+        schedule_half_warp(half, ent + h0 * kUnitEntries);
       }
       for (int i = 0; i < nunits; ++i) {
         const bool head = i == 0 || uslot[i - 1] != uslot[i] || (i % 32) == 0;

@@ -10,11 +10,11 @@
 //           vertex-conflict colouring (Section 7.4, Liszt's colouring);
 //   tiled   persistent CTAs over tiles of Morton-ordered tets; each tile's
 //           per-tet data arrives as one bulk copy into shared memory, its
-//           distinct vertices are gathered once, per-corner results go to
-//           shared memory, each distinct vertex sums its entries in a fixed
-//           order (no shared-memory atomics) and gets one add per component --
-//           a plain add when no other tile touches the vertex, a global atomic
-//           otherwise.
+//           distinct vertices are gathered once (asynchronously, by a
+//           producer warp), per-corner results go to shared memory, and each
+//           distinct vertex sums its entries in a fixed order (no
+//           shared-memory atomics) and gets one global atomic add per
+//           component.
 #include <cstdint>
 
 #include "async_copy.cuh"
@@ -169,34 +169,44 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
   }
 }
 
-// ---- tiled: persistent CTAs over tile blobs --------------------------------
-// Each CTA walks tiles blockIdx.x, blockIdx.x + G, ... (G = gridDim.x).  The
-// integer part of each tile blob (slots, entries, reduction units, vertex
-// ids) is fetched with one cp.async.bulk into a 3-deep shared ring, two
-// tiles ahead; the per-tet floats (Dm^-1, V, Lame) are read straight from
-// the blob in global memory with coalesced loads one tile ahead into
-// registers, and the next tile's vertex values are loaded into registers
-// while the current tile computes.  Per tile, with one CTA barrier:
-//   phase 1  one tet per thread: corner values from the slot vectors,
-//            element evaluation, per-corner outputs to shared memory (fields
-//            interleaved, conflict-free); then the prefetched vertex values
-//            of the next tile go to the other slot buffer;
-//                                    -- the one barrier per tile --
+// ---- tiled: warp-specialised persistent CTAs over tile blobs --------------
+// A CTA is kTileTets consumer threads (one tet each) plus one producer warp,
+// and walks tiles blockIdx.x, blockIdx.x + G, ... (G = gridDim.x).  The
+// producer keeps the consumers fed through two shared-memory rings guarded by
+// mbarriers (every wait bounded):
+//   blob ring  (RB stages)  each tile's whole blob -- integer prefix and
+//              per-tet Dm^-1, V, Lame planes -- as one cp.async.bulk;
+//   slot ring  (RV stages)  the tile's distinct vertex values (u, and w for
+//              K w), gathered by the producer's 32 lanes with element-wise
+//              cp.async as soon as the tile's vertex ids have landed, its
+//              completion tracked by an mbarrier (LAG tiles behind the
+//              blob copies).
+// The consumers, per tile, with one named barrier among themselves:
+//   phase 1  one tet per thread: corner values from the slot vectors, per-tet
+//            floats from the blob, element evaluation, per-corner outputs to
+//            shared memory (fields interleaved, conflict-free);
+//                                 -- the consumers' barrier --
+//            (the tile's slot vectors are released to the producer)
 //   phase 2  one reduction unit per thread: the sum of at most kUnitEntries
 //            entries of one vertex, in a fixed order; the units of one vertex
 //            on consecutive lanes are combined by a segmented shuffle tree and
 //            the run's first lane issues one atomic add per component (a
-//            fire-and-forget reduction).  Every thread does at most
-//            kUnitEntries steps, whatever the vertex degrees.
-// Slot vectors and per-corner outputs are double buffered, so phase 2 of one
-// tile overlaps phase 1 of the next.
-// Dynamic shared memory: prefix ring[3] | slot vectors[2] (u[S][4], then
-// w[S][4] for K w) | outputs[2][4][3][TT+1][NF] | mbarrier[3].
+//            fire-and-forget reduction); then each warp releases the blob.
+// With two per-corner output buffers phase 2 of one tile overlaps phase 1 of
+// the next; with one, a second consumer barrier precedes the output stores.  Dynamic shared memory: blob ring | slot ring (u[S][4]
+// then w[S][4] per stage) | outputs[2][4*3][TT+1][NF] | barriers, abort flag.
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
-constexpr int kRing = 3;
+constexpr int kTileThreads = kTileTets + 32;
 
 template <typename T, int OPS>
 struct TileSmem {
+  // Ring depths: FP32 blobs are small enough for four stages at three CTAs
+  // per SM; FP64 blobs take two stages at two CTAs per SM.
+  static constexpr int RB = sizeof(T) == 4 ? 4 : 2;   // blob stages
+  static constexpr int RV = 2;                        // slot-vector stages
+  static constexpr int LAG = sizeof(T) == 4 ? 2 : 1;  // gathers trail blob copies by LAG tiles
+  static constexpr int OB = 2;                        // per-corner output buffers
+  static_assert(LAG < RB, "the producer must not wait for a blob it has not issued");
   static constexpr bool FO = (OPS & OP_FORCE) != 0;
   static constexpr bool KV = (OPS & OP_KV) != 0;
   static constexpr bool DG = (OPS & OP_DIAG) != 0;
@@ -204,29 +214,13 @@ struct TileSmem {
   static constexpr int S = kTileSlots;
   static constexpr int TT = kTileTets;
   static constexpr size_t slot_elems = (size_t)S * 4 * (KV ? 2 : 1);
-  static constexpr size_t out_elems = (size_t)4 * 3 * (TT + 1) * NF;  // row TT stays zero
-  static constexpr size_t ring_bytes = (size_t)kRing * kBlobPrefix;
-  static constexpr size_t bytes = ring_bytes + sizeof(T) * (2 * slot_elems + 2 * out_elems) + kRing * sizeof(uint64_t);
+  static constexpr size_t out_elems = (size_t)4 * 3 * (TT + 1) * NF;  // rows of TT+1: column TT pads
+  static constexpr int nbar = 2 * RB + 2 * RV;
+  __host__ __device__ static size_t slot_off(const BlobLayout& L) { return (size_t)RB * L.bytes; }
+  __host__ __device__ static size_t out_off(const BlobLayout& L) { return slot_off(L) + sizeof(T) * RV * slot_elems; }
+  __host__ __device__ static size_t bar_off(const BlobLayout& L) { return out_off(L) + sizeof(T) * OB * out_elems; }
+  __host__ __device__ static size_t bytes(const BlobLayout& L) { return bar_off(L) + sizeof(uint64_t) * nbar + 16; }
 };
-
-template <typename T>
-struct TetRegs {
-  T B[9];
-  T V, mu, lam;
-};
-
-// Coalesced loads of one tile's per-tet floats (the blob is zero padded, so
-// every thread may load).
-template <typename T>
-__device__ __forceinline__ void load_tet_regs(const unsigned char* blob, const BlobLayout& L, int tid, T mu0,
-                                              T lam0, TetRegs<T>& r) {
-  const T* B = reinterpret_cast<const T*>(blob + L.B);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) r.B[i] = B[i * kTileTets + tid];
-  r.V = reinterpret_cast<const T*>(blob + L.V)[tid];
-  r.mu = L.mu >= 0 ? reinterpret_cast<const T*>(blob + L.mu)[tid] : mu0;
-  r.lam = L.lam >= 0 ? reinterpret_cast<const T*>(blob + L.lam)[tid] : lam0;
-}
 
 // 3-vectors stored 4 wide in shared memory.
 __device__ __forceinline__ void ld3(const float* p, float* v) {
@@ -240,13 +234,6 @@ __device__ __forceinline__ void ld3(const double* p, double* v) {
   v[0] = q.x;
   v[1] = q.y;
   v[2] = p[2];
-}
-__device__ __forceinline__ void st3(float* p, const float* v) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], 0.f);
-}
-__device__ __forceinline__ void st3(double* p, const double* v) {
-  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  p[2] = v[2];
 }
 
 // NF interleaved output values at p.
@@ -281,16 +268,106 @@ __device__ __forceinline__ void add_out(const T* p, T* acc) {
 }
 
 template <typename T, int MODEL, int OPS>
-__global__ void __launch_bounds__(kTileTets, sizeof(T) == 4 ? 5 : 2)
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
 tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, BlobLayout L,
                 const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err) {
   using Z = TileSmem<T, OPS>;
-  constexpr int TT = Z::TT, NF = Z::NF;
+  constexpr int TT = Z::TT, NF = Z::NF, RB = Z::RB, RV = Z::RV;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* ring = smem;
-  T* slotv = reinterpret_cast<T*>(smem + Z::ring_bytes);
-  T* so = slotv + 2 * Z::slot_elems;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(so + 2 * Z::out_elems);
+  T* slots = reinterpret_cast<T*>(smem + Z::slot_off(L));
+  T* outs = reinterpret_cast<T*>(smem + Z::out_off(L));
+  uint64_t* full_b = reinterpret_cast<uint64_t*>(smem + Z::bar_off(L));
+  uint64_t* empty_b = full_b + RB;
+  uint64_t* full_v = empty_b + RB;
+  uint64_t* empty_v = full_v + RV;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty_v + RV);
+
+  if (active != nullptr && *active == 0) return;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int G = gridDim.x;
+  if ((int)blockIdx.x >= ntiles) return;
+  const int n_my = (ntiles - (int)blockIdx.x + G - 1) / G;
+  if (tid == 0) {
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      mbar_init(&full_b[r], 1);
+      mbar_init(&empty_b[r], TT / 32);
+    }
+#pragma unroll
+    for (int r = 0; r < RV; ++r) {
+      mbar_init(&full_v[r], 32);
+      mbar_init(&empty_v[r], 1);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (tid >= TT) {
+    // ---------------------------------------------------------- producer --
+    unsigned pend = 0u, pend_parity = 0u;  // blob stages with an unwaited copy
+    bool bad = false;
+    for (int j = 0; j < n_my + Z::LAG && !bad; ++j) {
+      if (j < n_my) {
+        const int sb = j % RB;
+        bool ok = j < RB || mbar_wait_or_abort(&empty_b[sb], ((j / RB) - 1) & 1u, abort_flag, kWaitCycles);
+        if (__any_sync(0xffffffffu, !ok)) {
+          bad = true;
+          break;
+        }
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          bulk_load(ring + (size_t)sb * L.bytes, blobs + (size_t)((int)blockIdx.x + j * G) * L.bytes, L.copy,
+                    &full_b[sb]);
+        }
+        pend |= 1u << sb;
+        pend_parity = (pend_parity & ~(1u << sb)) | (((unsigned)(j / RB) & 1u) << sb);
+      }
+      const int jj = j - Z::LAG;
+      if (jj >= 0 && jj < n_my) {
+        const int sb = jj % RB, sv = jj % RV;
+        bool ok = mbar_wait_or_abort(&full_b[sb], (jj / RB) & 1u, abort_flag, kWaitCycles);
+        if (ok) pend &= ~(1u << sb);
+        ok = ok && (jj < RV || mbar_wait_or_abort(&empty_v[sv], ((jj / RV) - 1) & 1u, abort_flag, kWaitCycles));
+        if (__any_sync(0xffffffffu, !ok)) {
+          bad = true;
+          break;
+        }
+        const unsigned char* st = ring + (size_t)sb * L.bytes;
+        const int nvu = reinterpret_cast<const int4*>(st)->y;
+        const int* vid = reinterpret_cast<const int*>(st + kBlobVtx);
+        T* su = slots + (size_t)sv * Z::slot_elems;
+        // Lane l copies word l + 32k of the 4-wide slot vectors (component 3
+        // is padding): consecutive lanes write consecutive shared words.
+        for (int wd = lane; wd < 4 * nvu; wd += 32) {
+          const int c = wd & 3;
+          if (c < 3) {
+            const int v = vid[wd >> 2];
+            cp_async_elem(su + wd, io.u + (size_t)c * nv + v);
+            if (Z::KV) cp_async_elem(su + 4 * Z::S + wd, io.w + (size_t)c * nv + v);
+          }
+        }
+        cp_async_arrive_noinc(&full_v[sv]);
+      }
+    }
+    cp_async_wait_all();
+    if (bad) {
+      if (lane == 0) {
+        raise_error(err, EBB_ERR_TIMEOUT, blockIdx.x);
+        *abort_flag = 1;
+      }
+      // Bounded drain of the bulk copies still in flight before the CTA's
+      // shared memory goes away.
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if ((pend >> r) & 1u) mbar_wait(&full_b[r], (pend_parity >> r) & 1u, kWaitCycles);
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------ consumers --
   T* out_field[3];
   {
     int f = 0;
@@ -298,203 +375,115 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
     if (Z::KV) out_field[f++] = io.Kw;
     if (Z::DG) out_field[f++] = io.d;
   }
-
-  if (active != nullptr && *active == 0) return;
-  const int tid = threadIdx.x;
-  const int G = gridDim.x;
-  int tile = blockIdx.x;
-  if (tile >= ntiles) return;
-  if (tid == 0) {
-#pragma unroll
-    for (int r = 0; r < kRing; ++r) mbar_init(&bar[r], 1);
-    fence_mbar_init();
-  }
-  // Zero rows (tet index TT) read by padded reduction entries.
-  for (int i = tid; i < 2 * 12 * NF; i += TT) {
-    const int buf = i / (12 * NF), ac = (i / NF) % 12, f = i % NF;
-    so[buf * Z::out_elems + ((size_t)ac * (TT + 1) + TT) * NF + f] = T(0);
-  }
-  __syncthreads();
-  // Ring state, identical in every thread unless a wait times out: bit r of
-  // `pend` = a copy into ring slot r is in flight; bit r of `parity` = the
-  // phase parity to wait for next.
-  unsigned pend = 0u, parity = 0u;
-#pragma unroll
-  for (int r = 0; r < kRing - 1; ++r) {
-    const int t = tile + r * G;
-    if (t < ntiles) {
-      if (tid == 0) bulk_load(ring + r * kBlobPrefix, blobs + (size_t)t * L.bytes, kBlobPrefix, &bar[r]);
-      pend |= 1u << r;
-    }
-  }
-  TetRegs<T> tr;
-  load_tet_regs(blobs + (size_t)tile * L.bytes, L, tid, mu0, lam0, tr);
-  bool bad = !mbar_wait(&bar[0], 0u, kWaitCycles);
-  if (__syncthreads_or(bad)) goto drain;
-  pend &= ~1u;
-  parity ^= 1u;
-  {
-    const int4 h = *reinterpret_cast<const int4*>(ring);
-    for (int j = tid; j < h.y; j += TT) {
-      const int v = reinterpret_cast<const int*>(ring + kBlobVtx)[j];
-      T x[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) x[c] = io.u[(size_t)c * nv + v];
-      st3(slotv + 4 * j, x);
-      if (Z::KV) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) x[c] = io.w[(size_t)c * nv + v];
-        st3(slotv + 4 * (Z::S + j), x);
-      }
-    }
-  }
-  __syncthreads();
-
-  for (int k = 0;; ++k) {
-    const int b = k & 1;
-    const int rc = k % kRing, rn = (k + 1) % kRing;
-    const unsigned char* pre = ring + rc * kBlobPrefix;
-    const unsigned char* pren = ring + rn * kBlobPrefix;
-    const T* su = slotv + (b ? Z::slot_elems : 0);
+  for (int j = 0; j < n_my; ++j) {
+    const int sb = j % RB, sv = j % RV;
+    const unsigned char* st = ring + (size_t)sb * L.bytes;
+    const T* su = slots + (size_t)sv * Z::slot_elems;
     const T* sw = su + 4 * Z::S;
-    T* su_next = slotv + (b ? 0 : Z::slot_elems);
-    T* sob = so + (b ? Z::out_elems : 0);
-    const int next = tile + G;
-
-    // Next tile: wait for its prefix, start loading its vertex values.  No
-    // barrier here: a thread whose wait timed out skips the loads that depend
-    // on the copy and reports at the tile's barrier below.
-    T pu[3], pw[3];
-    TetRegs<T> tn;
-    int nvu_next = 0;
-    bad = false;
-    if (next < ntiles) {
-      load_tet_regs(blobs + (size_t)next * L.bytes, L, tid, mu0, lam0, tn);
-      if (mbar_wait(&bar[rn], (parity >> rn) & 1u, kWaitCycles)) {
-        pend &= ~(1u << rn);
-        parity ^= 1u << rn;
-        nvu_next = reinterpret_cast<const int4*>(pren)->y;
-      } else {
-        bad = true;
-      }
-      if (tid < nvu_next) {
-        const int v = reinterpret_cast<const int*>(pren + kBlobVtx)[tid];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          pu[c] = io.u[(size_t)c * nv + v];
-          if (Z::KV) pw[c] = io.w[(size_t)c * nv + v];
-        }
-      }
-    }
-    const int4 h = *reinterpret_cast<const int4*>(pre);
-
-    // Phase 1: one tet per thread.
+    T* sob = outs + (Z::OB == 2 ? (j & 1) : 0) * Z::out_elems;
+    const bool ok = mbar_wait_or_abort(&full_b[sb], (j / RB) & 1u, abort_flag, kWaitCycles) &&
+                    mbar_wait_or_abort(&full_v[sv], (j / RV) & 1u, abort_flag, kWaitCycles);
+    // Phase 1: one tet per thread (skipped by a thread whose wait gave up).
+    const int4 h = ok ? *reinterpret_cast<const int4*>(st) : make_int4(0, 0, 0, 0);
+    T fo[4][3], ko[4][3], dgo[4][3];
+    bool good = true;
     if (tid < h.x) {
-      const uchar4 sl4 = reinterpret_cast<const uchar4*>(pre + kBlobSlots)[tid];
+      const uchar4 sl4 = reinterpret_cast<const uchar4*>(st + kBlobSlots)[tid];
       const int sl[4] = {sl4.x, sl4.y, sl4.z, sl4.w};
       T Du[9], Dw[9];
       {
         T x0[3], xa[3];
         ld3(su + 4 * sl[0], x0);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          ld3(su + 4 * sl[j + 1], xa);
+        for (int q = 0; q < 3; ++q) {
+          ld3(su + 4 * sl[q + 1], xa);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) Du[c * 3 + j] = xa[c] - x0[c];
+          for (int c = 0; c < 3; ++c) Du[c * 3 + q] = xa[c] - x0[c];
         }
         if (Z::KV) {
           ld3(sw + 4 * sl[0], x0);
 #pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            ld3(sw + 4 * sl[j + 1], xa);
+          for (int q = 0; q < 3; ++q) {
+            ld3(sw + 4 * sl[q + 1], xa);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) Dw[c * 3 + j] = xa[c] - x0[c];
+            for (int c = 0; c < 3; ++c) Dw[c * 3 + q] = xa[c] - x0[c];
           }
         }
       }
-      T fo[4][3], ko[4][3], dgo[4][3];
-      const bool ok = element_eval<T, MODEL, OPS>(tr.B, tr.V, tr.mu, tr.lam, Du, Dw, fo, ko, dgo);
-      if (!ok) raise_error(err, EBB_ERR_INVERTED, perm[h.z + tid]);
+      T Bm[9];
+      const T* Bs = reinterpret_cast<const T*>(st + L.B);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Bm[i] = Bs[i * TT + tid];
+      const T V = reinterpret_cast<const T*>(st + L.V)[tid];
+      const T mu = L.mu >= 0 ? reinterpret_cast<const T*>(st + L.mu)[tid] : mu0;
+      const T lam = L.lam >= 0 ? reinterpret_cast<const T*>(st + L.lam)[tid] : lam0;
+      good = element_eval<T, MODEL, OPS>(Bm, V, mu, lam, Du, Dw, fo, ko, dgo);
+      if (!good) raise_error(err, EBB_ERR_INVERTED, perm[h.z + tid]);
+    }
+    // With one output buffer, the previous tile's phase 2 must be done with it.
+    if (Z::OB == 1) named_sync_or<TT>(false);
+    if (tid < h.x) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           T v[NF > 0 ? NF : 1];
           int f = 0;
-          if (Z::FO) v[f++] = ok ? fo[a][c] : T(0);
-          if (Z::KV) v[f++] = ok ? ko[a][c] : T(0);
-          if (Z::DG) v[f++] = ok ? dgo[a][c] : T(0);
+          if (Z::FO) v[f++] = good ? fo[a][c] : T(0);
+          if (Z::KV) v[f++] = good ? ko[a][c] : T(0);
+          if (Z::DG) v[f++] = good ? dgo[a][c] : T(0);
           st_out<T, NF>(sob + ((size_t)(a * 3 + c) * (TT + 1) + tid) * NF, v);
         }
       }
     }
-    if (tid < nvu_next) {
-      st3(su_next + 4 * tid, pu);
-      if (Z::KV) st3(su_next + 4 * (Z::S + tid), pw);
-    }
-    if (__syncthreads_or(bad)) goto drain;
-
-    // Ring slot of tile k-1 is free (its phase 2 finished before the barrier):
-    // refill it with the tile kRing-1 ahead.
-    {
-      const int tf = tile + (kRing - 1) * G;
-      if (tf < ntiles) {
-        const int rf = (k + kRing - 1) % kRing;
-        if (tid == 0) {
-          fence_proxy_async_smem();
-          bulk_load(ring + rf * kBlobPrefix, blobs + (size_t)tf * L.bytes, kBlobPrefix, &bar[rf]);
-        }
-        pend |= 1u << rf;
+    if (named_sync_or<TT>(!ok)) {
+      if (tid == 0) {
+        raise_error(err, EBB_ERR_TIMEOUT, blockIdx.x);
+        *abort_flag = 1;
       }
+      return;
     }
+    if (tid == 0) mbar_arrive(&empty_v[sv]);
 
     // Phase 2: one reduction unit per thread: kUnitEntries independent loads.
     {
-      const uint32_t d = reinterpret_cast<const uint32_t*>(pre + kBlobUnits)[tid];
+      const uint32_t d = reinterpret_cast<const uint32_t*>(st + kBlobUnits)[tid];
       const unsigned rem = (d >> 22) & 0xfu;
       T acc[3 * NF];
 #pragma unroll
       for (int o = 0; o < 3 * NF; ++o) acc[o] = T(0);
       if (d & 1u) {
-        const uint4 codes = reinterpret_cast<const uint4*>(pre + kBlobEnt)[tid];
+        const uint4 codes = reinterpret_cast<const uint4*>(st + kBlobEnt)[tid];
         const unsigned cw[4] = {codes.x, codes.y, codes.z, codes.w};
 #pragma unroll
         for (int q = 0; q < kUnitEntries; ++q) {
           const unsigned code = (cw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
-          const int base = (int)(code >> 8) * 3 * (TT + 1) + (int)(code & 255u);
+          if (code != kEntryNone) {
+            const T* p = sob + (size_t)code * NF;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) add_out<T, NF>(sob + ((size_t)base + c * (TT + 1)) * NF, acc + c * NF);
+            for (int c = 0; c < 3; ++c) add_out<T, NF>(p + c * (TT + 1) * NF, acc + c * NF);
+          }
         }
       }
       const unsigned maxrem = __reduce_max_sync(0xffffffffu, rem);
-      for (unsigned st = 1; st <= maxrem; st <<= 1) {
+      for (unsigned stp = 1; stp <= maxrem; stp <<= 1) {
 #pragma unroll
         for (int o = 0; o < 3 * NF; ++o) {
-          const T x = __shfl_down_sync(0xffffffffu, acc[o], st);
-          if (rem >= st) acc[o] += x;
+          const T x = __shfl_down_sync(0xffffffffu, acc[o], stp);
+          if (rem >= stp) acc[o] += x;
         }
       }
       if ((d >> 26) & 1u) {
-        const int v = reinterpret_cast<const int*>(pre + kBlobVtx)[(d >> 14) & 0xffu];
+        const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
           for (int f = 0; f < NF; ++f) atomicAdd(out_field[f] + (size_t)c * nv + v, acc[c * NF + f]);
       }
     }
-    tr = tn;
-    if (next >= ntiles) break;
-    tile = next;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_b[sb]);
   }
-  return;
-
-drain:
-  // A copy did not complete in time: report it and wait (bounded) for the
-  // copies still in flight before the CTA's shared memory goes away.
-  if (tid == 0) raise_error(err, EBB_ERR_TIMEOUT, blockIdx.x);
-#pragma unroll
-  for (int r = 0; r < kRing; ++r)
-    if ((pend >> r) & 1u) mbar_wait(&bar[r], (parity >> r) & 1u, kWaitCycles);
 }
 
 template <typename T, int MODEL, int OPS>
@@ -556,19 +545,19 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
   const Tiles& tl = rel->tiles;
   if (tl.ntiles == 0) return cudaSuccess;
   const BlobLayout& L = layout_of<T>(tl);
-  const size_t smem = TileSmem<T, OPS>::bytes;
+  const size_t smem = TileSmem<T, OPS>::bytes(L);
   using Cfg = TileLaunchCfg<T, MODEL, OPS>;
   if (Cfg::smem != smem) {
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tet_tile_kernel<T, MODEL, OPS>,
-                                                                  kTileTets, smem);
+                                                                  kTileThreads, smem);
     if (e != cudaSuccess) return e;
     Cfg::grid_per_sm = per_sm > 0 ? per_sm : 1;
     Cfg::smem = smem;
   }
   int grid = Cfg::grid_per_sm * sm_count();
   if (grid > tl.ntiles) grid = tl.ntiles;
-  tet_tile_kernel<T, MODEL, OPS><<<grid, kTileTets, smem, stream>>>(tl.ntiles, (int)rel->verts->size,
+  tet_tile_kernel<T, MODEL, OPS><<<grid, kTileThreads, smem, stream>>>(tl.ntiles, (int)rel->verts->size,
                                                                     blob_of<T>(tl), L, rel->tet_perm, mu0, lam0,
                                                                     io, active, rel->ctx->d_err);
   return cudaGetLastError();
