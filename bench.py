@@ -212,6 +212,10 @@ def run_ours(args, rank, world, local_rank):
     f = dm.vertex_field("f", torch.float32)
     Kw = dm.vertex_field("Kw", torch.float32)
     opts = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
+    # The autotuner picks the tile size and reduction variant EBB_REDUCE_AUTO
+    # resolves to (timing the K w map on these fields); untimed set-up.
+    tune = tune_report(abi, abi.ebb_relation_autotune(dm.ctx, dm.tets, "u32", "w32",
+                                                      abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32)))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     nt = m.n_tets
 
@@ -332,7 +336,9 @@ def run_ours(args, rank, world, local_rank):
     traffic = NCU_TRAFFIC["bytes_per_launch"] if kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"] else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
-            "kernel": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV>",
+            "kernel": {"tiled": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV>",
+                       "atomic": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic>",
+                       "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured>"}[tune["reduce"]],
             "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
 
     dm.close()
@@ -342,10 +348,12 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64^3 cube grid, 5 tets/cube (274,625 verts, 1,310,720 tets), NH, "
-                                   "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, tiled scatter",
+                                   "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, reduction variant "
+                                   "and tile size from the autotuner",
                        "n_tets": nt, "n_verts": m.n_verts, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
+            "autotune": tune,
             "reduction_variants": variants,
             "e2e": {"value": nt * args.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -390,6 +398,15 @@ def implicit_steps(dm, m, abi, torch, stream, args):
             "v_rel_diff_mixed_vs_fp64_form": du}
 
 
+REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled"}
+
+
+def tune_report(abi, rep):
+    return {"reduce": REDUCE_NAMES[rep.reduce], "tile_tets": rep.tile_tets,
+            "candidates_kw_map_us": [{"reduce": REDUCE_NAMES[rep.cand[i].reduce], "tile_tets": rep.cand[i].tile_tets,
+                                      "us": rep.cand[i].us} for i in range(rep.ncand)]}
+
+
 def batched_steps(abi, torch, local_rank, args):
     """256 independent cube grids, n log-uniform in [4, 24] (neo-Hookean,
     E = 1e5, nu = 0.45), one implicit step each: the batched call (mixed and
@@ -405,6 +422,11 @@ def batched_steps(abi, torch, local_rank, args):
         uu = dm.vertex_field("u", torch.float64)
         vv = dm.vertex_field("v", torch.float64)
         dm.bind("pinned", torch.from_numpy(b.pinned.astype(np.uint8)).to(uu.device))
+        # tile size and reduction variant of the batch picked by the autotuner
+        dm.vertex_field("tu", torch.float32)
+        dm.vertex_field("tw", torch.float32, value=meshgen.random_field(b.X.shape[0], seed=5))
+        out["autotune"] = tune_report(abi, abi.ebb_relation_autotune(
+            dm.ctx, dm.tets, "tu", "tw", abi.map_opts(abi.EBB_NEOHOOKEAN, mu, lam, precision=abi.EBB_PREC_F32)))
         for name, prec in (("mixed", abi.EBB_PREC_F32), ("fp64", abi.EBB_PREC_F64)):
             prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, mu, lam, precision=prec, rtol=1e-8)
             ts = []

@@ -219,6 +219,42 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
 ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                const char* d_out, const ebb_map_opts_t* opts);
 
+/* ---- autotuner (tile size and reduction variant) ------------------------ */
+/* Section 6.2 fixes one execution mapping (one row per thread, atomic
+ * reductions) and Section 8 leaves schedules and autotuning to future work;
+ * this call picks the mapping of a relation by measurement.  It times the
+ * K w map (the map the implicit step's CG solve runs every iteration) for
+ * opts->model and opts->precision (opts->reduce and opts->flags ignored) on
+ * the caller's vertex fields `u` and `w`, over the candidates: the tiled
+ * variant with tiles of 128, 96 and 64 tets, the atomic variant, and the
+ * coloured variant if the relation was finalized with EBB_FINALIZE_COLOR.
+ * Each candidate: 2 untimed launches, then the median of 7 launches timed
+ * with CUDA events on the context's stream.  Afterwards the relation's tiles
+ * use the fastest tile size (the blobs are rebuilt if it changed) and
+ * EBB_REDUCE_AUTO resolves to the fastest variant for this model and
+ * precision in every map and step on the relation (before any autotune it
+ * resolves to EBB_REDUCE_TILED).  Results are unaffected except for the
+ * order of floating-point additions.  Synchronous; allocates and frees an
+ * output scratch field.  Errors: EBB_ERR_ARG / EBB_ERR_STATE as for the maps;
+ * device errors of the timed maps (EBB_ERR_INVERTED) are returned. */
+#define EBB_AUTOTUNE_MAX_CAND 8
+typedef struct {
+  int32_t reduce;     /* EBB_REDUCE_TILED, _ATOMIC or _COLOR */
+  int32_t tile_tets;  /* tets per tile for EBB_REDUCE_TILED, 0 otherwise */
+  double us;          /* median duration of one K w map, microseconds */
+} ebb_autotune_cand_t;
+
+typedef struct {
+  int32_t reduce;     /* variant EBB_REDUCE_AUTO now selects */
+  int32_t tile_tets;  /* tets per tile of the relation's layout now */
+  int32_t ncand;
+  ebb_autotune_cand_t cand[EBB_AUTOTUNE_MAX_CAND];
+} ebb_autotune_report_t;
+
+ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                   const char* w, const ebb_map_opts_t* opts,
+                                   ebb_autotune_report_t* report);
+
 /* ---- implicit step (Section 7.2, Section 7.3) --------------------------- */
 
 /* One linearised backward-Euler step, in place on the F64 vertex fields

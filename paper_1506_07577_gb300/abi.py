@@ -62,6 +62,18 @@ class ebb_step_params_t(C.Structure):
                 ("rtol", C.c_double), ("fail_on_max_iters", C.c_int32)]
 
 
+EBB_AUTOTUNE_MAX_CAND = 8
+
+
+class ebb_autotune_cand_t(C.Structure):
+    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("us", C.c_double)]
+
+
+class ebb_autotune_report_t(C.Structure):
+    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("ncand", C.c_int32),
+                ("cand", ebb_autotune_cand_t * EBB_AUTOTUNE_MAX_CAND)]
+
+
 class ebb_cg_report_t(C.Structure):
     _fields_ = [("iters", C.c_int32), ("rel_residual", C.c_double), ("status", C.c_int32)]
 
@@ -80,6 +92,8 @@ _SIGS = {
     "ebb_map_tet_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_force_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_relation_autotune": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t),
+                               C.POINTER(ebb_autotune_report_t)], ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_vjp": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ebb_step_params_t),
@@ -191,6 +205,14 @@ def ebb_map_tet_force_Kv(ctx, tets, u, w, f_out, Kw_out, opts):
 
 def ebb_map_tet_diagK(ctx, tets, u, d_out, opts):
     return _check(ctx, _lib.ebb_map_tet_diagK(ctx, tets, _b(u), _b(d_out), C.byref(opts)))
+
+
+def ebb_relation_autotune(ctx, tets, u, w, opts):
+    """Pick the tile size and reduction variant of `tets` by timing the K w
+    map; returns the report (chosen variant, tile size, timed candidates)."""
+    rep = ebb_autotune_report_t()
+    _check(ctx, _lib.ebb_relation_autotune(ctx, tets, _b(u), _b(w), C.byref(opts), C.byref(rep)))
+    return rep
 
 
 def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,

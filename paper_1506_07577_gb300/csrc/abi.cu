@@ -7,6 +7,7 @@
 // maps read.  The phase rule of Section 4.1 is enforced per map call: a
 // field that a map reduces into may not also be read by it.
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -158,6 +159,17 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 }
 
 // Resolve a vertex field used by a map; checks dtype and width.
+// EBB_REDUCE_AUTO: the autotuned variant for this model and precision, else
+// the tiled one.
+ebb_reduce_t resolve_reduce(const ebb_rel_s* tets, ebb_reduce_t r, int model, int precision) {
+  if (r != EBB_REDUCE_AUTO) return r;
+  if ((model == EBB_STVK || model == EBB_NEOHOOKEAN) && (precision == EBB_PREC_F64 || precision == EBB_PREC_F32)) {
+    const int t = tets->tuned[model][precision];
+    if (t >= 0) return (ebb_reduce_t)t;
+  }
+  return EBB_REDUCE_TILED;
+}
+
 ebb_status_t vertex_field(ebb_ctx_s* ctx, ebb_rel_s* tets, const char* name, ebb_dtype_t want, int ncomp,
                           void** out) {
   if (!name) return set_error(ctx, EBB_ERR_ARG, "null field name");
@@ -186,8 +198,7 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
     return set_error(ctx, EBB_ERR_ARG, "unknown material model");
   if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
-  ebb_reduce_t reduce = opts->reduce;
-  if (reduce == EBB_REDUCE_AUTO) reduce = EBB_REDUCE_TILED;
+  const ebb_reduce_t reduce = resolve_reduce(tets, opts->reduce, opts->model, opts->precision);
   if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
@@ -596,6 +607,140 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, con
   return run_map(ctx, tets, mc, OP_DIAG, opts);
 }
 
+ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* w,
+                                   const ebb_map_opts_t* opts, ebb_autotune_report_t* report) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (report) memset(report, 0, sizeof *report);
+  if (!tets || !opts || !u || !w || !report) return set_error(ctx, EBB_ERR_ARG, "null argument");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (opts->model != EBB_STVK && opts->model != EBB_NEOHOOKEAN)
+    return set_error(ctx, EBB_ERR_ARG, "unknown material model");
+  if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
+    return set_error(ctx, EBB_ERR_ARG, "unknown precision");
+  const bool f64 = opts->precision == EBB_PREC_F64;
+  const ebb_dtype_t dt = f64 ? EBB_F64 : EBB_F32;
+  void *pu = nullptr, *pw = nullptr;
+  ebb_status_t s = vertex_field(ctx, tets, u, dt, 3, &pu);
+  if (!s) s = vertex_field(ctx, tets, w, dt, 3, &pw);
+  if (s) return s;
+  s = read_device_error(ctx);
+  if (s) return s;
+  const int nv = (int)tets->verts->size;
+  const size_t bytes = (size_t)nv * 3 * (f64 ? 8 : 4);
+  cudaStream_t st = ctx->stream;
+  void* out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaMalloc(&out, bytes > 0 ? bytes : 16);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  // Reordered vertices: time the map on operands in the internal order.
+  if (ce == cudaSuccess && tets->vperm) {
+    for (int i = 0; i < 2 && ce == cudaSuccess; ++i)
+      if (!tets->vscratch[i]) ce = cudaMalloc(&tets->vscratch[i], (size_t)nv * 3 * 8);
+    if (ce == cudaSuccess)
+      ce = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)pu, (double*)tets->vscratch[0], st)
+               : gather_vertex_field<float>(nv, tets->vperm, (const float*)pu, (float*)tets->vscratch[0], st);
+    if (ce == cudaSuccess)
+      ce = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)pw, (double*)tets->vscratch[1], st)
+               : gather_vertex_field<float>(nv, tets->vperm, (const float*)pw, (float*)tets->vscratch[1], st);
+    pu = tets->vscratch[0];
+    pw = tets->vscratch[1];
+  }
+  auto cleanup = [&]() {
+    cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (ce != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    return set_error(ctx, EBB_ERR_NOMEM, "autotune scratch allocation failed");
+  }
+  // Time one candidate: median of 7 launches after 2 untimed ones.
+  auto time_map = [&](ebb_reduce_t reduce, double* us) -> cudaError_t {
+    std::vector<float> t;
+    for (int it = 0; it < 9; ++it) {
+      cudaError_t e = cudaMemsetAsync(out, 0, bytes, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) {
+        if (f64) {
+          MapIO<double> io;
+          io.u = (const double*)pu;
+          io.w = (const double*)pw;
+          io.Kw = (double*)out;
+          e = launch_tet_map<double>(tets, opts->model, OP_KV, reduce, opts->mu, opts->lambda, io, nullptr, st);
+        } else {
+          MapIO<float> io;
+          io.u = (const float*)pu;
+          io.w = (const float*)pw;
+          io.Kw = (float*)out;
+          e = launch_tet_map<float>(tets, opts->model, OP_KV, reduce, (float)opts->mu, (float)opts->lambda, io,
+                                    nullptr, st);
+        }
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) return e;
+      if (it >= 2) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *us = 1e3 * t[t.size() / 2];
+    return cudaSuccess;
+  };
+  int nc = 0;
+  double best_tiled_us = 1e300, best_us = 1e300;
+  int best_cap = tets->tile_cap;
+  ebb_reduce_t best = EBB_REDUCE_TILED;
+  const int caps[3] = {128, 96, 64};
+  for (int ci = 0; ci < 3 && ce == cudaSuccess; ++ci) {
+    if (tets->tile_cap != caps[ci]) {
+      s = rebuild_tiles(ctx, tets, caps[ci]);
+      if (s) {
+        cleanup();
+        return s;
+      }
+    }
+    double us = 0.0;
+    ce = time_map(EBB_REDUCE_TILED, &us);
+    if (ce != cudaSuccess) break;
+    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], us};
+    if (us < best_tiled_us) {
+      best_tiled_us = us;
+      best_cap = caps[ci];
+    }
+  }
+  const ebb_reduce_t others[2] = {EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR};
+  for (int oi = 0; oi < 2 && ce == cudaSuccess; ++oi) {
+    if (others[oi] == EBB_REDUCE_COLOR && !tets->has_colour) continue;
+    double us = 0.0;
+    ce = time_map(others[oi], &us);
+    if (ce != cudaSuccess) break;
+    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, us};
+    if (us < best_us) {
+      best_us = us;
+      best = others[oi];
+    }
+  }
+  cleanup();
+  if (ce != cudaSuccess) return cuda_check(ctx, ce, "autotune timing");
+  s = read_device_error(ctx);
+  if (s) return s;
+  if (best_tiled_us <= best_us) best = EBB_REDUCE_TILED;
+  if (tets->tile_cap != best_cap) {
+    s = rebuild_tiles(ctx, tets, best_cap);
+    if (s) return s;
+  }
+  tets->tuned[opts->model][opts->precision] = (signed char)best;
+  report->reduce = best;
+  report->tile_tets = tets->tile_cap;
+  report->ncand = nc;
+  return EBB_OK;
+}
+
 ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v, const char* pinned,
                                   const ebb_step_params_t* params, ebb_cg_report_t* report) {
   if (!ctx) return EBB_ERR_ARG;
@@ -614,7 +759,7 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
-  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
+  ebb_reduce_t reduce = resolve_reduce(tets, params->reduce, params->model, params->precision);
   if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
@@ -655,7 +800,7 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
   if (tets->vperm) return set_error(ctx, EBB_ERR_STATE, "the step VJP does not support EBB_FINALIZE_REORDER_VERTS");
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
-  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
+  ebb_reduce_t reduce = resolve_reduce(tets, params->reduce, params->model, params->precision);
   if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
@@ -713,7 +858,7 @@ ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const c
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
-  ebb_reduce_t reduce = params->reduce == EBB_REDUCE_AUTO ? EBB_REDUCE_TILED : params->reduce;
+  ebb_reduce_t reduce = resolve_reduce(tets, params->reduce, params->model, params->precision);
   if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)

@@ -461,12 +461,13 @@ ebb_status_t batch_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, c
   kio.w = mixed ? pe : (const T*)s->p;
   kio.Kw = acc_kp;
   // Capture kChunk iterations once; re-capture when anything baked in changes.
-  std::vector<unsigned char> key(sizeof(BatchConst) + 4 * sizeof(double) + 3 * sizeof(void*));
+  std::vector<unsigned char> key(sizeof(BatchConst) + 5 * sizeof(double) + 3 * sizeof(void*));
   {
     unsigned char* k = key.data();
     memcpy(k, &c, sizeof c);
     k += sizeof c;
-    const double kd[4] = {(double)sizeof(T), (double)prm->model, (double)prm->reduce, prm->mu + 1e-300 * prm->lambda};
+    const double kd[5] = {(double)sizeof(T), (double)prm->model, (double)prm->reduce, prm->mu + 1e-300 * prm->lambda,
+                          (double)tets->layout_gen};
     memcpy(k, kd, sizeof kd);
     k += sizeof kd;
     const void* kp[3] = {pin, kio.u, kio.w};

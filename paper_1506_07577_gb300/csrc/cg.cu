@@ -339,6 +339,7 @@ __global__ void step_finish_kernel(int n, double dt, const double* __restrict__ 
 // of any field re-captures the graph.
 struct ChunkKey {
   int elem_bytes, pin_bytes, model, reduce;
+  unsigned layout_gen;  // tile blobs baked into the captured map launches
   double mu0, lam0;
   StepConst c;
   const void* pin;
@@ -508,6 +509,7 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   key.pin_bytes = (int)sizeof(PT);
   key.model = prm->model;
   key.reduce = prm->reduce;
+  key.layout_gen = tets->layout_gen;
   key.mu0 = prm->mu;
   key.lam0 = prm->lambda;
   key.c = c;

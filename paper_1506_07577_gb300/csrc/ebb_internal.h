@@ -136,6 +136,9 @@ struct ebb_rel_s {
   ebb::Colouring colour;
   bool has_colour = false;
   ebb::Tiles tiles;
+  int tile_cap = ebb::kTileTets;        // tets per tile the layout was cut with
+  unsigned layout_gen = 0;              // bumped whenever the tile blobs are rebuilt
+  signed char tuned[2][2] = {{-1, -1}, {-1, -1}};  // autotuned reduce per [model][precision], -1 none
   ebb::VertexIndex vindex;
 
   // ---- implicit-step scratch ----
@@ -196,6 +199,8 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
 // device-side per-tet streams (layout.cu).
 ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix);
 void free_layout(ebb_rel_s* tets);
+// Re-cut the tiles with at most `cap` tets each and repack the blobs.
+ebb_status_t rebuild_tiles(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap);
 
 // Step VJP (cg.cu) and its adjoint element map (adjoint.cu).
 ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const void* pinned,

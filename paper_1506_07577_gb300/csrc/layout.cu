@@ -159,78 +159,12 @@ __global__ void pack_blob_kernel(int nt, const unsigned char* __restrict__ prefi
   }
 }
 
-}  // namespace
-
-void free_layout(ebb_rel_s* tets) {
-  cudaFree(tets->tiles.blob32);
-  cudaFree(tets->tiles.blob64);
-  tets->tiles = Tiles();
-  cudaFree(tets->vindex.off);
-  cudaFree(tets->vindex.ent);
-  tets->vindex = VertexIndex();
-  cudaFree(tets->tet_perm);
-  tets->tet_perm = nullptr;
-}
-
-ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
-                          const std::vector<double>& X, const std::vector<int>* batch, std::vector<int>& perm,
-                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix) {
-  const int nt = (int)keys.size();
-  const int nv = (int)(X.size() / 3);
-  cudaStream_t st = ctx->stream;
-
-  // 1. Morton order of centroids.
-  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-  for (int c = 0; c < 3; ++c) {
-    if (nv > 0) {
-      auto mm = std::minmax_element(X.begin() + (size_t)c * nv, X.begin() + (size_t)(c + 1) * nv);
-      lo[c] = *mm.first;
-      hi[c] = *mm.second;
-    }
-    if (!(hi[c] > lo[c])) hi[c] = lo[c] + 1.0;
-  }
-  // Sort key: (group id, Morton code of the centroid, row).
-  std::vector<std::tuple<int, uint64_t, int>> code(nt);
-  const double q = (double)((1u << 21) - 1);
-  for (int t = 0; t < nt; ++t) {
-    const int k[4] = {keys[t].x, keys[t].y, keys[t].z, keys[t].w};
-    uint64_t m = 0;
-    for (int c = 0; c < 3; ++c) {
-      double s = 0.0;
-      for (int a = 0; a < 4; ++a) s += X[(size_t)c * nv + k[a]];
-      double r = (0.25 * s - lo[c]) / (hi[c] - lo[c]);
-      r = r < 0 ? 0 : (r > 1 ? 1 : r);
-      m |= spread3((uint64_t)(r * q)) << c;
-    }
-    code[t] = std::make_tuple(batch ? (*batch)[k[0]] : 0, m, t);
-  }
-  std::sort(code.begin(), code.end());
-  perm.resize(nt);
-  sorted.resize(nt);
-  for (int i = 0; i < nt; ++i) {
-    perm[i] = std::get<2>(code[i]);
-    sorted[i] = keys[perm[i]];
-  }
-
-  // 2. Vertex -> (tet, corner) index in internal order.
-  std::vector<int> voff(nv + 1, 0), vent((size_t)4 * nt);
-  for (int i = 0; i < nt; ++i) {
-    voff[sorted[i].x + 1]++;
-    voff[sorted[i].y + 1]++;
-    voff[sorted[i].z + 1]++;
-    voff[sorted[i].w + 1]++;
-  }
-  for (int v = 0; v < nv; ++v) voff[v + 1] += voff[v];
-  {
-    std::vector<int> fill(voff.begin(), voff.end() - 1);
-    for (int i = 0; i < nt; ++i) {
-      const int k[4] = {sorted[i].x, sorted[i].y, sorted[i].z, sorted[i].w};
-      for (int a = 0; a < 4; ++a) vent[fill[k[a]]++] = 4 * i + a;
-    }
-  }
-
-  // 3. Tiles: greedy cut of the Morton order.  A tile closes before it would
-  // exceed kTileTets tets, kTileSlots distinct vertices, kTileTets reduction
+// Cut the internal tet order into tiles of at most `cap` tets and build each
+// tile's blob prefix; returns the tile count.
+int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<unsigned char>& prefix) {
+  const int nt = (int)sorted.size();
+  // Tiles: greedy cut of the Morton order.  A tile closes before it would
+  // exceed `cap` tets, kTileSlots distinct vertices, kTileTets reduction
   // units (ceil(entries / kUnitEntries) summed over its vertices) or
   // kUnitMaxRun units for one vertex.
   std::vector<int> tet_off{0};
@@ -247,7 +181,7 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
         more_units += c % kUnitEntries == 0;
         run_ok = run_ok && (c + 1 + kUnitEntries - 1) / kUnitEntries <= kUnitMaxRun;
       }
-      if (tile_tets == kTileTets || tile_vtx + fresh > kTileSlots || tile_units + more_units > kTileTets ||
+      if (tile_tets == cap || tile_vtx + fresh > kTileSlots || tile_units + more_units > kTileTets ||
           !run_ok) {
         tet_off.push_back(i);
         ++tile;
@@ -268,7 +202,7 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
   }
   const int ntiles = (int)tet_off.size() - 1;
 
-  // 4. Blob prefix per tile: slots (numbered by decreasing entry count), the
+  // Blob prefix per tile: slots (numbered by decreasing entry count), the
   // entries grouped by slot, the reduction units and the vertex ids.
   prefix.assign((size_t)ntiles * kBlobPrefix, 0);
   {
@@ -358,6 +292,81 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     }
   }
 
+  return ntiles;
+}
+
+}  // namespace
+
+void free_layout(ebb_rel_s* tets) {
+  cudaFree(tets->tiles.blob32);
+  cudaFree(tets->tiles.blob64);
+  tets->tiles = Tiles();
+  cudaFree(tets->vindex.off);
+  cudaFree(tets->vindex.ent);
+  tets->vindex = VertexIndex();
+  cudaFree(tets->tet_perm);
+  tets->tet_perm = nullptr;
+}
+
+ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
+                          const std::vector<double>& X, const std::vector<int>* batch, std::vector<int>& perm,
+                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix) {
+  const int nt = (int)keys.size();
+  const int nv = (int)(X.size() / 3);
+  cudaStream_t st = ctx->stream;
+
+  // 1. Morton order of centroids.
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  for (int c = 0; c < 3; ++c) {
+    if (nv > 0) {
+      auto mm = std::minmax_element(X.begin() + (size_t)c * nv, X.begin() + (size_t)(c + 1) * nv);
+      lo[c] = *mm.first;
+      hi[c] = *mm.second;
+    }
+    if (!(hi[c] > lo[c])) hi[c] = lo[c] + 1.0;
+  }
+  // Sort key: (group id, Morton code of the centroid, row).
+  std::vector<std::tuple<int, uint64_t, int>> code(nt);
+  const double q = (double)((1u << 21) - 1);
+  for (int t = 0; t < nt; ++t) {
+    const int k[4] = {keys[t].x, keys[t].y, keys[t].z, keys[t].w};
+    uint64_t m = 0;
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int a = 0; a < 4; ++a) s += X[(size_t)c * nv + k[a]];
+      double r = (0.25 * s - lo[c]) / (hi[c] - lo[c]);
+      r = r < 0 ? 0 : (r > 1 ? 1 : r);
+      m |= spread3((uint64_t)(r * q)) << c;
+    }
+    code[t] = std::make_tuple(batch ? (*batch)[k[0]] : 0, m, t);
+  }
+  std::sort(code.begin(), code.end());
+  perm.resize(nt);
+  sorted.resize(nt);
+  for (int i = 0; i < nt; ++i) {
+    perm[i] = std::get<2>(code[i]);
+    sorted[i] = keys[perm[i]];
+  }
+
+  // 2. Vertex -> (tet, corner) index in internal order.
+  std::vector<int> voff(nv + 1, 0), vent((size_t)4 * nt);
+  for (int i = 0; i < nt; ++i) {
+    voff[sorted[i].x + 1]++;
+    voff[sorted[i].y + 1]++;
+    voff[sorted[i].z + 1]++;
+    voff[sorted[i].w + 1]++;
+  }
+  for (int v = 0; v < nv; ++v) voff[v + 1] += voff[v];
+  {
+    std::vector<int> fill(voff.begin(), voff.end() - 1);
+    for (int i = 0; i < nt; ++i) {
+      const int k[4] = {sorted[i].x, sorted[i].y, sorted[i].z, sorted[i].w};
+      for (int a = 0; a < 4; ++a) vent[fill[k[a]]++] = 4 * i + a;
+    }
+  }
+
+  const int ntiles = tile_prefix(sorted, nv, tets->tile_cap, prefix);
+
   cudaError_t e = upload(&tets->vindex.off, voff, st);
   if (e == cudaSuccess) e = upload(&tets->vindex.ent, vent, st);
   if (e == cudaSuccess) e = upload(&tets->tet_perm, perm, st);
@@ -369,6 +378,26 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
   }
   tets->tiles.ntiles = ntiles;
   return EBB_OK;
+}
+
+ebb_status_t rebuild_tiles(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap) {
+  if (cap < 1 || cap > kTileTets) return set_error(ctx, EBB_ERR_ARG, "tile size out of range");
+  const int nt = (int)tets->size;
+  const int nv = (int)tets->verts->size;
+  std::vector<int4> sorted(nt);
+  cudaError_t e = cudaSuccess;
+  if (nt > 0) e = cudaMemcpyAsync(sorted.data(), tets->keys, sizeof(int4) * nt, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "reading internal keys");
+  std::vector<unsigned char> prefix;
+  const int ntiles = tile_prefix(sorted, nv, cap, prefix);
+  cudaFree(tets->tiles.blob32);
+  cudaFree(tets->tiles.blob64);
+  tets->tiles = Tiles();
+  tets->tiles.ntiles = ntiles;
+  tets->tile_cap = cap;
+  ++tets->layout_gen;
+  return build_tile_blobs(ctx, tets, prefix);
 }
 
 ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix) {

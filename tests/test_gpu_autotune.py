@@ -1,0 +1,82 @@
+"""The autotuner (ebb_relation_autotune): it times every candidate, leaves the
+relation on the fastest tile size, and the maps and the implicit step still
+match the oracle afterwards (through EBB_REDUCE_AUTO and explicit variants)."""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+from oracle import fem, implicit
+from _problems import oracle_maps, problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _abi():
+    from paper_1506_07577_gb300 import abi
+    return abi
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_autotune_report_and_parity(prec):
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(7, "nh", seed=21)
+    f, Kw, d = oracle_maps(m, mu, lam, u, w, "nh")
+    dt = torch.float32 if prec == "f32" else torch.float64
+    p = abi.EBB_PREC_F32 if prec == "f32" else abi.EBB_PREC_F64
+    with DeviceTetMesh(m.X, m.tets, mu, lam, colour=True) as dm:
+        dm.vertex_field("u", dt, value=u)
+        dm.vertex_field("w", dt, value=w)
+        rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(abi.EBB_NEOHOOKEAN, precision=p))
+        cands = [(rep.cand[i].reduce, rep.cand[i].tile_tets, rep.cand[i].us) for i in range(rep.ncand)]
+        assert rep.ncand == 5  # tiled x3, atomic, colour
+        assert {c[1] for c in cands if c[0] == abi.EBB_REDUCE_TILED} == {128, 96, 64}
+        assert all(c[2] > 0 for c in cands)
+        best = min(cands, key=lambda c: c[2])
+        assert rep.reduce == best[0]
+        tiled = [c for c in cands if c[0] == abi.EBB_REDUCE_TILED]
+        assert rep.tile_tets == min(tiled, key=lambda c: c[2])[1]
+        tol = 1e-12 if prec == "f64" else 1e-5
+        out = {k: dm.vertex_field(k, dt) for k in ("f", "Kw", "d")}
+        for red in (abi.EBB_REDUCE_AUTO, abi.EBB_REDUCE_TILED):
+            o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=p, reduce=red, flags=abi.EBB_MAP_ZERO_OUT)
+            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "Kw", o)
+            abi.ebb_map_tet_diagK(dm.ctx, dm.tets, "u", "d", o)
+            abi.ebb_ctx_sync(dm.ctx)
+            got = {k: v.double().cpu().numpy().T for k, v in out.items()}
+            assert rel_err(got["f"], f) < tol
+            assert rel_err(got["Kw"], Kw) < tol
+            assert rel_err(got["d"], d) < tol
+
+
+def test_step_after_retiling_matches_oracle():
+    """A step captured before the autotuner re-cuts the tiles is re-captured
+    afterwards (the layout generation is part of the graph key)."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m = meshgen.cube_grid(5, jitter=0.01, seed=3)
+    mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+    B, V = fem.rest_shape(m.X, m.tets)
+    mass = fem.lumped_mass(V, m.tets, 1000.0, m.n_verts)
+    uo, vo = np.zeros_like(m.X), np.zeros_like(m.X)
+    for _ in range(3):
+        uo, vo, _ = implicit.implicit_step(m.X, uo, vo, m.tets, B, V, mass, mu, lam, fem.STVK, 1e-3,
+                                           np.array([0, 0, -9.81]), m.pinned, 400, 1e-12)
+    with DeviceTetMesh(m.X, m.tets) as dm:
+        uu = dm.vertex_field("u", torch.float64)
+        vv = dm.vertex_field("v", torch.float64)
+        dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(dm.device))
+        dm.vertex_field("pu", torch.float64, value=0.01 * meshgen.random_field(m.n_verts, seed=1))
+        dm.vertex_field("pw", torch.float64, value=meshgen.random_field(m.n_verts, seed=2))
+        prm = abi.step_params(abi.EBB_STVK, 1e-3, 1000.0, mu, lam, max_iters=400, rtol=1e-12)
+        abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm)
+        gen_tiles = abi.ebb_relation_autotune(dm.ctx, dm.tets, "pu", "pw", abi.map_opts(abi.EBB_STVK, mu, lam))
+        assert gen_tiles.tile_tets in (128, 96, 64)
+        # the candidates were timed on re-cut tiles (and the winner re-cut once
+        # more unless it was the last one tried), so the blobs the first
+        # step's graph captured are gone
+        for _ in range(2):
+            abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm)
+        assert rel_err(vv.cpu().numpy().T, vo) < 1e-10
+        assert rel_err(uu.cpu().numpy().T, uo) < 1e-10
