@@ -16,6 +16,7 @@
 // Scalars never leave the device inside the loop; the host reads one status
 // word per batch of iterations.  CG vectors, dots and updates are FP64 in
 // both precisions; the element maps run in the element precision T.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -40,8 +41,9 @@ struct CgScalars {
   double alpha, beta;
   int active[2];     // iteration with parity s runs iff active[s]
   int iter;          // iterations completed
-  int status;        // EBB_OK or EBB_ERR_CG_BREAKDOWN
+  int status;        // EBB_OK, EBB_ERR_CG_BREAKDOWN or EBB_ERR_TIMEOUT
   unsigned count[3];
+  unsigned bar_count, bar_gen;   // grid barrier of the fused iteration kernel
 };
 
 template <typename PT>
@@ -186,87 +188,230 @@ cg_init_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict
   }
 }
 
-// p.Ap over free rows (Ap = M p + dt^2 K p); alpha = r.z / p.Ap.
-template <typename T, typename PT>
-__global__ void __launch_bounds__(kVecThreads)
-cg_pq_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
-             const double* __restrict__ p, const T* __restrict__ acc_kp, double* part, CgScalars* sc) {
-  if (!sc->active[s]) return;
-  const int n = 3 * c.nv;
-  const double dt2 = c.dt * c.dt;
-  double pq = 0.0, zero = 0.0;
-#pragma unroll 4
-  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
-    const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
-    const int vtx = i - comp * c.nv;
-    if (is_pinned(pin, vtx)) continue;
-    const double pi = p[i];
-    pq += pi * (mass[vtx] * pi + dt2 * (double)acc_kp[i]);
-  }
-  if (reduce_last(pq, zero, part, &sc->count[1]) && threadIdx.x == 0) {
-    if (pq > 0.0) {
-      sc->alpha = sc->rz[s] / pq;
+// Grid-wide barrier of a cooperative launch (every block co-resident).  The
+// last block to arrive resets the counter and advances the generation the
+// others spin on.  Bounded: returns false if the barrier did not complete
+// within `limit` SM cycles.
+__device__ bool grid_sync(unsigned* count, unsigned* gen, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      *count = 0u;
+      __threadfence();
+      atomicExch(gen, g + 1u);
     } else {
-      sc->alpha = 0.0;
-      sc->status = EBB_ERR_CG_BREAKDOWN;
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > limit) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
     }
+    __threadfence();
+    s_ok = ok;
   }
+  __syncthreads();
+  return s_ok != 0;
 }
 
-// y += alpha p; r -= alpha Ap; then r.z and r.r, beta, and whether the next
-// iteration runs.
+// Sum of part[0..n) (stride `stride`, offset `off`) in a fixed order: the
+// same in every block, so every block obtains the same value.
+__device__ __forceinline__ double sum_partials(const double* part, int n, int stride, int off) {
+  double x = 0.0, zero = 0.0;
+  for (int i = threadIdx.x; i < n; i += kVecThreads) x += __ldcg(part + (size_t)stride * i + off);
+  block_sum2(x, zero);
+  __shared__ double s_tot;
+  if (threadIdx.x == 0) s_tot = x;
+  __syncthreads();
+  const double t = s_tot;
+  __syncthreads();
+  return t;
+}
+
+constexpr long long kGridWaitCycles = 2000000000LL;  // about 1 s at 2 GHz
+
+// dt^2 times a K p entry, in FP64: in the element precision first when that
+// is FP32 (K p carries FP32 accuracy either way), saving an FP64 multiply.
+__device__ __forceinline__ double dt2_times(float kp, double dt2) { return (double)((float)dt2 * kp); }
+__device__ __forceinline__ double dt2_times(double kp, double dt2) { return dt2 * kp; }
+
+// One CG iteration after the K p map, in one cooperative launch (the three
+// vector passes of the iteration separated by grid barriers, instead of
+// three launches with last-block reductions):
+//   A  q = Ap = M p + dt^2 K p (kept in qz); p.Ap    -> alpha = r.z / p.Ap
+//   B  y += alpha p; r -= alpha q; z = r / diag A (kept in qz); r.z, r.r
+//                                                      -> beta, next active
+//   C  p = z + beta p; K p accumulator cleared
+// On GB300 FP64 arithmetic runs at a small fraction of the FP32 rate and
+// bounds these passes, so each FP64 quantity is formed once (about eight
+// FP64 operations per free row and iteration) and q, z go through memory.
+// Each pass walks vertices (grid-stride, the same vertices per thread in
+// every pass), loading all three components at once; pinned rows keep
+// r = p = 0 and are skipped.  Every block sums the per-block partials of a
+// pass in the same fixed order (deterministic, identical in every block);
+// block 0 publishes the scalars.  A barrier that does not complete sets
+// EBB_ERR_TIMEOUT in the CG status.
 template <typename T, typename PT>
 __global__ void __launch_bounds__(kVecThreads)
-cg_update_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
-                 const double* __restrict__ p, const T* __restrict__ acc_kp, const double* __restrict__ dinv,
-                 double* r, double* y, double* part, CgScalars* sc) {
-  if (!sc->active[s] || sc->status != EBB_OK) return;
-  const double alpha = sc->alpha;
-  const int n = 3 * c.nv;
-  const double dt2 = c.dt * c.dt;
-  double rz = 0.0, rr = 0.0;
-#pragma unroll 4
-  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
-    const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
-    const int vtx = i - comp * c.nv;
-    if (is_pinned(pin, vtx)) continue;
-    const double pi = p[i];
-    const double q = mass[vtx] * pi + dt2 * (double)acc_kp[i];
-    y[i] += alpha * pi;
-    const double ri = r[i] - alpha * q;
-    r[i] = ri;
-    rz += ri * (ri * dinv[i]);
-    rr += ri * ri;
-  }
-  if (reduce_last(rz, rr, part, &sc->count[2]) && threadIdx.x == 0) {
-    const int it = sc->iter + 1;
-    sc->iter = it;
-    sc->beta = rz / sc->rz[s];
-    sc->rz[s ^ 1] = rz;
-    sc->rr = rr;
-    sc->active[s ^ 1] = (it < c.max_iters && sqrt(rr) > c.rtol * sqrt(sc->bb)) ? 1 : 0;
-  }
-}
-
-// p = z + beta p (z = r / diag A); clear the K p accumulator.  Propagates
-// "inactive" to the next parity when this iteration did not run.
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads)
-cg_pupdate_kernel(StepConst c, int s, const double* __restrict__ r, const double* __restrict__ dinv, double* p,
-                  T* pe, T* acc_kp, CgScalars* sc) {
+cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
+               double* __restrict__ p, T* __restrict__ acc_kp, const double* __restrict__ dinv,
+               double* __restrict__ r, double* __restrict__ y, double* __restrict__ qz, T* __restrict__ pe,
+               double* __restrict__ part_a, double* __restrict__ part_b, CgScalars* sc) {
   if (!sc->active[s] || sc->status != EBB_OK) {
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->active[s ^ 1] = 0;
     return;
   }
-  const double beta = sc->beta;
-  const int n = 3 * c.nv;
-#pragma unroll 4
-  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
-    const double pi = r[i] * dinv[i] + beta * p[i];
-    p[i] = pi;
-    if (pe) pe[i] = (T)pi;
-    acc_kp[i] = T(0);
+  const int nv = c.nv;
+  const int stride = gridDim.x * kVecThreads;
+  const int v0 = blockIdx.x * kVecThreads + threadIdx.x;
+  const double dt2 = c.dt * c.dt;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+
+  // A: q = Ap and p.Ap
+  double pq = 0.0, zero = 0.0;
+  for (int v = v0; v < nv; v += stride) {
+    if (is_pinned(pin, v)) continue;
+    const double m = mass[v];
+    double pv[3];
+    T kv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      pv[k] = p[(size_t)k * nv + v];
+      kv[k] = acc_kp[(size_t)k * nv + v];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double q = fma(m, pv[k], dt2_times(kv[k], dt2));
+      qz[(size_t)k * nv + v] = q;
+      pq = fma(pv[k], q, pq);
+    }
   }
+  block_sum2(pq, zero);
+  if (threadIdx.x == 0) part_a[blockIdx.x] = pq;
+  if (!grid_sync(&sc->bar_count, &sc->bar_gen, kGridWaitCycles)) {
+    if (threadIdx.x == 0) atomicCAS(&sc->status, EBB_OK, EBB_ERR_TIMEOUT);
+    return;
+  }
+  pq = sum_partials(part_a, gridDim.x, 1, 0);
+  const double rz_old = sc->rz[s];
+  if (!(pq > 0.0)) {
+    if (lead) {
+      sc->alpha = 0.0;
+      sc->status = EBB_ERR_CG_BREAKDOWN;
+      sc->active[s ^ 1] = 0;
+    }
+    return;
+  }
+  const double alpha = rz_old / pq;
+  if (lead) sc->alpha = alpha;
+
+  // B: y, r, z and the dots r.z, r.r
+  double rz = 0.0, rr = 0.0;
+  for (int v = v0; v < nv; v += stride) {
+    if (is_pinned(pin, v)) continue;
+    double pv[3], qv[3], rv[3], yv[3], dv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const size_t i = (size_t)k * nv + v;
+      pv[k] = p[i];
+      qv[k] = qz[i];
+      rv[k] = r[i];
+      yv[k] = y[i];
+      dv[k] = dinv[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const size_t i = (size_t)k * nv + v;
+      y[i] = fma(alpha, pv[k], yv[k]);
+      const double ri = fma(-alpha, qv[k], rv[k]);
+      const double zi = ri * dv[k];
+      r[i] = ri;
+      qz[i] = zi;
+      rz = fma(ri, zi, rz);
+      rr = fma(ri, ri, rr);
+    }
+  }
+  block_sum2(rz, rr);
+  if (threadIdx.x == 0) {
+    part_b[2 * blockIdx.x] = rz;
+    part_b[2 * blockIdx.x + 1] = rr;
+  }
+  if (!grid_sync(&sc->bar_count, &sc->bar_gen, kGridWaitCycles)) {
+    if (threadIdx.x == 0) atomicCAS(&sc->status, EBB_OK, EBB_ERR_TIMEOUT);
+    return;
+  }
+  rz = sum_partials(part_b, gridDim.x, 2, 0);
+  rr = sum_partials(part_b, gridDim.x, 2, 1);
+  const double beta = rz / rz_old;
+  if (lead) {
+    const int it = sc->iter + 1;
+    sc->iter = it;
+    sc->beta = beta;
+    sc->rz[s ^ 1] = rz;
+    sc->rr = rr;
+    sc->active[s ^ 1] = (it < c.max_iters && sqrt(rr) > c.rtol * sqrt(sc->bb)) ? 1 : 0;
+  }
+
+  // C: p = z + beta p
+  for (int v = v0; v < nv; v += stride) {
+    const bool pinned = is_pinned(pin, v);
+    double zv[3], pv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const size_t i = (size_t)k * nv + v;
+      zv[k] = pinned ? 0.0 : qz[i];
+      pv[k] = pinned ? 0.0 : p[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const size_t i = (size_t)k * nv + v;
+      const double pi = pinned ? 0.0 : fma(beta, pv[k], zv[k]);
+      p[i] = pi;
+      if (pe) pe[i] = (T)pi;
+      acc_kp[i] = T(0);
+    }
+  }
+}
+
+// Blocks of cg_iter_kernel: all co-resident (a cooperative launch), at most
+// kVecBlocks (the size of the partial-sum arrays).
+template <typename T, typename PT>
+int iter_grid() {
+  static int g = 0;
+  if (g == 0) {
+    int per_sm = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_iter_kernel<T, PT>, kVecThreads, 0);
+    g = std::min(kVecBlocks, std::min(per_sm, 2) * std::max(nsm, 1));
+    if (g < 1) g = 1;
+  }
+  return g;
+}
+
+template <typename T, typename PT>
+cudaError_t launch_cg_iter(int grid, cudaStream_t st, StepConst c, int s, const PT* pin, const double* mass,
+                           double* p, T* acc_kp, const double* dinv, double* r, double* y, double* qz, T* pe,
+                           double* part_a, double* part_b, CgScalars* sc) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kVecThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, cg_iter_kernel<T, PT>, c, s, pin, mass, p, acc_kp, dinv, r, y, qz, pe, part_a,
+                            part_b, sc);
 }
 
 // Adjoint solve set-up: b = dL/dv' + dt dL/du' (0 on pinned rows); r = b;
@@ -357,6 +502,7 @@ struct StepScratch {
   void* ue = nullptr;                                    // element-precision displacement
   void* pe = nullptr;                                    // element-precision v, then p
   double *r = nullptr, *p = nullptr, *y = nullptr, *dinv = nullptr, *mass = nullptr;
+  double* qz = nullptr;     // Ap, then z = r / diag A, within one CG iteration
   double* part = nullptr;   // 2 sets of kVecBlocks pairs
   CgScalars* sc = nullptr;
   CgScalars* h_sc = nullptr;
@@ -376,6 +522,7 @@ void free_step_scratch(ebb_rel_s* rel) {
   cudaFree(s->p);
   cudaFree(s->y);
   cudaFree(s->dinv);
+  cudaFree(s->qz);
   cudaFree(s->mass);
   cudaFree(s->part);
   cudaFree(s->sc);
@@ -418,6 +565,7 @@ ebb_status_t ensure_scratch(ebb_ctx_s* ctx, ebb_rel_s* tets) {
   if (e == cudaSuccess) e = cudaMalloc(&s->p, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->y, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->dinv, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->qz, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->mass, (size_t)nv * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->part, 4 * kVecBlocks * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->sc, sizeof(CgScalars));
@@ -525,12 +673,9 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
     for (int k = 0; k < kChunk && le == cudaSuccess; ++k) {
       const int par = k & 1;
       le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
-      cg_pq_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, part_a, s->sc);
-      cg_update_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, pin, s->mass, s->p, acc_kp, s->dinv,
-                                                                   s->r, s->y, part_b, s->sc);
-      cg_pupdate_kernel<T><<<kVecBlocks, kVecThreads, 0, st>>>(c, par, s->r, s->dinv, s->p, mixed ? pe : nullptr,
-                                                               acc_kp, s->sc);
-      if (le == cudaSuccess) le = cudaGetLastError();
+      if (le == cudaSuccess)
+        le = launch_cg_iter<T, PT>(iter_grid<T, PT>(), st, c, par, pin, s->mass, s->p, acc_kp, s->dinv, s->r, s->y,
+                                   s->qz, mixed ? pe : nullptr, part_a, part_b, s->sc);
     }
     if (le == cudaSuccess) le = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
     cudaGraph_t g = nullptr;

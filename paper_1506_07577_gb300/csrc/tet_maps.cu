@@ -318,9 +318,11 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
           break;
         }
         if (lane == 0) {
+          // Blobs are read once per map: evict them first, so that the
+          // vertex fields and the CG vectors stay in L2.
           fence_proxy_async_smem();
-          bulk_load(ring + (size_t)sb * L.bytes, blobs + (size_t)((int)blockIdx.x + j * G) * L.bytes, L.copy,
-                    &full_b[sb]);
+          bulk_load_hint(ring + (size_t)sb * L.bytes, blobs + (size_t)((int)blockIdx.x + j * G) * L.bytes, L.copy,
+                         &full_b[sb], make_policy_evict_first());
         }
         pend |= 1u << sb;
         pend_parity = (pend_parity & ~(1u << sb)) | (((unsigned)(j / RB) & 1u) << sb);

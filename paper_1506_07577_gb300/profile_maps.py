@@ -19,6 +19,7 @@ if ROOT not in sys.path:
 
 
 def main(argv=None):
+    import numpy as np
     import torch
 
     import meshgen
@@ -28,7 +29,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--variant", choices=["atomic", "tiled", "colour"], default="tiled")
-    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag"], default="fused")
+    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step"], default="fused")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
     ap.add_argument("--permute", action="store_true")
@@ -40,16 +41,25 @@ def main(argv=None):
     u = meshgen.random_displacement(m.X, a.n, amp=0.05, seed=2, smooth=0.01)
     w = meshgen.random_field(m.n_verts, seed=2)
     dt = torch.float32 if a.prec == "f32" else torch.float64
+    mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED, "colour": abi.EBB_REDUCE_COLOR}[a.variant]
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=(a.variant == "colour")) as dm:
         dm.vertex_field("u", dt, value=u)
         dm.vertex_field("w", dt, value=w)
         dm.vertex_field("f", dt)
         dm.vertex_field("k", dt)
-        mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
         o = abi.map_opts(mdl, precision=abi.EBB_PREC_F32 if a.prec == "f32" else abi.EBB_PREC_F64, reduce=red,
                          flags=abi.EBB_MAP_ZERO_OUT)
-        for _ in range(a.iters):
+        if a.ops == "step":
+            # implicit steps (dt 1e-3, rho 1000, rtol 1e-8) from rest, pinned bottom face
+            dm.vertex_field("uu", torch.float64)
+            dm.vertex_field("vv", torch.float64)
+            dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(dm.device))
+            prm = abi.step_params(mdl, 1e-3, 1000.0, precision=abi.EBB_PREC_F32 if a.prec == "f32" else abi.EBB_PREC_F64,
+                                  reduce=red, rtol=1e-8)
+            for _ in range(a.iters):
+                abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "uu", "vv", "pinned", prm)
+        for _ in range(a.iters if a.ops != "step" else 0):
             if a.ops == "fused":
                 abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
             elif a.ops == "kv":
