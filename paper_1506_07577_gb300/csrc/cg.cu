@@ -221,18 +221,39 @@ __device__ bool grid_sync(unsigned* count, unsigned* gen, long long limit) {
   return s_ok != 0;
 }
 
-// Sum of part[0..n) (stride `stride`, offset `off`) in a fixed order: the
-// same in every block, so every block obtains the same value.
-__device__ __forceinline__ double sum_partials(const double* part, int n, int stride, int off) {
-  double x = 0.0, zero = 0.0;
-  for (int i = threadIdx.x; i < n; i += kVecThreads) x += __ldcg(part + (size_t)stride * i + off);
-  block_sum2(x, zero);
-  __shared__ double s_tot;
-  if (threadIdx.x == 0) s_tot = x;
+// FP64 is slow on GB300, so the iteration kernel's reductions keep FP64 adds
+// few: values go through shared memory and one warp adds them (kVecThreads/32
+// per lane, then a 5-level shuffle tree), instead of a shuffle tree in every
+// warp.  Block sum of (a, b), fixed order; result in thread 0.
+__device__ __forceinline__ void block_sum2_w0(double& a, double& b) {
+  __shared__ double sa[kVecThreads], sb[kVecThreads];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
   __syncthreads();
-  const double t = s_tot;
+  if (threadIdx.x < 32) {
+    double x = 0.0, y = 0.0;
+#pragma unroll
+    for (int i = 0; i < kVecThreads / 32; ++i) {
+      x += sa[threadIdx.x + 32 * i];
+      y += sb[threadIdx.x + 32 * i];
+    }
+    a = warp_sum(x);
+    b = warp_sum(y);
+  }
   __syncthreads();
-  return t;
+}
+
+// Sums of part[stride*i + 0] and part[stride*i + 1] (the latter only when
+// stride is 2) over i < n, in a fixed order, by warp 0: the same in every
+// block, so every block obtains the same values.  Result in lane 0 of warp 0.
+__device__ __forceinline__ void sum_partials_w0(const double* part, int n, int stride, double& a, double& b) {
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) {
+    x += __ldcg(part + (size_t)stride * i);
+    if (stride == 2) y += __ldcg(part + (size_t)stride * i + 1);
+  }
+  a = warp_sum(x);
+  b = warp_sum(y);
 }
 
 constexpr long long kGridWaitCycles = 2000000000LL;  // about 1 s at 2 GHz
@@ -293,14 +314,24 @@ cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __r
       pq = fma(pv[k], q, pq);
     }
   }
-  block_sum2(pq, zero);
+  __shared__ double s_scal[2];
+  block_sum2_w0(pq, zero);
   if (threadIdx.x == 0) part_a[blockIdx.x] = pq;
   if (!grid_sync(&sc->bar_count, &sc->bar_gen, kGridWaitCycles)) {
     if (threadIdx.x == 0) atomicCAS(&sc->status, EBB_OK, EBB_ERR_TIMEOUT);
     return;
   }
-  pq = sum_partials(part_a, gridDim.x, 1, 0);
   const double rz_old = sc->rz[s];
+  if (threadIdx.x < 32) {
+    sum_partials_w0(part_a, gridDim.x, 1, pq, zero);
+    if (threadIdx.x == 0) {
+      s_scal[0] = pq;
+      s_scal[1] = pq > 0.0 ? rz_old / pq : 0.0;
+    }
+  }
+  __syncthreads();
+  pq = s_scal[0];
+  const double alpha = s_scal[1];
   if (!(pq > 0.0)) {
     if (lead) {
       sc->alpha = 0.0;
@@ -309,7 +340,6 @@ cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __r
     }
     return;
   }
-  const double alpha = rz_old / pq;
   if (lead) sc->alpha = alpha;
 
   // B: y, r, z and the dots r.z, r.r
@@ -338,7 +368,7 @@ cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __r
       rr = fma(ri, ri, rr);
     }
   }
-  block_sum2(rz, rr);
+  block_sum2_w0(rz, rr);
   if (threadIdx.x == 0) {
     part_b[2 * blockIdx.x] = rz;
     part_b[2 * blockIdx.x + 1] = rr;
@@ -347,9 +377,13 @@ cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __r
     if (threadIdx.x == 0) atomicCAS(&sc->status, EBB_OK, EBB_ERR_TIMEOUT);
     return;
   }
-  rz = sum_partials(part_b, gridDim.x, 2, 0);
-  rr = sum_partials(part_b, gridDim.x, 2, 1);
-  const double beta = rz / rz_old;
+  __shared__ double s_beta;
+  if (threadIdx.x < 32) {
+    sum_partials_w0(part_b, gridDim.x, 2, rz, rr);
+    if (threadIdx.x == 0) s_beta = rz / rz_old;
+  }
+  __syncthreads();
+  const double beta = s_beta;
   if (lead) {
     const int it = sc->iter + 1;
     sc->iter = it;
