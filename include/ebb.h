@@ -108,6 +108,13 @@ typedef enum {
 
 /* map flags */
 #define EBB_MAP_ZERO_OUT      1u  /* zero the output fields before reducing into them */
+/* Testing (failure detection): the tiled map skips the bulk copy of tile 0
+ * and shortens its bounded waits to about 1 ms, so the CTA that owns tile 0
+ * gives up waiting, reports EBB_ERR_TIMEOUT through the device status word
+ * (returned by the next synchronising call) and drains its copies; the
+ * call's outputs are incomplete and the context stays usable.  Requires
+ * EBB_REDUCE_TILED (or AUTO resolving to it), else EBB_ERR_ARG. */
+#define EBB_MAP_TEST_DROP_TILE 0x80000000u
 
 typedef struct {
   ebb_model_t model;

@@ -42,6 +42,7 @@ EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED = 0, 1, 2
 EBB_FINALIZE_COLOR = 1
 EBB_FINALIZE_REORDER_VERTS = 2
 EBB_MAP_ZERO_OUT = 1
+EBB_MAP_TEST_DROP_TILE = 0x80000000
 EBB_NOALLOC_MAX_VERTS = 4096
 EBB_NOALLOC_MAX_TETS = 24576
 

@@ -228,6 +228,9 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
       if (ranges_overlap(out[i], bytes, out[j], bytes))
         return set_error(ctx, EBB_ERR_PHASE, "two reduce targets of one map overlap");
   }
+  const bool drop = (opts->flags & EBB_MAP_TEST_DROP_TILE) != 0;
+  if (drop && reduce != EBB_REDUCE_TILED)
+    return set_error(ctx, EBB_ERR_ARG, "EBB_MAP_TEST_DROP_TILE needs the tiled reduction");
   if (opts->flags & EBB_MAP_ZERO_OUT) {
     for (int i = 0; i < mc.nout; ++i) {
       ebb_status_t s = cuda_check(ctx, cudaMemsetAsync(out[i], 0, bytes, ctx->stream), "zeroing output");
@@ -266,7 +269,9 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
     if (ops & OP_FORCE) io.f = (double*)out[oi++];
     if (ops & OP_KV) io.Kw = (double*)out[oi++];
     if (ops & OP_DIAG) io.d = (double*)out[oi++];
+    tets->test_drop_tile = drop ? 0 : -1;
     e = launch_tet_map<double>(tets, opts->model, ops, reduce, opts->mu, opts->lambda, io, nullptr, ctx->stream);
+    tets->test_drop_tile = -1;
   } else {
     MapIO<float> io;
     io.u = (const float*)in[0];
@@ -274,8 +279,10 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
     if (ops & OP_FORCE) io.f = (float*)out[oi++];
     if (ops & OP_KV) io.Kw = (float*)out[oi++];
     if (ops & OP_DIAG) io.d = (float*)out[oi++];
+    tets->test_drop_tile = drop ? 0 : -1;
     e = launch_tet_map<float>(tets, opts->model, ops, reduce, (float)opts->mu, (float)opts->lambda, io, nullptr,
                               ctx->stream);
+    tets->test_drop_tile = -1;
   }
   if (e == cudaSuccess && tets->vperm) {
     for (int i = 0; i < mc.nout && e == cudaSuccess; ++i)

@@ -139,6 +139,7 @@ struct ebb_rel_s {
   int tile_cap = ebb::kTileTets;        // tets per tile the layout was cut with
   unsigned layout_gen = 0;              // bumped whenever the tile blobs are rebuilt
   signed char tuned[2][2] = {{-1, -1}, {-1, -1}};  // autotuned reduce per [model][precision], -1 none
+  int test_drop_tile = -1;              // EBB_MAP_TEST_DROP_TILE: tile whose blob copy the next map skips
   ebb::VertexIndex vindex;
 
   // ---- implicit-step scratch ----

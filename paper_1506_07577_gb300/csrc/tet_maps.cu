@@ -196,6 +196,7 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
 // the next; with one, a second consumer barrier precedes the output stores.  Dynamic shared memory: blob ring | slot ring (u[S][4]
 // then w[S][4] per stage) | outputs[2][4*3][TT+1][NF] | barriers, abort flag.
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+constexpr long long kTestWaitCycles = 2000000LL;  // about 1 ms: waits under EBB_MAP_TEST_DROP_TILE
 constexpr int kTileThreads = kTileTets + 32;
 
 template <typename T, int OPS>
@@ -270,7 +271,8 @@ __device__ __forceinline__ void add_out(const T* p, T* acc) {
 template <typename T, int MODEL, int OPS>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
 tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, BlobLayout L,
-                const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err) {
+                const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err,
+                int drop_tile, long long wait_cycles) {
   using Z = TileSmem<T, OPS>;
   constexpr int TT = Z::TT, NF = Z::NF, RB = Z::RB, RV = Z::RV;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -312,27 +314,30 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
     for (int j = 0; j < n_my + Z::LAG && !bad; ++j) {
       if (j < n_my) {
         const int sb = j % RB;
-        bool ok = j < RB || mbar_wait_or_abort(&empty_b[sb], ((j / RB) - 1) & 1u, abort_flag, kWaitCycles);
+        bool ok = j < RB || mbar_wait_or_abort(&empty_b[sb], ((j / RB) - 1) & 1u, abort_flag, wait_cycles);
         if (__any_sync(0xffffffffu, !ok)) {
           bad = true;
           break;
         }
-        if (lane == 0) {
-          // Blobs are read once per map: evict them first, so that the
-          // vertex fields and the CG vectors stay in L2.
-          fence_proxy_async_smem();
-          bulk_load_hint(ring + (size_t)sb * L.bytes, blobs + (size_t)((int)blockIdx.x + j * G) * L.bytes, L.copy,
-                         &full_b[sb], make_policy_evict_first());
+        const int tj = (int)blockIdx.x + j * G;
+        if (tj != drop_tile) {  // drop_tile: failure-detection tests only (-1 otherwise)
+          if (lane == 0) {
+            // Blobs are read once per map: evict them first, so that the
+            // vertex fields and the CG vectors stay in L2.
+            fence_proxy_async_smem();
+            bulk_load_hint(ring + (size_t)sb * L.bytes, blobs + (size_t)tj * L.bytes, L.copy, &full_b[sb],
+                           make_policy_evict_first());
+          }
+          pend |= 1u << sb;
+          pend_parity = (pend_parity & ~(1u << sb)) | (((unsigned)(j / RB) & 1u) << sb);
         }
-        pend |= 1u << sb;
-        pend_parity = (pend_parity & ~(1u << sb)) | (((unsigned)(j / RB) & 1u) << sb);
       }
       const int jj = j - Z::LAG;
       if (jj >= 0 && jj < n_my) {
         const int sb = jj % RB, sv = jj % RV;
-        bool ok = mbar_wait_or_abort(&full_b[sb], (jj / RB) & 1u, abort_flag, kWaitCycles);
+        bool ok = mbar_wait_or_abort(&full_b[sb], (jj / RB) & 1u, abort_flag, wait_cycles);
         if (ok) pend &= ~(1u << sb);
-        ok = ok && (jj < RV || mbar_wait_or_abort(&empty_v[sv], ((jj / RV) - 1) & 1u, abort_flag, kWaitCycles));
+        ok = ok && (jj < RV || mbar_wait_or_abort(&empty_v[sv], ((jj / RV) - 1) & 1u, abort_flag, wait_cycles));
         if (__any_sync(0xffffffffu, !ok)) {
           bad = true;
           break;
@@ -364,7 +369,7 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
       // shared memory goes away.
 #pragma unroll
       for (int r = 0; r < RB; ++r)
-        if ((pend >> r) & 1u) mbar_wait(&full_b[r], (pend_parity >> r) & 1u, kWaitCycles);
+        if ((pend >> r) & 1u) mbar_wait(&full_b[r], (pend_parity >> r) & 1u, wait_cycles);
     }
     return;
   }
@@ -383,8 +388,8 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
     const T* su = slots + (size_t)sv * Z::slot_elems;
     const T* sw = su + 4 * Z::S;
     T* sob = outs + (Z::OB == 2 ? (j & 1) : 0) * Z::out_elems;
-    const bool ok = mbar_wait_or_abort(&full_b[sb], (j / RB) & 1u, abort_flag, kWaitCycles) &&
-                    mbar_wait_or_abort(&full_v[sv], (j / RV) & 1u, abort_flag, kWaitCycles);
+    const bool ok = mbar_wait_or_abort(&full_b[sb], (j / RB) & 1u, abort_flag, wait_cycles) &&
+                    mbar_wait_or_abort(&full_v[sv], (j / RV) & 1u, abort_flag, wait_cycles);
     // Phase 1: one tet per thread (skipped by a thread whose wait gave up).
     const int4 h = ok ? *reinterpret_cast<const int4*>(st) : make_int4(0, 0, 0, 0);
     T fo[4][3], ko[4][3], dgo[4][3];
@@ -559,9 +564,10 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
   }
   int grid = Cfg::grid_per_sm * sm_count();
   if (grid > tl.ntiles) grid = tl.ntiles;
-  tet_tile_kernel<T, MODEL, OPS><<<grid, kTileThreads, smem, stream>>>(tl.ntiles, (int)rel->verts->size,
-                                                                    blob_of<T>(tl), L, rel->tet_perm, mu0, lam0,
-                                                                    io, active, rel->ctx->d_err);
+  const int drop = rel->test_drop_tile;
+  tet_tile_kernel<T, MODEL, OPS><<<grid, kTileThreads, smem, stream>>>(
+      tl.ntiles, (int)rel->verts->size, blob_of<T>(tl), L, rel->tet_perm, mu0, lam0, io, active, rel->ctx->d_err,
+      drop, drop >= 0 ? kTestWaitCycles : kWaitCycles);
   return cudaGetLastError();
 }
 

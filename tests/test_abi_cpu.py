@@ -19,7 +19,7 @@ def _declared():
 
 def _header_defines():
     src = open(HEADER).read()
-    return {k: int(v) for k, v in re.findall(r"#define\s+(EBB_\w+)\s+(\d+)u?", src)}
+    return {k: int(v, 0) for k, v in re.findall(r"#define\s+(EBB_\w+)\s+(0x[0-9a-fA-F]+|\d+)u?", src)}
 
 
 @pytest.fixture(scope="module")

@@ -168,3 +168,38 @@ def test_single_tet_matches_hand_derived_forces():
             abi.ebb_map_tet_forces(dm.ctx, dm.tets, "u", "f", abi.map_opts(mdl, case["mu"], case["lam"]))
             abi.ebb_ctx_sync(dm.ctx)
             assert np.max(np.abs(f.cpu().numpy().T - np.array(case["f"]))) < 1e-14
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """Failure detection without a fault: the tiled map is told to skip one
+    tile's bulk copy (EBB_MAP_TEST_DROP_TILE), so that CTA's bounded wait
+    runs out; the next synchronising call reports EBB_ERR_TIMEOUT, and the
+    same context then runs the map correctly."""
+    abi = _abi()
+    from _problems import oracle_maps, problem, rel_err
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(6, "stvk", seed=3)
+    f, Kw, _ = oracle_maps(m, mu, lam, u, w, "stvk")
+    with DeviceTetMesh(m.X, m.tets, mu, lam) as dm:
+        dm.vertex_field("u", torch.float32, value=u)
+        dm.vertex_field("w", torch.float32, value=w)
+        tf = dm.vertex_field("f", torch.float32)
+        tk = dm.vertex_field("k", torch.float32)
+        o = abi.map_opts(abi.EBB_STVK, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED,
+                         flags=abi.EBB_MAP_ZERO_OUT | abi.EBB_MAP_TEST_DROP_TILE)
+        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+        with pytest.raises(abi.EbbError) as ei:
+            abi.ebb_ctx_sync(dm.ctx)
+        assert ei.value.status == abi.EBB_ERR_TIMEOUT
+        abi.ebb_ctx_sync(dm.ctx)   # the status word was consumed
+        o.flags = abi.EBB_MAP_ZERO_OUT
+        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+        abi.ebb_ctx_sync(dm.ctx)
+        assert rel_err(tf.double().cpu().numpy().T, f) < 1e-5
+        assert rel_err(tk.double().cpu().numpy().T, Kw) < 1e-5
+        # the flag is refused outside the tiled variant
+        o.flags = abi.EBB_MAP_TEST_DROP_TILE
+        o.reduce = abi.EBB_REDUCE_ATOMIC
+        with pytest.raises(abi.EbbError) as ei:
+            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+        assert ei.value.status == abi.EBB_ERR_ARG
