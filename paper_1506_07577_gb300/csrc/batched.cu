@@ -60,22 +60,30 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Block sum of (a, b), fixed order, result in thread 0.  FP64 adds are slow
+// on GB300, so values go through shared memory and one warp adds them
+// (kBT/32 per lane, then a shuffle tree) instead of a shuffle tree per warp.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-  __shared__ double sa[kBT / 32], sb[kBT / 32];
-  a = warp_sum(a);
-  b = warp_sum(b);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    sa[w] = a;
-    sb[w] = b;
-  }
+  __shared__ double sa[kBT], sb[kBT];
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
   __syncthreads();
-  if (w == 0) {
-    a = warp_sum(l < kBT / 32 ? sa[l] : 0.0);
-    b = warp_sum(l < kBT / 32 ? sb[l] : 0.0);
+  if (threadIdx.x < 32) {
+    double x = 0.0, y = 0.0;
+#pragma unroll
+    for (int i = 0; i < kBT / 32; ++i) {
+      x += sa[threadIdx.x + 32 * i];
+      y += sb[threadIdx.x + 32 * i];
+    }
+    a = warp_sum(x);
+    b = warp_sum(y);
   }
   __syncthreads();
 }
+
+// dt^2 times a K p entry in FP64 (in FP32 first when K p is FP32).
+__device__ __forceinline__ double dt2_times(float kp, double dt2) { return (double)((float)dt2 * kp); }
+__device__ __forceinline__ double dt2_times(double kp, double dt2) { return dt2 * kp; }
 
 // Per-mesh two-pass sum: block partial to part[2*b]; the mesh's last block
 // sums its blocks' partials in block order and returns true with the totals.
@@ -161,7 +169,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBT)
 batch_pq_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restrict__ pin,
                 const double* __restrict__ mass, const double* __restrict__ p, const T* __restrict__ acc_kp,
-                double* part, MeshCg* sc, int* n_active) {
+                double* __restrict__ qz, double* part, MeshCg* sc, int* n_active) {
   const int m = tb.blk_mesh[blockIdx.x];
   MeshCg& st = sc[m];
   if (!st.active[s]) return;
@@ -174,7 +182,9 @@ batch_pq_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restr
     for (int comp = 0; comp < 3; ++comp) {
       const int i = comp * c.nv + v;
       const double pi = p[i];
-      pq += pi * (mv * pi + dt2 * (double)acc_kp[i]);
+      const double q = fma(mv, pi, dt2_times(acc_kp[i], dt2));
+      qz[i] = q;
+      pq = fma(pi, q, pq);
     }
   }
   if (mesh_reduce_last(pq, zero, part, &st.count[1], tb.mesh_blk0[m], tb.mesh_nblk[m]) && threadIdx.x == 0) {
@@ -191,28 +201,26 @@ batch_pq_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restr
 template <typename T>
 __global__ void __launch_bounds__(kBT)
 batch_update_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restrict__ pin,
-                    const double* __restrict__ mass, const double* __restrict__ p, const T* __restrict__ acc_kp,
-                    const double* __restrict__ dinv, double* r, double* y, double* part, MeshCg* sc,
-                    int* n_active) {
+                    const double* __restrict__ p, const double* __restrict__ dinv, double* __restrict__ r,
+                    double* __restrict__ y, double* __restrict__ qz, double* part, MeshCg* sc, int* n_active) {
   const int m = tb.blk_mesh[blockIdx.x];
   MeshCg& st = sc[m];
   if (!st.active[s] || st.status != EBB_OK) return;
   const double alpha = st.alpha;
   const int v = tb.blk_v0[blockIdx.x] + threadIdx.x;
-  const double dt2 = c.dt * c.dt;
   double rz = 0.0, rr = 0.0;
   if (v < tb.blk_v1[blockIdx.x] && !pinned_at(pin, v)) {
-    const double mv = mass[v];
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const int i = comp * c.nv + v;
       const double pi = p[i];
-      const double q = mv * pi + dt2 * (double)acc_kp[i];
-      y[i] += alpha * pi;
-      const double ri = r[i] - alpha * q;
+      y[i] = fma(alpha, pi, y[i]);
+      const double ri = fma(-alpha, qz[i], r[i]);
+      const double zi = ri * dinv[i];
       r[i] = ri;
-      rz += ri * (ri * dinv[i]);
-      rr += ri * ri;
+      qz[i] = zi;
+      rz = fma(ri, zi, rz);
+      rr = fma(ri, ri, rr);
     }
   }
   if (mesh_reduce_last(rz, rr, part, &st.count[2], tb.mesh_blk0[m], tb.mesh_nblk[m]) && threadIdx.x == 0) {
@@ -229,8 +237,9 @@ batch_update_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __r
 
 template <typename T>
 __global__ void __launch_bounds__(kBT)
-batch_pupdate_kernel(BatchConst c, BatchTable tb, int s, const double* __restrict__ r,
-                     const double* __restrict__ dinv, double* p, T* pe, T* acc_kp, MeshCg* sc) {
+batch_pupdate_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restrict__ pin,
+                     const double* __restrict__ qz, double* __restrict__ p, T* __restrict__ pe,
+                     T* __restrict__ acc_kp, MeshCg* sc) {
   const int m = tb.blk_mesh[blockIdx.x];
   MeshCg& st = sc[m];
   if (!st.active[s] || st.status != EBB_OK) {
@@ -240,10 +249,11 @@ batch_pupdate_kernel(BatchConst c, BatchTable tb, int s, const double* __restric
   const double beta = st.beta;
   const int v = tb.blk_v0[blockIdx.x] + threadIdx.x;
   if (v < tb.blk_v1[blockIdx.x]) {
+    const bool pinned = pinned_at(pin, v);   // r = p = 0 there; z was not formed
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const int i = comp * c.nv + v;
-      const double pi = r[i] * dinv[i] + beta * p[i];
+      const double pi = pinned ? 0.0 : fma(beta, p[i], qz[i]);
       p[i] = pi;
       if (pe) pe[i] = (T)pi;
       acc_kp[i] = T(0);
@@ -291,6 +301,7 @@ struct BatchScratch {
   void* acc[4] = {nullptr, nullptr, nullptr, nullptr};
   void *ue = nullptr, *pe = nullptr;
   double *r = nullptr, *p = nullptr, *y = nullptr, *dinv = nullptr, *mass = nullptr, *part = nullptr;
+  double* qz = nullptr;              // A p, then z = r / diag A, within one CG iteration
   MeshCg* sc = nullptr;
   int* n_active = nullptr;
   std::vector<MeshCg> h_sc;
@@ -312,6 +323,7 @@ void free_batch_scratch(ebb_rel_s* rel) {
   cudaFree(s->p);
   cudaFree(s->y);
   cudaFree(s->dinv);
+  cudaFree(s->qz);
   cudaFree(s->mass);
   cudaFree(s->part);
   cudaFree(s->sc);
@@ -375,6 +387,7 @@ ebb_status_t prepare_batch(ebb_ctx_s* ctx, ebb_rel_s* tets, const int* batch, in
   if (e == cudaSuccess) e = cudaMalloc(&s->p, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->y, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->dinv, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&s->qz, n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->mass, (size_t)nv * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->part, 2 * (size_t)nb * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&s->sc, (size_t)nmesh * sizeof(MeshCg));
@@ -482,11 +495,11 @@ ebb_status_t batch_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, c
     for (int k = 0; k < kChunk && le == cudaSuccess; ++k) {
       const int par = k & 1;
       le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, s->n_active, st);
-      batch_pq_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->mass, s->p, acc_kp, s->part, s->sc,
+      batch_pq_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->mass, s->p, acc_kp, s->qz, s->part, s->sc,
                                              s->n_active);
-      batch_update_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->mass, s->p, acc_kp, s->dinv, s->r, s->y,
-                                                 s->part, s->sc, s->n_active);
-      batch_pupdate_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, s->r, s->dinv, s->p, mixed ? pe : nullptr, acc_kp,
+      batch_update_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->p, s->dinv, s->r, s->y, s->qz, s->part,
+                                                 s->sc, s->n_active);
+      batch_pupdate_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->qz, s->p, mixed ? pe : nullptr, acc_kp,
                                                   s->sc);
       if (le == cudaSuccess) le = cudaGetLastError();
     }
