@@ -110,6 +110,19 @@ __device__ __forceinline__ void cp_async_elem(double* dst, const double* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// 16-byte asynchronous global->shared copy (both addresses 16-byte aligned),
+// bypassing L1.
+__device__ __forceinline__ void cp_async_16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Fire-and-forget atomic add of (x, y, z, 0) to four consecutive floats
+// (16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* p, float x, float y, float z) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(x), "f"(y), "f"(z), "f"(0.f)
+               : "memory");
+}
+
 // One arrival on `bar` once every cp.async this thread issued so far has
 // landed (the barrier's expected count includes this arrival).
 __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {

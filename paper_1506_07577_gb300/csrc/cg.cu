@@ -112,18 +112,32 @@ __device__ __forceinline__ bool reduce_last(double& a, double& b, double* part, 
 }
 
 // u32 = u, w32 = v (mixed precision), accumulators zeroed.
-template <typename T>
-__global__ void step_prep_kernel(int n, const double* __restrict__ u, const double* __restrict__ v, T* ue,
+// Element-precision operands of the step's maps are library-internal, so in
+// FP32 with the tiled reduction they are stored vertex-interleaved (AOS: nv
+// groups of x, y, z, padding), which lets the tiled map fetch a vertex with
+// one 16-byte copy and add into it with one vector atomic.
+template <bool AOS>
+__device__ __forceinline__ size_t vidx(int nv, int v, int k) {
+  return AOS ? 4 * (size_t)v + k : (size_t)k * nv + v;
+}
+
+// ue = u, ve = v in the element precision (mixed only); accumulators zeroed.
+template <typename T, bool AOS>
+__global__ void step_prep_kernel(int nv, const double* __restrict__ u, const double* __restrict__ v, T* ue,
                                  T* ve, T* acc_f, T* acc_kv, T* acc_d, T* acc_kp, bool copy) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (copy) {
-      ue[i] = (T)u[i];
-      ve[i] = (T)v[i];
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nv; x += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < (AOS ? 4 : 3); ++k) {
+      const size_t i = vidx<AOS>(nv, x, k);
+      if (copy) {
+        ue[i] = k < 3 ? (T)u[(size_t)k * nv + x] : T(0);
+        ve[i] = k < 3 ? (T)v[(size_t)k * nv + x] : T(0);
+      }
+      acc_f[i] = T(0);
+      acc_kv[i] = T(0);
+      acc_d[i] = T(0);
+      acc_kp[i] = T(0);
     }
-    acc_f[i] = T(0);
-    acc_kv[i] = T(0);
-    acc_d[i] = T(0);
-    acc_kp[i] = T(0);
   }
 }
 
@@ -149,7 +163,7 @@ struct StepConst {
 
 // b = dt (f + m g - dt K v) (0 on pinned rows); r = b; z = r / diag(A);
 // p = z; y = 0; then r.z and r.r, and the CG state for iteration 0.
-template <typename T, typename PT>
+template <typename T, typename PT, bool AOS>
 __global__ void __launch_bounds__(kVecThreads)
 cg_init_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict__ mass,
                const T* __restrict__ acc_f, const T* __restrict__ acc_kv, const T* __restrict__ acc_d,
@@ -160,18 +174,19 @@ cg_init_kernel(StepConst c, const PT* __restrict__ pin, const double* __restrict
   for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += kVecBlocks * kVecThreads) {
     const int comp = i >= c.nv ? (i >= 2 * c.nv ? 2 : 1) : 0;
     const int vtx = i - comp * c.nv;
+    const size_t ie = vidx<AOS>(c.nv, vtx, comp);
     double b = 0.0, di = 1.0;
     if (!is_pinned(pin, vtx)) {
       const double m = mass[vtx];
-      b = c.dt * ((double)acc_f[i] + m * c.g[comp] - c.dt * (double)acc_kv[i]);
-      di = 1.0 / (m + c.dt * c.dt * (double)acc_d[i]);
+      b = c.dt * ((double)acc_f[ie] + m * c.g[comp] - c.dt * (double)acc_kv[ie]);
+      di = 1.0 / (m + c.dt * c.dt * (double)acc_d[ie]);
     }
     const double z = b * di;
     r[i] = b;
     p[i] = z;
     y[i] = 0.0;
     dinv[i] = di;
-    if (pe) pe[i] = (T)z;
+    if (pe) pe[ie] = (T)z;
     rz += b * z;
     rr += b * b;
   }
@@ -279,7 +294,7 @@ __device__ __forceinline__ double dt2_times(double kp, double dt2) { return dt2 
 // pass in the same fixed order (deterministic, identical in every block);
 // block 0 publishes the scalars.  A barrier that does not complete sets
 // EBB_ERR_TIMEOUT in the CG status.
-template <typename T, typename PT>
+template <typename T, typename PT, bool AOS>
 __global__ void __launch_bounds__(kVecThreads)
 cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __restrict__ mass,
                double* __restrict__ p, T* __restrict__ acc_kp, const double* __restrict__ dinv,
@@ -302,11 +317,17 @@ cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __r
     const double m = mass[v];
     double pv[3];
     T kv[3];
+    if constexpr (AOS) {
+      const float4 k4 = reinterpret_cast<const float4*>(acc_kp)[v];
+      kv[0] = k4.x;
+      kv[1] = k4.y;
+      kv[2] = k4.z;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      pv[k] = p[(size_t)k * nv + v];
-      kv[k] = acc_kp[(size_t)k * nv + v];
+      for (int k = 0; k < 3; ++k) kv[k] = acc_kp[(size_t)k * nv + v];
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pv[k] = p[(size_t)k * nv + v];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const double q = fma(m, pv[k], dt2_times(kv[k], dt2));
@@ -403,34 +424,42 @@ cg_iter_kernel(StepConst c, int s, const PT* __restrict__ pin, const double* __r
       zv[k] = pinned ? 0.0 : qz[i];
       pv[k] = pinned ? 0.0 : p[i];
     }
+    double pn[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const size_t i = (size_t)k * nv + v;
-      const double pi = pinned ? 0.0 : fma(beta, pv[k], zv[k]);
-      p[i] = pi;
-      if (pe) pe[i] = (T)pi;
-      acc_kp[i] = T(0);
+      pn[k] = pinned ? 0.0 : fma(beta, pv[k], zv[k]);
+      p[(size_t)k * nv + v] = pn[k];
+    }
+    if constexpr (AOS) {
+      if (pe) reinterpret_cast<float4*>(pe)[v] = make_float4((float)pn[0], (float)pn[1], (float)pn[2], 0.f);
+      reinterpret_cast<float4*>(acc_kp)[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (pe) pe[(size_t)k * nv + v] = (T)pn[k];
+        acc_kp[(size_t)k * nv + v] = T(0);
+      }
     }
   }
 }
 
 // Blocks of cg_iter_kernel: all co-resident (a cooperative launch), at most
 // kVecBlocks (the size of the partial-sum arrays).
-template <typename T, typename PT>
+template <typename T, typename PT, bool AOS>
 int iter_grid() {
   static int g = 0;
   if (g == 0) {
     int per_sm = 0, dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_iter_kernel<T, PT>, kVecThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_iter_kernel<T, PT, AOS>, kVecThreads, 0);
     g = std::min(kVecBlocks, std::min(per_sm, 2) * std::max(nsm, 1));
     if (g < 1) g = 1;
   }
   return g;
 }
 
-template <typename T, typename PT>
+template <typename T, typename PT, bool AOS>
 cudaError_t launch_cg_iter(int grid, cudaStream_t st, StepConst c, int s, const PT* pin, const double* mass,
                            double* p, T* acc_kp, const double* dinv, double* r, double* y, double* qz, T* pe,
                            double* part_a, double* part_b, CgScalars* sc) {
@@ -444,7 +473,7 @@ cudaError_t launch_cg_iter(int grid, cudaStream_t st, StepConst c, int s, const 
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, cg_iter_kernel<T, PT>, c, s, pin, mass, p, acc_kp, dinv, r, y, qz, pe, part_a,
+  return cudaLaunchKernelEx(&cfg, cg_iter_kernel<T, PT, AOS>, c, s, pin, mass, p, acc_kp, dinv, r, y, qz, pe, part_a,
                             part_b, sc);
 }
 
@@ -657,7 +686,13 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   // Arrival counters of the last-block reductions start at zero.
   e = cudaMemsetAsync(s->sc, 0, sizeof(CgScalars), st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "CG state reset");
-  step_prep_kernel<T><<<vgrid, 256, 0, st>>>(n, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
+  // FP32 operands with the tiled reduction are vertex-interleaved (see vidx).
+  bool aos = false;
+  if constexpr (sizeof(T) == 4) aos = mixed && prm->reduce == EBB_REDUCE_TILED;
+  if (aos)
+    step_prep_kernel<T, true><<<vgrid, 256, 0, st>>>(nv, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
+  else
+    step_prep_kernel<T, false><<<vgrid, 256, 0, st>>>(nv, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "step prep");
 
@@ -668,13 +703,19 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   io.f = acc_f;
   io.Kw = acc_kv;
   io.d = acc_d;
+  io.aos = aos;
   e = launch_tet_map<T>(tets, prm->model, OP_FORCE | OP_KV | OP_DIAG, prm->reduce, mu0, lam0, io, nullptr, st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "force/Kv/diag map");
 
   double* part_a = s->part;
   double* part_b = s->part + 2 * kVecBlocks;
-  cg_init_kernel<T, PT><<<kVecBlocks, kVecThreads, 0, st>>>(c, pin, s->mass, acc_f, acc_kv, acc_d, s->r, s->p,
-                                                             s->y, s->dinv, mixed ? pe : nullptr, part_a, s->sc);
+  if (aos)
+    cg_init_kernel<T, PT, true><<<kVecBlocks, kVecThreads, 0, st>>>(c, pin, s->mass, acc_f, acc_kv, acc_d, s->r,
+                                                                     s->p, s->y, s->dinv, pe, part_a, s->sc);
+  else
+    cg_init_kernel<T, PT, false><<<kVecBlocks, kVecThreads, 0, st>>>(c, pin, s->mass, acc_f, acc_kv, acc_d, s->r,
+                                                                      s->p, s->y, s->dinv, mixed ? pe : nullptr,
+                                                                      part_a, s->sc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(ctx, e, "CG init");
 
@@ -682,6 +723,7 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   kio.u = io.u;
   kio.w = mixed ? pe : (const T*)s->p;
   kio.Kw = acc_kp;
+  kio.aos = aos;
 
   // kChunk CG iterations (plus the status read-back) are captured once as a
   // CUDA graph and relaunched until the device reports convergence.
@@ -708,8 +750,11 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
       const int par = k & 1;
       le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
       if (le == cudaSuccess)
-        le = launch_cg_iter<T, PT>(iter_grid<T, PT>(), st, c, par, pin, s->mass, s->p, acc_kp, s->dinv, s->r, s->y,
-                                   s->qz, mixed ? pe : nullptr, part_a, part_b, s->sc);
+        le = aos ? launch_cg_iter<T, PT, true>(iter_grid<T, PT, true>(), st, c, par, pin, s->mass, s->p, acc_kp,
+                                               s->dinv, s->r, s->y, s->qz, pe, part_a, part_b, s->sc)
+                 : launch_cg_iter<T, PT, false>(iter_grid<T, PT, false>(), st, c, par, pin, s->mass, s->p, acc_kp,
+                                                s->dinv, s->r, s->y, s->qz, mixed ? pe : nullptr, part_a, part_b,
+                                                s->sc);
     }
     if (le == cudaSuccess) le = cudaMemcpyAsync(s->h_sc, s->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st);
     cudaGraph_t g = nullptr;

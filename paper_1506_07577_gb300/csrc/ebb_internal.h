@@ -163,6 +163,10 @@ struct MapIO {
   T* f = nullptr;          // force accumulator
   T* Kw = nullptr;         // K w accumulator
   T* d = nullptr;          // diag(K) accumulator
+  // Vertex-interleaved operands (library-internal fields only): every field
+  // above is nv groups of 4 (x, y, z, padding) instead of 3 planes; FP32 and
+  // the tiled reduction only.
+  bool aos = false;
 };
 
 // Launch one element map over all tets of `rel` on `stream`.  `active`

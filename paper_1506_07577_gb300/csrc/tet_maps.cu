@@ -268,7 +268,10 @@ __device__ __forceinline__ void add_out(const T* p, T* acc) {
   }
 }
 
-template <typename T, int MODEL, int OPS>
+// AOS: vertex-interleaved operands (MapIO::aos): the producer copies each
+// vertex's 16 bytes with one cp.async, the reduction adds each vertex's three
+// components with one vector atomic.
+template <typename T, int MODEL, int OPS, bool AOS>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
 tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, BlobLayout L,
                 const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err,
@@ -346,14 +349,22 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
         const int nvu = reinterpret_cast<const int4*>(st)->y;
         const int* vid = reinterpret_cast<const int*>(st + kBlobVtx);
         T* su = slots + (size_t)sv * Z::slot_elems;
-        // Lane l copies word l + 32k of the 4-wide slot vectors (component 3
-        // is padding): consecutive lanes write consecutive shared words.
-        for (int wd = lane; wd < 4 * nvu; wd += 32) {
-          const int c = wd & 3;
-          if (c < 3) {
-            const int v = vid[wd >> 2];
-            cp_async_elem(su + wd, io.u + (size_t)c * nv + v);
-            if (Z::KV) cp_async_elem(su + 4 * Z::S + wd, io.w + (size_t)c * nv + v);
+        if (AOS) {
+          for (int sl = lane; sl < nvu; sl += 32) {
+            const int v = vid[sl];
+            cp_async_16(su + 4 * sl, io.u + 4 * (size_t)v);
+            if (Z::KV) cp_async_16(su + 4 * (Z::S + sl), io.w + 4 * (size_t)v);
+          }
+        } else {
+          // Lane l copies word l + 32k of the 4-wide slot vectors (component
+          // 3 is padding): consecutive lanes write consecutive shared words.
+          for (int wd = lane; wd < 4 * nvu; wd += 32) {
+            const int c = wd & 3;
+            if (c < 3) {
+              const int v = vid[wd >> 2];
+              cp_async_elem(su + wd, io.u + (size_t)c * nv + v);
+              if (Z::KV) cp_async_elem(su + 4 * Z::S + wd, io.w + (size_t)c * nv + v);
+            }
           }
         }
         cp_async_arrive_noinc(&full_v[sv]);
@@ -482,10 +493,16 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
       }
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
+        if constexpr (AOS) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+          for (int f = 0; f < NF; ++f)
+            red_add_v4(out_field[f] + 4 * (size_t)v, acc[f], acc[NF + f], acc[2 * NF + f]);
+        } else {
 #pragma unroll
-          for (int f = 0; f < NF; ++f) atomicAdd(out_field[f] + (size_t)c * nv + v, acc[c * NF + f]);
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int f = 0; f < NF; ++f) atomicAdd(out_field[f] + (size_t)c * nv + v, acc[c * NF + f]);
+        }
       }
     }
     __syncwarp();
@@ -493,15 +510,15 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
   }
 }
 
-template <typename T, int MODEL, int OPS>
+template <typename T, int MODEL, int OPS, bool AOS>
 struct TileLaunchCfg {
   static size_t smem;
   static int grid_per_sm;
 };
-template <typename T, int MODEL, int OPS>
-size_t TileLaunchCfg<T, MODEL, OPS>::smem = 0;
-template <typename T, int MODEL, int OPS>
-int TileLaunchCfg<T, MODEL, OPS>::grid_per_sm = 0;
+template <typename T, int MODEL, int OPS, bool AOS>
+size_t TileLaunchCfg<T, MODEL, OPS, AOS>::smem = 0;
+template <typename T, int MODEL, int OPS, bool AOS>
+int TileLaunchCfg<T, MODEL, OPS, AOS>::grid_per_sm = 0;
 
 int sm_count() {
   static int n = 0;
@@ -514,12 +531,13 @@ int sm_count() {
   return n;
 }
 
-template <typename T, int MODEL, int OPS>
+template <typename T, int MODEL, int OPS, bool AOS = false>
 cudaError_t configure_tiles() {
-  cudaError_t e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS, AOS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS, AOS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             100);
   return e;
 }
 
@@ -530,6 +548,11 @@ cudaError_t configure_tiles_model() {
   if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV>();
   if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_DIAG>();
   if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV | OP_DIAG>();
+  // Vertex-interleaved variants: the implicit step's FP32 maps.
+  if constexpr (sizeof(T) == 4) {
+    if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_KV, true>();
+    if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV | OP_DIAG, true>();
+  }
   return e;
 }
 
@@ -546,17 +569,17 @@ const BlobLayout& layout_of<float>(const Tiles& tl) { return tl.L32; }
 template <>
 const BlobLayout& layout_of<double>(const Tiles& tl) { return tl.L64; }
 
-template <typename T, int MODEL, int OPS>
+template <typename T, int MODEL, int OPS, bool AOS>
 cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, const int* active,
                          cudaStream_t stream) {
   const Tiles& tl = rel->tiles;
   if (tl.ntiles == 0) return cudaSuccess;
   const BlobLayout& L = layout_of<T>(tl);
   const size_t smem = TileSmem<T, OPS>::bytes(L);
-  using Cfg = TileLaunchCfg<T, MODEL, OPS>;
+  using Cfg = TileLaunchCfg<T, MODEL, OPS, AOS>;
   if (Cfg::smem != smem) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tet_tile_kernel<T, MODEL, OPS>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tet_tile_kernel<T, MODEL, OPS, AOS>,
                                                                   kTileThreads, smem);
     if (e != cudaSuccess) return e;
     Cfg::grid_per_sm = per_sm > 0 ? per_sm : 1;
@@ -565,7 +588,7 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
   int grid = Cfg::grid_per_sm * sm_count();
   if (grid > tl.ntiles) grid = tl.ntiles;
   const int drop = rel->test_drop_tile;
-  tet_tile_kernel<T, MODEL, OPS><<<grid, kTileThreads, smem, stream>>>(
+  tet_tile_kernel<T, MODEL, OPS, AOS><<<grid, kTileThreads, smem, stream>>>(
       tl.ntiles, (int)rel->verts->size, blob_of<T>(tl), L, rel->tet_perm, mu0, lam0, io, active, rel->ctx->d_err,
       drop, drop >= 0 ? kTestWaitCycles : kWaitCycles);
   return cudaGetLastError();
@@ -609,7 +632,16 @@ cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, 
     }
     return cudaSuccess;
   }
-  if (reduce == EBB_REDUCE_TILED) return launch_tiles<T, MODEL, OPS>(rel, mu0, lam0, io, active, stream);
+  if (reduce == EBB_REDUCE_TILED) {
+    if (io.aos) {
+      // vertex-interleaved operands: FP32, and only the maps the step runs
+      constexpr bool kAos = sizeof(T) == 4 && (OPS == OP_KV || OPS == (OP_FORCE | OP_KV | OP_DIAG));
+      if constexpr (kAos) return launch_tiles<T, MODEL, OPS, true>(rel, mu0, lam0, io, active, stream);
+      return cudaErrorInvalidValue;
+    }
+    return launch_tiles<T, MODEL, OPS, false>(rel, mu0, lam0, io, active, stream);
+  }
+  if (io.aos) return cudaErrorInvalidValue;
   return launch_range<T, MODEL, OPS, true>(0, nt, nt, nv, rel->keys, rel->tet_perm, streams_of<T>(rel, false), mu0,
                                            lam0, io, active, err, stream);
 }
