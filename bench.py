@@ -402,9 +402,10 @@ REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled"}
 
 
 def tune_report(abi, rep):
-    return {"reduce": REDUCE_NAMES[rep.reduce], "tile_tets": rep.tile_tets,
+    return {"reduce": REDUCE_NAMES[rep.reduce], "tile_tets": rep.tile_tets, "interleaved": bool(rep.interleaved),
             "candidates_kw_map_us": [{"reduce": REDUCE_NAMES[rep.cand[i].reduce], "tile_tets": rep.cand[i].tile_tets,
-                                      "us": rep.cand[i].us} for i in range(rep.ncand)]}
+                                      "interleaved": bool(rep.cand[i].interleaved), "us": rep.cand[i].us}
+                                     for i in range(rep.ncand)]}
 
 
 def batched_steps(abi, torch, local_rank, args):

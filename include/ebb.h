@@ -233,8 +233,12 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * K w map (the map the implicit step's CG solve runs every iteration) for
  * opts->model and opts->precision (opts->reduce and opts->flags ignored) on
  * the caller's vertex fields `u` and `w`, over the candidates: the tiled
- * variant with tiles of 128, 96 and 64 tets, the atomic variant, and the
- * coloured variant if the relation was finalized with EBB_FINALIZE_COLOR.
+ * variant with tiles of 128, 96 and 64 tets on the fields in place, in FP32
+ * also at the best of those with the operands staged vertex-interleaved
+ * (library-owned copies that let a vertex be fetched with one 16-byte copy
+ * and reduced with one vector atomic, at the price of a copy in and an add
+ * back per call), the atomic variant, and the coloured variant if the
+ * relation was finalized with EBB_FINALIZE_COLOR.
  * Each candidate: 2 untimed launches, then the median of 7 launches timed
  * with CUDA events on the context's stream.  Afterwards the relation's tiles
  * use the fastest tile size (the blobs are rebuilt if it changed) and
@@ -246,14 +250,16 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * device errors of the timed maps (EBB_ERR_INVERTED) are returned. */
 #define EBB_AUTOTUNE_MAX_CAND 8
 typedef struct {
-  int32_t reduce;     /* EBB_REDUCE_TILED, _ATOMIC or _COLOR */
-  int32_t tile_tets;  /* tets per tile for EBB_REDUCE_TILED, 0 otherwise */
-  double us;          /* median duration of one K w map, microseconds */
+  int32_t reduce;       /* EBB_REDUCE_TILED, _ATOMIC or _COLOR */
+  int32_t tile_tets;    /* tets per tile for EBB_REDUCE_TILED, 0 otherwise */
+  int32_t interleaved;  /* 1: FP32 operands staged vertex-interleaved */
+  double us;            /* median duration of one K w map call, microseconds */
 } ebb_autotune_cand_t;
 
 typedef struct {
-  int32_t reduce;     /* variant EBB_REDUCE_AUTO now selects */
-  int32_t tile_tets;  /* tets per tile of the relation's layout now */
+  int32_t reduce;       /* variant EBB_REDUCE_AUTO now selects */
+  int32_t tile_tets;    /* tets per tile of the relation's layout now */
+  int32_t interleaved;  /* FP32 tiled maps now stage operands vertex-interleaved */
   int32_t ncand;
   ebb_autotune_cand_t cand[EBB_AUTOTUNE_MAX_CAND];
 } ebb_autotune_report_t;
@@ -261,6 +267,16 @@ typedef struct {
 ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                    const char* w, const ebb_map_opts_t* opts,
                                    ebb_autotune_report_t* report);
+
+/* Set by hand what ebb_relation_autotune would choose: EBB_REDUCE_AUTO
+ * resolves to `reduce` (TILED, ATOMIC or COLOR) for `model` and `precision`;
+ * the tiles are re-cut to at most `tile_tets` tets (1..128) if that differs;
+ * `interleaved` (0/1) sets the FP32 vertex-interleaved staging of the tiled
+ * maps.  Synchronous.  Errors: EBB_ERR_ARG (out-of-range value),
+ * EBB_ERR_STATE (not finalized, or COLOR without EBB_FINALIZE_COLOR). */
+ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t model,
+                                     int32_t precision, int32_t reduce, int32_t tile_tets,
+                                     int32_t interleaved);
 
 /* ---- implicit step (Section 7.2, Section 7.3) --------------------------- */
 

@@ -67,11 +67,11 @@ EBB_AUTOTUNE_MAX_CAND = 8
 
 
 class ebb_autotune_cand_t(C.Structure):
-    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("us", C.c_double)]
+    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("interleaved", C.c_int32), ("us", C.c_double)]
 
 
 class ebb_autotune_report_t(C.Structure):
-    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("ncand", C.c_int32),
+    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("interleaved", C.c_int32), ("ncand", C.c_int32),
                 ("cand", ebb_autotune_cand_t * EBB_AUTOTUNE_MAX_CAND)]
 
 
@@ -95,6 +95,8 @@ _SIGS = {
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_relation_autotune": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t),
                                C.POINTER(ebb_autotune_report_t)], ebb_status_t),
+    "ebb_relation_set_tuning": ([ebb_ctx_t, ebb_rel_t, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
+                                ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_vjp": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ebb_step_params_t),
@@ -214,6 +216,11 @@ def ebb_relation_autotune(ctx, tets, u, w, opts):
     rep = ebb_autotune_report_t()
     _check(ctx, _lib.ebb_relation_autotune(ctx, tets, _b(u), _b(w), C.byref(opts), C.byref(rep)))
     return rep
+
+
+def ebb_relation_set_tuning(ctx, tets, model, precision, reduce, tile_tets, interleaved):
+    return _check(ctx, _lib.ebb_relation_set_tuning(ctx, tets, int(model), int(precision), int(reduce),
+                                                    int(tile_tets), int(bool(interleaved))))
 
 
 def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,

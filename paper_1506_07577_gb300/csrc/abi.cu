@@ -188,6 +188,84 @@ struct MapCall {
 };
 
 // One entry point for the four map calls.
+// Launch a map on caller-layout (3-plane) device fields: FP32 tiled maps on
+// a relation the autotuner set to stage move their operands into
+// library-owned vertex-interleaved buffers and add the results back; relations with reordered vertices stage in the internal order;
+// otherwise the map runs on the caller's fields directly.  Outputs are `+=`
+// targets in every case.
+ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int model, double mu, double lambda,
+                               ebb_reduce_t reduce, bool f64, void* const* in_user, int nin, void* const* out_user,
+                               int nout, bool drop) {
+  const int nv = (int)tets->verts->size;
+  const size_t bytes = (size_t)nv * 3 * (f64 ? 8 : 4);
+  const bool stage = !f64 && reduce == EBB_REDUCE_TILED && tets->stage_interleaved;
+  void* in[2] = {in_user[0], nin > 1 ? in_user[1] : nullptr};
+  void* out[3] = {nullptr, nullptr, nullptr};
+  for (int i = 0; i < nout; ++i) out[i] = out_user[i];
+  if (stage || tets->vperm) {
+    for (int i = 0; i < 5; ++i)   // 3 nv doubles: holds either precision and the interleaved FP32 layout
+      if (!tets->vscratch[i] && cudaMalloc(&tets->vscratch[i], (size_t)nv * 3 * 8 + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, EBB_ERR_NOMEM, "device allocation for staged map operands failed");
+      }
+    cudaError_t ge = cudaSuccess;
+    if (stage) {
+      ge = interleave_fields(nv, tets->vperm, (const float*)in[0], (const float*)in[1], (float*)tets->vscratch[0],
+                             (float*)tets->vscratch[1], ctx->stream);
+      in[0] = tets->vscratch[0];
+      if (nin > 1) in[1] = tets->vscratch[1];
+    } else {
+      for (int i = 0; i < nin && ge == cudaSuccess; ++i) {
+        ge = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)in[i], (double*)tets->vscratch[i],
+                                               ctx->stream)
+                 : gather_vertex_field<float>(nv, tets->vperm, (const float*)in[i], (float*)tets->vscratch[i],
+                                              ctx->stream);
+        in[i] = tets->vscratch[i];
+      }
+    }
+    for (int i = 0; i < nout && ge == cudaSuccess; ++i) {
+      out[i] = tets->vscratch[2 + i];
+      ge = cudaMemsetAsync(out[i], 0, stage ? (size_t)nv * 16 : bytes, ctx->stream);
+    }
+    if (ge != cudaSuccess) return cuda_check(ctx, ge, "staging map operands");
+  }
+  cudaError_t e;
+  int oi = 0;
+  if (f64) {
+    MapIO<double> io;
+    io.u = (const double*)in[0];
+    io.w = (const double*)in[1];
+    if (ops & OP_FORCE) io.f = (double*)out[oi++];
+    if (ops & OP_KV) io.Kw = (double*)out[oi++];
+    if (ops & OP_DIAG) io.d = (double*)out[oi++];
+    tets->test_drop_tile = drop ? 0 : -1;
+    e = launch_tet_map<double>(tets, model, ops, reduce, mu, lambda, io, nullptr, ctx->stream);
+    tets->test_drop_tile = -1;
+  } else {
+    MapIO<float> io;
+    io.u = (const float*)in[0];
+    io.w = (const float*)in[1];
+    if (ops & OP_FORCE) io.f = (float*)out[oi++];
+    if (ops & OP_KV) io.Kw = (float*)out[oi++];
+    if (ops & OP_DIAG) io.d = (float*)out[oi++];
+    io.aos = stage;
+    tets->test_drop_tile = drop ? 0 : -1;
+    e = launch_tet_map<float>(tets, model, ops, reduce, (float)mu, (float)lambda, io, nullptr, ctx->stream);
+    tets->test_drop_tile = -1;
+  }
+  if (e == cudaSuccess && stage) {
+    e = deinterleave_add_fields(nv, tets->vperm, (const float* const*)out, (float* const*)out_user, nout,
+                                ctx->stream);
+  } else if (e == cudaSuccess && tets->vperm) {
+    for (int i = 0; i < nout && e == cudaSuccess; ++i)
+      e = f64 ? scatter_add_vertex_field<double>(nv, tets->vperm, (const double*)out[i], (double*)out_user[i],
+                                                 ctx->stream)
+              : scatter_add_vertex_field<float>(nv, tets->vperm, (const float*)out[i], (float*)out_user[i],
+                                                ctx->stream);
+  }
+  return cuda_check(ctx, e, "launching tet map");
+}
+
 ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, const ebb_map_opts_t* opts) {
   if (!ctx) return EBB_ERR_ARG;
   ctx->last_error.clear();
@@ -237,61 +315,8 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
       if (s) return s;
     }
   }
-  // Reordered vertices: operands move into the internal order and back.
-  void* user_out[3] = {out[0], out[1], out[2]};
-  const int nv = (int)tets->verts->size;
-  if (tets->vperm) {
-    for (int i = 0; i < 5; ++i)   // sized for FP64 so either precision fits
-      if (!tets->vscratch[i] && cudaMalloc(&tets->vscratch[i], (size_t)nv * 3 * 8) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(ctx, EBB_ERR_NOMEM, "device allocation for reordered map operands failed");
-      }
-    cudaError_t ge = cudaSuccess;
-    for (int i = 0; i < mc.nin && ge == cudaSuccess; ++i) {
-      ge = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)in[i], (double*)tets->vscratch[i],
-                                             ctx->stream)
-               : gather_vertex_field<float>(nv, tets->vperm, (const float*)in[i], (float*)tets->vscratch[i],
-                                            ctx->stream);
-      in[i] = tets->vscratch[i];
-    }
-    for (int i = 0; i < mc.nout && ge == cudaSuccess; ++i) {
-      out[i] = tets->vscratch[2 + i];
-      ge = cudaMemsetAsync(out[i], 0, bytes, ctx->stream);
-    }
-    if (ge != cudaSuccess) return cuda_check(ctx, ge, "reordering map operands");
-  }
-  cudaError_t e;
-  int oi = 0;
-  if (f64) {
-    MapIO<double> io;
-    io.u = (const double*)in[0];
-    io.w = mc.nin > 1 ? (const double*)in[1] : nullptr;
-    if (ops & OP_FORCE) io.f = (double*)out[oi++];
-    if (ops & OP_KV) io.Kw = (double*)out[oi++];
-    if (ops & OP_DIAG) io.d = (double*)out[oi++];
-    tets->test_drop_tile = drop ? 0 : -1;
-    e = launch_tet_map<double>(tets, opts->model, ops, reduce, opts->mu, opts->lambda, io, nullptr, ctx->stream);
-    tets->test_drop_tile = -1;
-  } else {
-    MapIO<float> io;
-    io.u = (const float*)in[0];
-    io.w = mc.nin > 1 ? (const float*)in[1] : nullptr;
-    if (ops & OP_FORCE) io.f = (float*)out[oi++];
-    if (ops & OP_KV) io.Kw = (float*)out[oi++];
-    if (ops & OP_DIAG) io.d = (float*)out[oi++];
-    tets->test_drop_tile = drop ? 0 : -1;
-    e = launch_tet_map<float>(tets, opts->model, ops, reduce, (float)opts->mu, (float)opts->lambda, io, nullptr,
-                              ctx->stream);
-    tets->test_drop_tile = -1;
-  }
-  if (e == cudaSuccess && tets->vperm) {
-    for (int i = 0; i < mc.nout && e == cudaSuccess; ++i)
-      e = f64 ? scatter_add_vertex_field<double>(nv, tets->vperm, (const double*)out[i], (double*)user_out[i],
-                                                 ctx->stream)
-              : scatter_add_vertex_field<float>(nv, tets->vperm, (const float*)out[i], (float*)user_out[i],
-                                                ctx->stream);
-  }
-  return cuda_check(ctx, e, "launching tet map");
+  return launch_map_staged(ctx, tets, ops, opts->model, opts->mu, opts->lambda, reduce, f64, in, mc.nin, out,
+                           mc.nout, drop);
 }
 
 }  // namespace
@@ -614,6 +639,28 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, con
   return run_map(ctx, tets, mc, OP_DIAG, opts);
 }
 
+ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t model, int32_t precision,
+                                     int32_t reduce, int32_t tile_tets, int32_t interleaved) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!tets) return set_error(ctx, EBB_ERR_ARG, "null relation");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if ((model != EBB_STVK && model != EBB_NEOHOOKEAN) || (precision != EBB_PREC_F64 && precision != EBB_PREC_F32) ||
+      (reduce != EBB_REDUCE_TILED && reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR) || tile_tets < 1 ||
+      tile_tets > kTileTets || (interleaved != 0 && interleaved != 1))
+    return set_error(ctx, EBB_ERR_ARG, "tuning value out of range");
+  if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
+    return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
+  if (tets->tile_cap != tile_tets) {
+    ebb_status_t s = rebuild_tiles(ctx, tets, tile_tets);
+    if (s) return s;
+  }
+  tets->tuned[model][precision] = (signed char)reduce;
+  tets->stage_interleaved = interleaved != 0;
+  return EBB_OK;
+}
+
 ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* w,
                                    const ebb_map_opts_t* opts, ebb_autotune_report_t* report) {
   if (!ctx) return EBB_ERR_ARG;
@@ -628,35 +675,22 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   const bool f64 = opts->precision == EBB_PREC_F64;
   const ebb_dtype_t dt = f64 ? EBB_F64 : EBB_F32;
-  void *pu = nullptr, *pw = nullptr;
-  ebb_status_t s = vertex_field(ctx, tets, u, dt, 3, &pu);
-  if (!s) s = vertex_field(ctx, tets, w, dt, 3, &pw);
+  void* in[2] = {nullptr, nullptr};
+  ebb_status_t s = vertex_field(ctx, tets, u, dt, 3, &in[0]);
+  if (!s) s = vertex_field(ctx, tets, w, dt, 3, &in[1]);
   if (s) return s;
   s = read_device_error(ctx);
   if (s) return s;
   const int nv = (int)tets->verts->size;
   const size_t bytes = (size_t)nv * 3 * (f64 ? 8 : 4);
   cudaStream_t st = ctx->stream;
-  void* out = nullptr;
+  void* out[1] = {nullptr};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t ce = cudaMalloc(&out, bytes > 0 ? bytes : 16);
+  cudaError_t ce = cudaMalloc(&out[0], bytes > 0 ? bytes : 16);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-  // Reordered vertices: time the map on operands in the internal order.
-  if (ce == cudaSuccess && tets->vperm) {
-    for (int i = 0; i < 2 && ce == cudaSuccess; ++i)
-      if (!tets->vscratch[i]) ce = cudaMalloc(&tets->vscratch[i], (size_t)nv * 3 * 8);
-    if (ce == cudaSuccess)
-      ce = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)pu, (double*)tets->vscratch[0], st)
-               : gather_vertex_field<float>(nv, tets->vperm, (const float*)pu, (float*)tets->vscratch[0], st);
-    if (ce == cudaSuccess)
-      ce = f64 ? gather_vertex_field<double>(nv, tets->vperm, (const double*)pw, (double*)tets->vscratch[1], st)
-               : gather_vertex_field<float>(nv, tets->vperm, (const float*)pw, (float*)tets->vscratch[1], st);
-    pu = tets->vscratch[0];
-    pw = tets->vscratch[1];
-  }
   auto cleanup = [&]() {
-    cudaFree(out);
+    cudaFree(out[0]);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
   };
@@ -665,85 +699,81 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
     cudaGetLastError();
     return set_error(ctx, EBB_ERR_NOMEM, "autotune scratch allocation failed");
   }
-  // Time one candidate: median of 7 launches after 2 untimed ones.
-  auto time_map = [&](ebb_reduce_t reduce, double* us) -> cudaError_t {
+  // Time one candidate as a map call runs it (staging included): median of 7
+  // launches after 2 untimed ones.
+  auto time_map = [&](ebb_reduce_t reduce, double* us) -> ebb_status_t {
     std::vector<float> t;
     for (int it = 0; it < 9; ++it) {
-      cudaError_t e = cudaMemsetAsync(out, 0, bytes, st);
+      cudaError_t e = cudaMemsetAsync(out[0], 0, bytes, st);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-      if (e == cudaSuccess) {
-        if (f64) {
-          MapIO<double> io;
-          io.u = (const double*)pu;
-          io.w = (const double*)pw;
-          io.Kw = (double*)out;
-          e = launch_tet_map<double>(tets, opts->model, OP_KV, reduce, opts->mu, opts->lambda, io, nullptr, st);
-        } else {
-          MapIO<float> io;
-          io.u = (const float*)pu;
-          io.w = (const float*)pw;
-          io.Kw = (float*)out;
-          e = launch_tet_map<float>(tets, opts->model, OP_KV, reduce, (float)opts->mu, (float)opts->lambda, io,
-                                    nullptr, st);
-        }
-      }
-      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e != cudaSuccess) return cuda_check(ctx, e, "autotune timing");
+      ebb_status_t ms = launch_map_staged(ctx, tets, OP_KV, opts->model, opts->mu, opts->lambda, reduce, f64, in, 2,
+                                          out, 1, false);
+      if (ms) return ms;
+      e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) return e;
-      if (it >= 2) t.push_back(ms);
+      float msec = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&msec, e0, e1);
+      if (e != cudaSuccess) return cuda_check(ctx, e, "autotune timing");
+      if (it >= 2) t.push_back(msec);
     }
     std::sort(t.begin(), t.end());
     *us = 1e3 * t[t.size() / 2];
-    return cudaSuccess;
+    return EBB_OK;
   };
   int nc = 0;
   double best_tiled_us = 1e300, best_us = 1e300;
   int best_cap = tets->tile_cap;
   ebb_reduce_t best = EBB_REDUCE_TILED;
+  tets->stage_interleaved = false;
   const int caps[3] = {128, 96, 64};
-  for (int ci = 0; ci < 3 && ce == cudaSuccess; ++ci) {
+  for (int ci = 0; ci < 3; ++ci) {
     if (tets->tile_cap != caps[ci]) {
       s = rebuild_tiles(ctx, tets, caps[ci]);
-      if (s) {
-        cleanup();
-        return s;
-      }
+      if (s) break;
     }
     double us = 0.0;
-    ce = time_map(EBB_REDUCE_TILED, &us);
-    if (ce != cudaSuccess) break;
-    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], us};
+    s = time_map(EBB_REDUCE_TILED, &us);
+    if (s) break;
+    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], 0, us};
     if (us < best_tiled_us) {
       best_tiled_us = us;
       best_cap = caps[ci];
     }
   }
+  if (!s && tets->tile_cap != best_cap) s = rebuild_tiles(ctx, tets, best_cap);
+  if (!s && !f64) {
+    // the same tile size with the operands staged vertex-interleaved
+    tets->stage_interleaved = true;
+    double us = 0.0;
+    s = time_map(EBB_REDUCE_TILED, &us);
+    if (!s) {
+      report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, best_cap, 1, us};
+      if (us < best_tiled_us) best_tiled_us = us;
+      else tets->stage_interleaved = false;
+    }
+  }
   const ebb_reduce_t others[2] = {EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR};
-  for (int oi = 0; oi < 2 && ce == cudaSuccess; ++oi) {
+  for (int oi = 0; oi < 2 && !s; ++oi) {
     if (others[oi] == EBB_REDUCE_COLOR && !tets->has_colour) continue;
     double us = 0.0;
-    ce = time_map(others[oi], &us);
-    if (ce != cudaSuccess) break;
-    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, us};
+    s = time_map(others[oi], &us);
+    if (s) break;
+    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, 0, us};
     if (us < best_us) {
       best_us = us;
       best = others[oi];
     }
   }
   cleanup();
-  if (ce != cudaSuccess) return cuda_check(ctx, ce, "autotune timing");
+  if (s) return s;
   s = read_device_error(ctx);
   if (s) return s;
   if (best_tiled_us <= best_us) best = EBB_REDUCE_TILED;
-  if (tets->tile_cap != best_cap) {
-    s = rebuild_tiles(ctx, tets, best_cap);
-    if (s) return s;
-  }
   tets->tuned[opts->model][opts->precision] = (signed char)best;
   report->reduce = best;
   report->tile_tets = tets->tile_cap;
+  report->interleaved = (!f64 && tets->stage_interleaved) ? 1 : 0;
   report->ncand = nc;
   return EBB_OK;
 }

@@ -140,6 +140,7 @@ struct ebb_rel_s {
   unsigned layout_gen = 0;              // bumped whenever the tile blobs are rebuilt
   signed char tuned[2][2] = {{-1, -1}, {-1, -1}};  // autotuned reduce per [model][precision], -1 none
   int test_drop_tile = -1;              // EBB_MAP_TEST_DROP_TILE: tile whose blob copy the next map skips
+  bool stage_interleaved = false;       // FP32 tiled maps stage operands vertex-interleaved (autotuned)
   ebb::VertexIndex vindex;
 
   // ---- implicit-step scratch ----
@@ -219,6 +220,14 @@ cudaError_t launch_adjoint_map(ebb_rel_s* rel, double mu0, double lam0, const do
 ebb_status_t run_batched_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, const void* pinned,
                               const int* batch, int nmesh, const ebb_step_params_t* p, ebb_cg_report_t* reps);
 void free_batch_scratch(ebb_rel_s* rel);
+
+// Staging in the vertex-interleaved layout (reorder.cu): da/db[4 i + c] =
+// a/b[c][o(i)] (b may be null); dst[k][c][o(i)] += src[k][4 i + c] for k < n
+// (n <= 3); o(i) = vperm[i], or i when vperm is null.
+cudaError_t interleave_fields(int nv, const int* vperm, const float* a, const float* b, float* da, float* db,
+                              cudaStream_t st);
+cudaError_t deinterleave_add_fields(int nv, const int* vperm, const float* const* src, float* const* dst, int n,
+                                    cudaStream_t st);
 
 // Vertex reordering helpers (reorder.cu).  Gather: dst[c][i] = src[c][vperm[i]];
 // scatter-add: dst[c][vperm[i]] += src[c][i]; scatter: dst[c][vperm[i]] = src[c][i].

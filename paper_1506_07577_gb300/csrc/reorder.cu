@@ -1,4 +1,5 @@
-// Vertex renumbering (EBB_FINALIZE_REORDER_VERTS).
+// Vertex renumbering (EBB_FINALIZE_REORDER_VERTS) and staging of map
+// operands in the vertex-interleaved layout.
 //
 // Keys are opaque (Section 5.1 and its footnote), so the library may number
 // vertices its own way: Morton order of the rest positions, which puts the
@@ -52,6 +53,36 @@ __global__ void gather_pin_kernel(int nv, const int* __restrict__ vperm, const P
   dst[i] = src == nullptr ? 0 : (src[vperm[i]] != 0 ? 1 : 0);
 }
 
+// dst_k[4 i + c] = src_k[c][o(i)] (padding 0), o = vperm or identity, for
+// one or two fields.
+__global__ void interleave_kernel(int nv, const int* __restrict__ vperm, const float* __restrict__ a,
+                                  const float* __restrict__ b, float4* __restrict__ da, float4* __restrict__ db) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  const int o = vperm ? vperm[i] : i;
+  da[i] = make_float4(a[o], a[(size_t)nv + o], a[2 * (size_t)nv + o], 0.f);
+  if (b) db[i] = make_float4(b[o], b[(size_t)nv + o], b[2 * (size_t)nv + o], 0.f);
+}
+
+// dst_k[c][o(i)] += src_k[4 i + c] for up to three fields.
+__global__ void deinterleave_add_kernel(int nv, const int* __restrict__ vperm, const float4* __restrict__ s0,
+                                        float* d0, const float4* __restrict__ s1, float* d1,
+                                        const float4* __restrict__ s2, float* d2) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  const size_t o = vperm ? vperm[i] : i;
+  const float4* src[3] = {s0, s1, s2};
+  float* dst[3] = {d0, d1, d2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (!src[k]) continue;
+    const float4 x = src[k][i];
+    dst[k][o] += x.x;
+    dst[k][(size_t)nv + o] += x.y;
+    dst[k][2 * (size_t)nv + o] += x.z;
+  }
+}
+
 uint64_t spread3(uint64_t x) {
   x &= 0x1fffffull;
   x = (x | (x << 32)) & 0x1f00000000ffffull;
@@ -88,6 +119,27 @@ template <typename PT>
 cudaError_t gather_pinned(int nv, const int* vperm, const PT* src, unsigned char* dst, cudaStream_t st) {
   if (nv == 0) return cudaSuccess;
   gather_pin_kernel<PT><<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t interleave_fields(int nv, const int* vperm, const float* a, const float* b, float* da, float* db,
+                              cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  interleave_kernel<<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, a, b, (float4*)da, (float4*)db);
+  return cudaGetLastError();
+}
+
+cudaError_t deinterleave_add_fields(int nv, const int* vperm, const float* const* src, float* const* dst, int n,
+                                    cudaStream_t st) {
+  if (nv == 0 || n == 0) return cudaSuccess;
+  const float4* s[3] = {nullptr, nullptr, nullptr};
+  float* d[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < n && k < 3; ++k) {
+    s[k] = (const float4*)src[k];
+    d[k] = dst[k];
+  }
+  deinterleave_add_kernel<<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, s[0], d[0], s[1], d[1],
+                                                                             s[2], d[2]);
   return cudaGetLastError();
 }
 

@@ -548,9 +548,12 @@ cudaError_t configure_tiles_model() {
   if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV>();
   if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_DIAG>();
   if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV | OP_DIAG>();
-  // Vertex-interleaved variants: the implicit step's FP32 maps.
+  // Vertex-interleaved variants (FP32 only).
   if constexpr (sizeof(T) == 4) {
+    if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE, true>();
     if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_KV, true>();
+    if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV, true>();
+    if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_DIAG, true>();
     if (e == cudaSuccess) e = configure_tiles<T, MODEL, OP_FORCE | OP_KV | OP_DIAG, true>();
   }
   return e;
@@ -634,9 +637,8 @@ cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, 
   }
   if (reduce == EBB_REDUCE_TILED) {
     if (io.aos) {
-      // vertex-interleaved operands: FP32, and only the maps the step runs
-      constexpr bool kAos = sizeof(T) == 4 && (OPS == OP_KV || OPS == (OP_FORCE | OP_KV | OP_DIAG));
-      if constexpr (kAos) return launch_tiles<T, MODEL, OPS, true>(rel, mu0, lam0, io, active, stream);
+      // vertex-interleaved operands: FP32 only
+      if constexpr (sizeof(T) == 4) return launch_tiles<T, MODEL, OPS, true>(rel, mu0, lam0, io, active, stream);
       return cudaErrorInvalidValue;
     }
     return launch_tiles<T, MODEL, OPS, false>(rel, mu0, lam0, io, active, stream);

@@ -30,7 +30,13 @@ def test_autotune_report_and_parity(prec):
         dm.vertex_field("w", dt, value=w)
         rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(abi.EBB_NEOHOOKEAN, precision=p))
         cands = [(rep.cand[i].reduce, rep.cand[i].tile_tets, rep.cand[i].us) for i in range(rep.ncand)]
-        assert rep.ncand == 5  # tiled x3, atomic, colour
+        # tiled at 3 tile sizes (FP32: staged interleaved, plus in place at the best size), atomic, colour
+        assert rep.ncand == (6 if prec == "f32" else 5)
+        staged = [rep.cand[i].us for i in range(rep.ncand) if rep.cand[i].interleaved]
+        assert len(staged) == (1 if prec == "f32" else 0)
+        in_place = [rep.cand[i].us for i in range(rep.ncand)
+                    if rep.cand[i].reduce == abi.EBB_REDUCE_TILED and not rep.cand[i].interleaved]
+        assert rep.interleaved == (1 if staged and staged[0] < min(in_place) else 0)
         assert {c[1] for c in cands if c[0] == abi.EBB_REDUCE_TILED} == {128, 96, 64}
         assert all(c[2] > 0 for c in cands)
         best = min(cands, key=lambda c: c[2])
@@ -80,3 +86,50 @@ def test_step_after_retiling_matches_oracle():
             abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm)
         assert rel_err(vv.cpu().numpy().T, vo) < 1e-10
         assert rel_err(uu.cpu().numpy().T, uo) < 1e-10
+
+
+@pytest.mark.parametrize("reorder", [False, True])
+@pytest.mark.parametrize("tile_tets", [128, 64, 37])
+def test_hand_tuning_staged_interleaved_maps(reorder, tile_tets):
+    """Maps on a relation set by hand to stage FP32 operands vertex-interleaved
+    (and to re-cut tiles, including a tile size that is not a warp multiple)
+    still match the oracle, with and without reordered vertices."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(6, "nh", seed=31, permute=reorder)
+    f, Kw, d = oracle_maps(m, mu, lam, u, w, "nh")
+    with DeviceTetMesh(m.X, m.tets, mu, lam, reorder_verts=reorder) as dm:
+        dm.vertex_field("u", torch.float32, value=u)
+        dm.vertex_field("w", torch.float32, value=w)
+        out = {k: dm.vertex_field(k, torch.float32) for k in ("f", "Kw", "d", "f2")}
+        out["f2"].fill_(2.0)
+        abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_NEOHOOKEAN, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED,
+                                    tile_tets, 1)
+        o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, flags=abi.EBB_MAP_ZERO_OUT)
+        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "Kw", o)
+        abi.ebb_map_tet_diagK(dm.ctx, dm.tets, "u", "d", o)
+        o.flags = 0
+        abi.ebb_map_tet_forces(dm.ctx, dm.tets, "u", "f2", o)   # accumulates onto 2.0
+        abi.ebb_ctx_sync(dm.ctx)
+        got = {k: v.double().cpu().numpy().T for k, v in out.items()}
+    assert rel_err(got["f"], f) < 1e-5
+    assert rel_err(got["Kw"], Kw) < 1e-5
+    assert rel_err(got["d"], d) < 1e-5
+    assert rel_err(got["f2"] - 2.0, f) < 1e-5
+
+
+def test_set_tuning_rejects_bad_values():
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m = meshgen.cube_grid(2, seed=1)
+    with DeviceTetMesh(m.X, m.tets) as dm:
+        for args in ((abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED, 0, 0),
+                     (abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED, 129, 0),
+                     (abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_AUTO, 128, 0),
+                     (abi.EBB_STVK, 7, abi.EBB_REDUCE_TILED, 128, 0)):
+            with pytest.raises(abi.EbbError) as ei:
+                abi.ebb_relation_set_tuning(dm.ctx, dm.tets, *args)
+            assert ei.value.status == abi.EBB_ERR_ARG
+        with pytest.raises(abi.EbbError) as ei:   # finalized without colouring
+            abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_COLOR, 128, 0)
+        assert ei.value.status == abi.EBB_ERR_STATE
