@@ -189,8 +189,9 @@ struct MapCall {
 
 // One entry point for the four map calls.
 // Launch a map on caller-layout (3-plane) device fields: FP32 tiled maps on
-// a relation the autotuner set to stage move their operands into
-// library-owned vertex-interleaved buffers and add the results back; relations with reordered vertices stage in the internal order;
+// a relation the autotuner set to stage, or with reordered vertices, move
+// their operands into library-owned vertex-interleaved buffers and add the
+// results back; relations with reordered vertices stage in the internal order;
 // otherwise the map runs on the caller's fields directly.  Outputs are `+=`
 // targets in every case.
 ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int model, double mu, double lambda,
@@ -198,7 +199,9 @@ ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int mod
                                int nout, bool drop) {
   const int nv = (int)tets->verts->size;
   const size_t bytes = (size_t)nv * 3 * (f64 ? 8 : 4);
-  const bool stage = !f64 && reduce == EBB_REDUCE_TILED && tets->stage_interleaved;
+  // Reordered vertices are staged anyway, so their FP32 tiled maps always
+  // stage interleaved.
+  const bool stage = !f64 && reduce == EBB_REDUCE_TILED && (tets->stage_interleaved || tets->vperm != nullptr);
   void* in[2] = {in_user[0], nin > 1 ? in_user[1] : nullptr};
   void* out[3] = {nullptr, nullptr, nullptr};
   for (int i = 0; i < nout; ++i) out[i] = out_user[i];
