@@ -158,6 +158,24 @@ def cpu_baseline(seconds, m, mu, lam, u, w):
                       f"repeated for {el:.1f} s ({done} tet evaluations), numpy single thread"}
 
 
+def max_over_ranks(seconds, dist, device):
+    """The timing contract across replicas: the slowest rank's time (an
+    all-reduce MAX when `dist` is torch.distributed, the value itself when
+    it is None)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, seconds_max, world):
+    """Whole-job throughput of `world` independent replicas that each did
+    `units_per_rank` units, over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -250,12 +268,8 @@ def run_ours(args, rank, world, local_rank):
         abi.ebb_ctx_sync(dm.ctx)
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     kern_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = nt * args.steps * world / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    value = replica_throughput(nt * args.steps, total_s, world)
 
     # ---- end to end: pinned host inputs -> device -> map -> host outputs ----
     uh = u32.cpu().pin_memory()
@@ -277,11 +291,7 @@ def run_ours(args, rank, world, local_rank):
             e1.synchronize()
             if k >= args.warmup:
                 e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
     h2d = (uh.numel() + wh.numel()) * 4
     d2h = (fh.numel() + kh.numel()) * 4
 
@@ -355,7 +365,8 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof,
             "autotune": tune,
             "reduction_variants": variants,
-            "e2e": {"value": nt * args.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "clocks": clk,
