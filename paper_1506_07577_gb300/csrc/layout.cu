@@ -207,7 +207,8 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
   prefix.assign((size_t)ntiles * kBlobPrefix, 0);
   {
     std::vector<int> slot_of(nv, -1);
-    std::vector<int> vtx;
+    std::vector<int> vtx, rk, label, member_off, members;
+    std::vector<long> grp_count;
     std::vector<int> cnt(kTileSlots + 1);
     for (int ti = 0; ti < ntiles; ++ti) {
       unsigned char* b = prefix.data() + (size_t)ti * kBlobPrefix;
@@ -228,34 +229,83 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
         }
       }
       std::stable_sort(vtx.begin(), vtx.end(), [&](int x, int y) { return slot_of[x] > slot_of[y]; });
+      // Rank j = position by decreasing entry count (the reduction units
+      // follow this order).
       for (size_t j = 0; j < vtx.size(); ++j) slot_of[vtx[j]] = (int)j;
+      const int nvu = (int)vtx.size();
+      const int T = te - tb;
+      rk.resize((size_t)4 * T);
       for (int t = tb; t < te; ++t) {
         const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
-        slots[t - tb] = make_uchar4((unsigned char)slot_of[k[0]], (unsigned char)slot_of[k[1]],
-                                    (unsigned char)slot_of[k[2]], (unsigned char)slot_of[k[3]]);
+        for (int a = 0; a < 4; ++a) rk[(size_t)4 * (t - tb) + a] = slot_of[k[a]];
       }
-      const int nvu = (int)vtx.size();
+      // Slot labels: phase 1 reads slot vectors (16 bytes each) for corner a
+      // of 8 consecutive tets per shared-memory wavefront, conflict-free when
+      // their distinct slots differ mod 8.  Each rank gets the residue class
+      // that adds the fewest collisions over the (8 tets, corner) groups it
+      // belongs to (greedy, in rank order), with the labels kept compact:
+      // class c holds the labels c, c + 8, ... below nvu.
+      {
+        const int ngroups = ((T + 7) / 8) * 4;
+        grp_count.assign((size_t)ngroups * 8, 0);
+        member_off.assign(nvu + 1, 0);
+        for (int g = 0; g < ngroups; ++g) {
+          const int q0 = (g / 4) * 8, a = g % 4;
+          for (int t = q0; t < std::min(T, q0 + 8); ++t) {
+            const int r = rk[(size_t)4 * t + a];
+            bool seen = false;
+            for (int t2 = q0; t2 < t; ++t2) seen = seen || rk[(size_t)4 * t2 + a] == r;
+            if (!seen) member_off[r + 1]++;
+          }
+        }
+        for (int r = 0; r < nvu; ++r) member_off[r + 1] += member_off[r];
+        members.resize(member_off[nvu]);
+        std::vector<int> fillm(member_off.begin(), member_off.end() - 1);
+        for (int g = 0; g < ngroups; ++g) {
+          const int q0 = (g / 4) * 8, a = g % 4;
+          for (int t = q0; t < std::min(T, q0 + 8); ++t) {
+            const int r = rk[(size_t)4 * t + a];
+            bool seen = false;
+            for (int t2 = q0; t2 < t; ++t2) seen = seen || rk[(size_t)4 * t2 + a] == r;
+            if (!seen) members[fillm[r]++] = g;
+          }
+        }
+        int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        label.resize(nvu);
+        for (int r = 0; r < nvu; ++r) {
+          int best = -1;
+          long bestc = 0;
+          for (int c = 0; c < 8; ++c) {
+            const int cap = nvu > c ? (nvu - c + 7) / 8 : 0;
+            if (used[c] >= cap) continue;
+            long cost = 0;
+            for (int i = member_off[r]; i < member_off[r + 1]; ++i) cost += grp_count[(size_t)members[i] * 8 + c];
+            if (best < 0 || cost < bestc) {
+              best = c;
+              bestc = cost;
+            }
+          }
+          label[r] = best + 8 * used[best]++;
+          for (int i = member_off[r]; i < member_off[r + 1]; ++i) grp_count[(size_t)members[i] * 8 + best]++;
+        }
+      }
+      for (int t = 0; t < T; ++t)
+        slots[t] = make_uchar4((unsigned char)label[rk[(size_t)4 * t]], (unsigned char)label[rk[(size_t)4 * t + 1]],
+                               (unsigned char)label[rk[(size_t)4 * t + 2]],
+                               (unsigned char)label[rk[(size_t)4 * t + 3]]);
       std::fill(cnt.begin(), cnt.end(), 0);
-      for (int t = tb; t < te; ++t) {
-        const uchar4 s4 = slots[t - tb];
-        cnt[s4.x + 1]++;
-        cnt[s4.y + 1]++;
-        cnt[s4.z + 1]++;
-        cnt[s4.w + 1]++;
-      }
+      for (size_t i = 0; i < (size_t)4 * T; ++i) cnt[rk[i] + 1]++;
       for (int j = 0; j < nvu; ++j) cnt[j + 1] += cnt[j];
-      // Units: thread i sums a run of <= kUnitEntries entries of one slot.
-      // Consecutive units of a slot inside one warp form a segment combined
-      // by shuffles; its first lane adds the sum into the field.
+      // Units: thread i sums a run of <= kUnitEntries entries of one vertex
+      // (ranks in order).  Consecutive units of a vertex inside one warp form
+      // a segment combined by shuffles; its first lane adds the sum into the
+      // field.
       std::vector<unsigned short> grouped(cnt[nvu]);
       {
         std::vector<int> fill(cnt.begin(), cnt.begin() + nvu);
-        for (int t = tb; t < te; ++t) {
-          const uchar4 s4 = slots[t - tb];
-          const int sl[4] = {s4.x, s4.y, s4.z, s4.w};
+        for (int t = 0; t < T; ++t)
           for (int a = 0; a < 4; ++a)
-            grouped[fill[sl[a]]++] = (unsigned short)(3 * a * (kTileTets + 1) + (t - tb));
-        }
+            grouped[fill[rk[(size_t)4 * t + a]]++] = (unsigned short)(3 * a * (kTileTets + 1) + t);
       }
       int nunits = 0;
       std::vector<int> uslot;
@@ -264,7 +314,7 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
         for (int e = cnt[j]; e < cnt[j + 1]; e += kUnitEntries) {
           const int n = std::min(kUnitEntries, cnt[j + 1] - e);
           unit_ent.emplace_back(grouped.begin() + e, grouped.begin() + e + n);
-          units[nunits] = 1u | ((uint32_t)j << 14);
+          units[nunits] = 1u | ((uint32_t)label[j] << 14);
           uslot.push_back(j);
           ++nunits;
         }
@@ -281,7 +331,7 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
         units[i] |= ((uint32_t)(last - i) << 22) | ((uint32_t)head << 26);
       }
       for (int j = 0; j < nvu; ++j) {
-        bvtx[j] = vtx[j];
+        bvtx[label[j]] = vtx[j];
         slot_of[vtx[j]] = -1;
       }
       int* hdr = reinterpret_cast<int*>(b);
