@@ -319,8 +319,8 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
                                       ebb_cg_report_t* report);
 
 /* Batched form: one implicit step for each of many independent meshes
- * stored in one verts/tets relation pair (the batched meshes of the
- * spec workload list; the per-mesh step is exactly the one above).
+ * stored in one verts/tets relation pair (for example hundreds of small
+ * meshes of uneven sizes; the per-mesh step is exactly the one above).
  * `batch` names an I32 one-component vertex field giving each vertex its mesh
  * id in [0, nbatch); ids must be non-decreasing along verts (each mesh's
  * vertices contiguous) and every id must occur.  Bind the field as
