@@ -48,11 +48,12 @@ SEED = 2
 L2_FLUSH_BYTES = 256 << 20
 
 
-# DRAM bytes (read + write) per launch of the bench kernel from one ncu
-# capture on the 64^3 workload (profiles/tet_tile_kernel_fused_nh64.md).  Valid
+# DRAM bytes (read + write) per launch of the bench kernel (interleaved
+# fields) from one ncu capture on the 64^3 workload
+# (profiles/tet_tile_kernel_fused_nh64.md).  Valid
 # only while the kernel's sources are the ones captured; otherwise reported
 # as null.
-NCU_TRAFFIC = {"sources_sha256_16": "a2b7da21e43870cd", "bytes_per_launch": 117.42e6}
+NCU_TRAFFIC = {"sources_sha256_16": "601c55f25b88c320", "bytes_per_launch": 121.77e6}
 KERNEL_SOURCES = ["tet_maps.cu", "tet_math.cuh", "async_copy.cuh", "ebb_internal.h", "layout.cu"]
 
 
@@ -170,6 +171,10 @@ def cpu_baseline(seconds, m, mu, lam, u, w, f_gpu, kw_gpu):
             "gpu_parity_max_rel_err_sampled": err}
 
 
+def kern_avg_us(kern_ms):
+    return 1e3 * sum(kern_ms) / len(kern_ms)
+
+
 def max_over_ranks(seconds, dist, device):
     """The timing contract across replicas: the slowest rank's time (an
     all-reduce MAX when `dist` is torch.distributed, the value itself when
@@ -237,10 +242,17 @@ def run_ours(args, rank, world, local_rank):
     m, mu, lam, u, w = workload()
     stream = torch.cuda.Stream(device=dev)
     dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream, colour=True)
-    u32 = dm.vertex_field("u32", torch.float32, value=u)
-    w32 = dm.vertex_field("w32", torch.float32, value=w)
-    f = dm.vertex_field("f", torch.float32)
-    Kw = dm.vertex_field("Kw", torch.float32)
+    # Vector fields stored element by element (EBB_F32X4: x, y, z, padding), the
+    # per-field contiguous vec3 storage of Section 6.1 padded to 16 bytes; the
+    # same map on 3-plane fields is reported under "layouts".
+    u32 = dm.vertex_field("u32", value=u, x4=True)
+    w32 = dm.vertex_field("w32", value=w, x4=True)
+    f = dm.vertex_field("f", x4=True)
+    Kw = dm.vertex_field("Kw", x4=True)
+    dm.vertex_field("u32p", torch.float32, value=u)
+    dm.vertex_field("w32p", torch.float32, value=w)
+    dm.vertex_field("fp", torch.float32)
+    dm.vertex_field("Kwp", torch.float32)
     opts = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
     # The autotuner picks the tile size and reduction variant EBB_REDUCE_AUTO
     # resolves to (timing the K w map on these fields); untimed set-up.
@@ -307,8 +319,8 @@ def run_ours(args, rank, world, local_rank):
     h2d = (uh.numel() + wh.numel()) * 4
     d2h = (fh.numel() + kh.numel()) * 4
 
-    f_last = fh.double().numpy().T.copy()
-    kw_last = kh.double().numpy().T.copy()
+    f_last = fh[:, :3].double().numpy().copy()
+    kw_last = kh[:, :3].double().numpy().copy()
 
     # ---- reduction variants of the fused map (kernel time only) ----------
     variants = {}
@@ -330,6 +342,26 @@ def run_ours(args, rank, world, local_rank):
                     ts.append(a.elapsed_time(b) * 1e3)
         variants[name] = {"us": statistics.median(ts), "tets_per_s": nt / (statistics.median(ts) * 1e-6)}
 
+    # ---- field layouts: the same tiled map on 3-plane fields --------------
+    layouts = {"f32x4": {"us": kern_avg_us(kern_ms)}}
+    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
+    ts = []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup + 5):
+            flush.fill_(float(k))
+            dm._tensors["fp"].zero_()
+            dm._tensors["Kwp"].zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32p", "w32p", "fp", "Kwp", o)
+            b.record(stream)
+            b.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b) * 1e3)
+    layouts["planes"] = {"us": statistics.median(ts)}
+    for v in layouts.values():
+        v["tets_per_s"] = nt / (v["us"] * 1e-6)
+
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
     bat = batched_steps(abi, torch, local_rank, args) if args.batch_meshes > 0 else None
@@ -344,9 +376,9 @@ def run_ours(args, rank, world, local_rank):
     traffic = NCU_TRAFFIC["bytes_per_launch"] if kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"] else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
-            "kernel": {"tiled": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV>",
-                       "atomic": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic>",
-                       "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured>"}[tune["reduce"]],
+            "kernel": {"tiled": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved>",
+                       "atomic": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic, interleaved>",
+                       "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured, interleaved>"}[tune["reduce"]],
             "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
 
     dm.close()
@@ -357,12 +389,13 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64^3 cube grid, 5 tets/cube (274,625 verts, 1,310,720 tets), NH, "
                                    "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, reduction variant "
-                                   "and tile size from the autotuner",
+                                   "and tile size from the autotuner, vector fields stored as 4-float elements",
                        "n_tets": nt, "n_verts": m.n_verts, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
             "autotune": tune,
             "reduction_variants": variants,
+            "layouts": layouts,
             "e2e": {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

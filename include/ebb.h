@@ -62,7 +62,15 @@ typedef int32_t ebb_status_t;
 #define EBB_ERR_STATE          9  /* call out of order (e.g. map before finalize) */
 #define EBB_ERR_NOMEM         10  /* device allocation failed */
 
-typedef enum { EBB_F32 = 1, EBB_F64 = 2, EBB_I32 = 3, EBB_U8 = 4 } ebb_dtype_t;
+/* Field element types.  A field of ncomp components is stored as ncomp
+ * contiguous planes of `size` values (plane c holds component c of every
+ * row), except EBB_F32X4: FP32 3-vectors stored element by element as four
+ * floats (x, y, z, and a padding value the maps ignore: reductions add zero
+ * to it, EBB_MAP_ZERO_OUT zeroes it), ncomp 3, the pointer 16-byte aligned
+ * -- Section 6.1's per-field
+ * contiguous array of vector-valued elements, padded so that one element is
+ * one 16-byte vector load or vector atomic. */
+typedef enum { EBB_F32 = 1, EBB_F64 = 2, EBB_I32 = 3, EBB_U8 = 4, EBB_F32X4 = 5 } ebb_dtype_t;
 
 /* Material models.  Section 7.2 names St. Venant-Kirchhoff, Section 7.3
  * neo-Hookean; the paper prints neither formula, the library uses the
@@ -201,7 +209,8 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags);
 /* Vertex-field arguments are names of fields bound on the key target of
  * tets.v.  `u` is the displacement from the rest shape (x = X + u), so
  * F = Ds Dm^-1 = I + Du Dm^-1.  Field dtypes must match opts->precision
- * (F64 or F32, 3 components).  Outputs are reduce(+=) targets: the map adds
+ * (F64 or F32, 3 components; in F32 either all EBB_F32 planes or all
+ * EBB_F32X4 elements).  Outputs are reduce(+=) targets: the map adds
  * into them (zero them first or pass EBB_MAP_ZERO_OUT).  An output that is
  * also an input of the same map is a phase error (EBB_ERR_PHASE). */
 

@@ -35,7 +35,7 @@ EBB_ERR_STATE = 9
 EBB_ERR_NOMEM = 10
 STATUS_NAMES = {v: k for k, v in dict(globals()).items() if k.startswith("EBB_ERR_") or k == "EBB_OK"}
 
-EBB_F32, EBB_F64, EBB_I32, EBB_U8 = 1, 2, 3, 4
+EBB_F32, EBB_F64, EBB_I32, EBB_U8, EBB_F32X4 = 1, 2, 3, 4, 5
 EBB_STVK, EBB_NEOHOOKEAN = 0, 1
 EBB_PREC_F64, EBB_PREC_F32 = 0, 1
 EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED = 0, 1, 2, 3
@@ -174,11 +174,18 @@ def ebb_relation_create(ctx, name, size):
 _DT = {"torch.float32": EBB_F32, "torch.float64": EBB_F64, "torch.int32": EBB_I32, "torch.uint8": EBB_U8}
 
 
-def ebb_field_bind(ctx, rel, name, tensor, key_target=None):
+def ebb_field_bind(ctx, rel, name, tensor, key_target=None, x4=False):
     """Bind a CUDA tensor shaped (ncomp, rows) or (rows,) as a column-store
-    field (ncomp contiguous planes).  The tensor must stay alive while bound."""
+    field (ncomp contiguous planes), or with ``x4`` a float32 tensor shaped
+    (rows, 4) as an EBB_F32X4 field of 3-vectors (x, y, z, padding).  The
+    tensor must stay alive while bound."""
     if not tensor.is_cuda or not tensor.is_contiguous():
         raise ValueError("fields must be contiguous CUDA tensors")
+    if x4:
+        if str(tensor.dtype) != "torch.float32" or tensor.dim() != 2 or int(tensor.shape[1]) != 4:
+            raise ValueError("EBB_F32X4 fields are float32 tensors shaped (rows, 4)")
+        return _check(ctx, _lib.ebb_field_bind(rel, _b(name), EBB_F32X4, 3, C.c_void_p(tensor.data_ptr()),
+                                               key_target))
     dt = _DT.get(str(tensor.dtype))
     if dt is None:
         raise ValueError(f"unsupported dtype {tensor.dtype}")

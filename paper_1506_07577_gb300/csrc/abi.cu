@@ -6,6 +6,7 @@
 // of bounds, Section 5.1) and precomputes the per-tet rest-shape data the
 // maps read.  The phase rule of Section 4.1 is enforced per map call: a
 // field that a map reduces into may not also be read by it.
+#include <cstdint>
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -39,6 +40,7 @@ size_t dtype_size(ebb_dtype_t d) {
     case EBB_F64: return 8;
     case EBB_I32: return 4;
     case EBB_U8: return 1;
+    case EBB_F32X4: return 4;
   }
   return 0;
 }
@@ -158,7 +160,6 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
   return pa < pb + nb && pb < pa + na;
 }
 
-// Resolve a vertex field used by a map; checks dtype and width.
 // EBB_REDUCE_AUTO: the autotuned variant for this model and precision, else
 // the tiled one.
 ebb_reduce_t resolve_reduce(const ebb_rel_s* tets, ebb_reduce_t r, int model, int precision) {
@@ -170,6 +171,7 @@ ebb_reduce_t resolve_reduce(const ebb_rel_s* tets, ebb_reduce_t r, int model, in
   return EBB_REDUCE_TILED;
 }
 
+// Resolve a vertex field used by a map or step; checks dtype and width.
 ebb_status_t vertex_field(ebb_ctx_s* ctx, ebb_rel_s* tets, const char* name, ebb_dtype_t want, int ncomp,
                           void** out) {
   if (!name) return set_error(ctx, EBB_ERR_ARG, "null field name");
@@ -188,6 +190,26 @@ struct MapCall {
 };
 
 // One entry point for the four map calls.
+// Resolve the vertex fields of one map call: F64 planes, or F32 as all
+// planes or all EBB_F32X4 elements (*x4 reports which).
+ebb_status_t map_fields(ebb_ctx_s* ctx, ebb_rel_s* tets, const char* const* names, int n, bool f64, void** out,
+                        bool* x4) {
+  *x4 = false;
+  for (int i = 0; i < n; ++i) {
+    if (!names[i]) return set_error(ctx, EBB_ERR_ARG, "null field name");
+    const Field* f = find_field(tets->verts, names[i]);
+    if (!f) return set_error(ctx, EBB_ERR_ARG, std::string("no vertex field named '") + names[i] + "'");
+    const bool ok = f->ncomp == 3 && (f64 ? f->dtype == EBB_F64 : (f->dtype == EBB_F32 || f->dtype == EBB_F32X4));
+    if (!ok)
+      return set_error(ctx, EBB_ERR_ARG, std::string("vertex field '") + names[i] + "' has the wrong dtype or width");
+    const bool fx4 = f->dtype == EBB_F32X4;
+    if (i == 0) *x4 = fx4;
+    if (fx4 != *x4) return set_error(ctx, EBB_ERR_ARG, "a map's F32 fields must all be planes or all EBB_F32X4");
+    out[i] = f->ptr;
+  }
+  return EBB_OK;
+}
+
 // Launch a map on caller-layout (3-plane) device fields: FP32 tiled maps on
 // a relation the autotuner set to stage, or with reordered vertices, move
 // their operands into library-owned vertex-interleaved buffers and add the
@@ -195,24 +217,30 @@ struct MapCall {
 // otherwise the map runs on the caller's fields directly.  Outputs are `+=`
 // targets in every case.
 ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int model, double mu, double lambda,
-                               ebb_reduce_t reduce, bool f64, void* const* in_user, int nin, void* const* out_user,
-                               int nout, bool drop) {
+                               ebb_reduce_t reduce, bool f64, bool x4, void* const* in_user, int nin,
+                               void* const* out_user, int nout, bool drop) {
   const int nv = (int)tets->verts->size;
-  const size_t bytes = (size_t)nv * 3 * (f64 ? 8 : 4);
+  const size_t bytes = (size_t)nv * (x4 ? 16 : 3 * (f64 ? 8 : 4));
   // Reordered vertices are staged anyway, so their FP32 tiled maps always
-  // stage interleaved.
-  const bool stage = !f64 && reduce == EBB_REDUCE_TILED && (tets->stage_interleaved || tets->vperm != nullptr);
+  // stage interleaved.  EBB_F32X4 fields are interleaved already.
+  const bool stage =
+      !x4 && !f64 && reduce == EBB_REDUCE_TILED && (tets->stage_interleaved || tets->vperm != nullptr);
   void* in[2] = {in_user[0], nin > 1 ? in_user[1] : nullptr};
   void* out[3] = {nullptr, nullptr, nullptr};
   for (int i = 0; i < nout; ++i) out[i] = out_user[i];
-  if (stage || tets->vperm) {
+  if (stage || tets->vperm) {   // (EBB_F32X4 fields with reordered vertices are permuted as whole elements)
     for (int i = 0; i < 5; ++i)   // 3 nv doubles: holds either precision and the interleaved FP32 layout
       if (!tets->vscratch[i] && cudaMalloc(&tets->vscratch[i], (size_t)nv * 3 * 8 + 16) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, EBB_ERR_NOMEM, "device allocation for staged map operands failed");
       }
     cudaError_t ge = cudaSuccess;
-    if (stage) {
+    if (x4) {
+      for (int i = 0; i < nin && ge == cudaSuccess; ++i) {
+        ge = permute_vec4(nv, tets->vperm, (const float*)in[i], (float*)tets->vscratch[i], ctx->stream);
+        in[i] = tets->vscratch[i];
+      }
+    } else if (stage) {
       ge = interleave_fields(nv, tets->vperm, (const float*)in[0], (const float*)in[1], (float*)tets->vscratch[0],
                              (float*)tets->vscratch[1], ctx->stream);
       in[0] = tets->vscratch[0];
@@ -228,7 +256,7 @@ ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int mod
     }
     for (int i = 0; i < nout && ge == cudaSuccess; ++i) {
       out[i] = tets->vscratch[2 + i];
-      ge = cudaMemsetAsync(out[i], 0, stage ? (size_t)nv * 16 : bytes, ctx->stream);
+      ge = cudaMemsetAsync(out[i], 0, (stage || x4) ? (size_t)nv * 16 : bytes, ctx->stream);
     }
     if (ge != cudaSuccess) return cuda_check(ctx, ge, "staging map operands");
   }
@@ -251,12 +279,15 @@ ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int mod
     if (ops & OP_FORCE) io.f = (float*)out[oi++];
     if (ops & OP_KV) io.Kw = (float*)out[oi++];
     if (ops & OP_DIAG) io.d = (float*)out[oi++];
-    io.aos = stage;
+    io.aos = stage || x4;
     tets->test_drop_tile = drop ? 0 : -1;
     e = launch_tet_map<float>(tets, model, ops, reduce, (float)mu, (float)lambda, io, nullptr, ctx->stream);
     tets->test_drop_tile = -1;
   }
-  if (e == cudaSuccess && stage) {
+  if (e == cudaSuccess && x4 && tets->vperm) {
+    for (int i = 0; i < nout && e == cudaSuccess; ++i)
+      e = permute_add_vec4(nv, tets->vperm, (const float*)out[i], (float*)out_user[i], ctx->stream);
+  } else if (e == cudaSuccess && stage) {
     e = deinterleave_add_fields(nv, tets->vperm, (const float* const*)out, (float* const*)out_user, nout,
                                 ctx->stream);
   } else if (e == cudaSuccess && tets->vperm) {
@@ -285,19 +316,20 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
   const bool f64 = opts->precision == EBB_PREC_F64;
-  const ebb_dtype_t dt = f64 ? EBB_F64 : EBB_F32;
-  const size_t bytes = (size_t)tets->verts->size * 3 * (f64 ? 8 : 4);
-
   void* in[2] = {nullptr, nullptr};
   void* out[3] = {nullptr, nullptr, nullptr};
-  for (int i = 0; i < mc.nin; ++i) {
-    ebb_status_t s = vertex_field(ctx, tets, mc.in[i], dt, 3, &in[i]);
+  const char* names[5];
+  void* ptrs[5];
+  for (int i = 0; i < mc.nin; ++i) names[i] = mc.in[i];
+  for (int i = 0; i < mc.nout; ++i) names[mc.nin + i] = mc.out[i];
+  bool x4 = false;
+  {
+    ebb_status_t s = map_fields(ctx, tets, names, mc.nin + mc.nout, f64, ptrs, &x4);
     if (s) return s;
   }
-  for (int i = 0; i < mc.nout; ++i) {
-    ebb_status_t s = vertex_field(ctx, tets, mc.out[i], dt, 3, &out[i]);
-    if (s) return s;
-  }
+  for (int i = 0; i < mc.nin; ++i) in[i] = ptrs[i];
+  for (int i = 0; i < mc.nout; ++i) out[i] = ptrs[mc.nin + i];
+  const size_t bytes = (size_t)tets->verts->size * (x4 ? 16 : 3 * (f64 ? 8 : 4));
   // Phase rule: a reduce target may not be read by the same map, nor be
   // reduced into twice.
   for (int i = 0; i < mc.nout; ++i) {
@@ -318,7 +350,7 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
       if (s) return s;
     }
   }
-  return launch_map_staged(ctx, tets, ops, opts->model, opts->mu, opts->lambda, reduce, f64, in, mc.nin, out,
+  return launch_map_staged(ctx, tets, ops, opts->model, opts->mu, opts->lambda, reduce, f64, x4, in, mc.nin, out,
                            mc.nout, drop);
 }
 
@@ -401,6 +433,8 @@ ebb_status_t ebb_field_bind(ebb_rel_t rel, const char* name, ebb_dtype_t dtype, 
   if (ncomp < 1 || ncomp > 16) return set_error(ctx, EBB_ERR_ARG, "ncomp out of range [1,16]");
   if (!device_ptr && rel->size > 0) return set_error(ctx, EBB_ERR_ARG, "null device pointer");
   if (key_target && dtype != EBB_I32) return set_error(ctx, EBB_ERR_ARG, "key-fields must be I32");
+  if (dtype == EBB_F32X4 && (ncomp != 3 || ((uintptr_t)device_ptr & 15u) != 0))
+    return set_error(ctx, EBB_ERR_ARG, "EBB_F32X4 fields need ncomp 3 and a 16-byte aligned pointer");
   if (key_target && key_target->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "key target in another context");
   Field f;
   f.name = name;
@@ -677,15 +711,15 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
   if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   const bool f64 = opts->precision == EBB_PREC_F64;
-  const ebb_dtype_t dt = f64 ? EBB_F64 : EBB_F32;
   void* in[2] = {nullptr, nullptr};
-  ebb_status_t s = vertex_field(ctx, tets, u, dt, 3, &in[0]);
-  if (!s) s = vertex_field(ctx, tets, w, dt, 3, &in[1]);
+  bool x4 = false;
+  const char* names[2] = {u, w};
+  ebb_status_t s = map_fields(ctx, tets, names, 2, f64, in, &x4);
   if (s) return s;
   s = read_device_error(ctx);
   if (s) return s;
   const int nv = (int)tets->verts->size;
-  const size_t bytes = (size_t)nv * 3 * (f64 ? 8 : 4);
+  const size_t bytes = (size_t)nv * (x4 ? 16 : 3 * (f64 ? 8 : 4));
   cudaStream_t st = ctx->stream;
   void* out[1] = {nullptr};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -710,8 +744,8 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
       cudaError_t e = cudaMemsetAsync(out[0], 0, bytes, st);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
       if (e != cudaSuccess) return cuda_check(ctx, e, "autotune timing");
-      ebb_status_t ms = launch_map_staged(ctx, tets, OP_KV, opts->model, opts->mu, opts->lambda, reduce, f64, in, 2,
-                                          out, 1, false);
+      ebb_status_t ms = launch_map_staged(ctx, tets, OP_KV, opts->model, opts->mu, opts->lambda, reduce, f64, x4, in,
+                                          2, out, 1, false);
       if (ms) return ms;
       e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -738,14 +772,14 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
     double us = 0.0;
     s = time_map(EBB_REDUCE_TILED, &us);
     if (s) break;
-    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], 0, us};
+    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], x4 ? 1 : 0, us};
     if (us < best_tiled_us) {
       best_tiled_us = us;
       best_cap = caps[ci];
     }
   }
   if (!s && tets->tile_cap != best_cap) s = rebuild_tiles(ctx, tets, best_cap);
-  if (!s && !f64) {
+  if (!s && !f64 && !x4) {
     // the same tile size with the operands staged vertex-interleaved
     tets->stage_interleaved = true;
     double us = 0.0;
@@ -762,7 +796,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
     double us = 0.0;
     s = time_map(others[oi], &us);
     if (s) break;
-    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, 0, us};
+    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, x4 ? 1 : 0, us};
     if (us < best_us) {
       best_us = us;
       best = others[oi];
@@ -776,7 +810,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
   tets->tuned[opts->model][opts->precision] = (signed char)best;
   report->reduce = best;
   report->tile_tets = tets->tile_cap;
-  report->interleaved = (!f64 && tets->stage_interleaved) ? 1 : 0;
+  report->interleaved = (!f64 && (x4 || tets->stage_interleaved)) ? 1 : 0;
   report->ncand = nc;
   return EBB_OK;
 }

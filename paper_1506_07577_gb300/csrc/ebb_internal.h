@@ -228,6 +228,10 @@ cudaError_t interleave_fields(int nv, const int* vperm, const float* a, const fl
                               cudaStream_t st);
 cudaError_t deinterleave_add_fields(int nv, const int* vperm, const float* const* src, float* const* dst, int n,
                                     cudaStream_t st);
+// Interleaved (4-float) elements in the internal vertex order: dst[i] =
+// src[vperm[i]], and dst[vperm[i]].xyz += src[i].xyz.
+cudaError_t permute_vec4(int nv, const int* vperm, const float* src, float* dst, cudaStream_t st);
+cudaError_t permute_add_vec4(int nv, const int* vperm, const float* src, float* dst, cudaStream_t st);
 
 // Vertex reordering helpers (reorder.cu).  Gather: dst[c][i] = src[c][vperm[i]];
 // scatter-add: dst[c][vperm[i]] += src[c][i]; scatter: dst[c][vperm[i]] = src[c][i].

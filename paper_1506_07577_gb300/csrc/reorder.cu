@@ -83,6 +83,24 @@ __global__ void deinterleave_add_kernel(int nv, const int* __restrict__ vperm, c
   }
 }
 
+__global__ void permute_vec4_kernel(int nv, const int* __restrict__ vperm, const float4* __restrict__ src,
+                                    float4* __restrict__ dst) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i < nv) dst[i] = src[vperm[i]];
+}
+
+__global__ void permute_add_vec4_kernel(int nv, const int* __restrict__ vperm, const float4* __restrict__ src,
+                                        float4* dst) {
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= nv) return;
+  const float4 s = src[i];
+  float4 d = dst[vperm[i]];
+  d.x += s.x;
+  d.y += s.y;
+  d.z += s.z;
+  dst[vperm[i]] = d;
+}
+
 uint64_t spread3(uint64_t x) {
   x &= 0x1fffffull;
   x = (x | (x << 32)) & 0x1f00000000ffffull;
@@ -119,6 +137,20 @@ template <typename PT>
 cudaError_t gather_pinned(int nv, const int* vperm, const PT* src, unsigned char* dst, cudaStream_t st) {
   if (nv == 0) return cudaSuccess;
   gather_pin_kernel<PT><<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t permute_vec4(int nv, const int* vperm, const float* src, float* dst, cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  permute_vec4_kernel<<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, (const float4*)src,
+                                                                          (float4*)dst);
+  return cudaGetLastError();
+}
+
+cudaError_t permute_add_vec4(int nv, const int* vperm, const float* src, float* dst, cudaStream_t st) {
+  if (nv == 0) return cudaSuccess;
+  permute_add_vec4_kernel<<<(nv + kThreads - 1) / kThreads, kThreads, 0, st>>>(nv, vperm, (const float4*)src,
+                                                                              (float4*)dst);
   return cudaGetLastError();
 }
 

@@ -121,7 +121,10 @@ __device__ __forceinline__ void load_tet(const TetStreams<T>& s, int nt, int t, 
 }
 
 // ---- direct: one thread per tet -------------------------------------------
-template <typename T, int MODEL, int OPS, bool ATOMIC>
+// AOS: vertex-interleaved operands (MapIO::aos, FP32): one 16-byte load per
+// corner and field, one vector atomic (or one 16-byte read-modify-write)
+// per corner and output.
+template <typename T, int MODEL, int OPS, bool ATOMIC, bool AOS>
 __global__ void __launch_bounds__(kMapThreads)
 tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ keys, const int* __restrict__ perm,
                TetStreams<T> s, T mu0, T lam0, MapIO<T> io, const int* active, int* err) {
@@ -133,17 +136,37 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
   T B[9], V, mu, lam;
   load_tet(s, nt, t, mu0, lam0, B, V, mu, lam);
   T Du[9], Dw[9];
+  if constexpr (AOS) {
+    float4 q[4], r[4];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const T* uc = io.u + (size_t)c * nv;
-    const T u0 = uc[kk[0]];
+    for (int a = 0; a < 4; ++a) {
+      q[a] = reinterpret_cast<const float4*>(io.u)[kk[a]];
+      if (OPS & OP_KV) r[a] = reinterpret_cast<const float4*>(io.w)[kk[a]];
+    }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) Du[c * 3 + j] = uc[kk[j + 1]] - u0;
-    if (OPS & OP_KV) {
-      const T* wc = io.w + (size_t)c * nv;
-      const T w0 = wc[kk[0]];
+    for (int j = 0; j < 3; ++j) {
+      Du[0 * 3 + j] = q[j + 1].x - q[0].x;
+      Du[1 * 3 + j] = q[j + 1].y - q[0].y;
+      Du[2 * 3 + j] = q[j + 1].z - q[0].z;
+      if (OPS & OP_KV) {
+        Dw[0 * 3 + j] = r[j + 1].x - r[0].x;
+        Dw[1 * 3 + j] = r[j + 1].y - r[0].y;
+        Dw[2 * 3 + j] = r[j + 1].z - r[0].z;
+      }
+    }
+  } else {
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Dw[c * 3 + j] = wc[kk[j + 1]] - w0;
+    for (int c = 0; c < 3; ++c) {
+      const T* uc = io.u + (size_t)c * nv;
+      const T u0 = uc[kk[0]];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Du[c * 3 + j] = uc[kk[j + 1]] - u0;
+      if (OPS & OP_KV) {
+        const T* wc = io.w + (size_t)c * nv;
+        const T w0 = wc[kk[0]];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Dw[c * 3 + j] = wc[kk[j + 1]] - w0;
+      }
     }
   }
   T fo[4][3], ko[4][3], dgo[4][3];
@@ -151,19 +174,42 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
     raise_error(err, EBB_ERR_INVERTED, perm[t]);
     return;
   }
+  if constexpr (AOS) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < 4; ++a) {
+      const T* vals[3] = {fo[a], ko[a], dgo[a]};
+      T* outs[3] = {io.f, io.Kw, io.d};
+      const int on[3] = {OPS & OP_FORCE, OPS & OP_KV, OPS & OP_DIAG};
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const size_t o = (size_t)c * nv + kk[a];
-      if (ATOMIC) {
-        if (OPS & OP_FORCE) atomicAdd(io.f + o, fo[a][c]);
-        if (OPS & OP_KV) atomicAdd(io.Kw + o, ko[a][c]);
-        if (OPS & OP_DIAG) atomicAdd(io.d + o, dgo[a][c]);
-      } else {
-        if (OPS & OP_FORCE) io.f[o] += fo[a][c];
-        if (OPS & OP_KV) io.Kw[o] += ko[a][c];
-        if (OPS & OP_DIAG) io.d[o] += dgo[a][c];
+      for (int k = 0; k < 3; ++k) {
+        if (!on[k]) continue;
+        float* p = outs[k] + 4 * (size_t)kk[a];
+        if (ATOMIC) {
+          red_add_v4(p, vals[k][0], vals[k][1], vals[k][2]);
+        } else {
+          float4 x = *reinterpret_cast<float4*>(p);
+          x.x += vals[k][0];
+          x.y += vals[k][1];
+          x.z += vals[k][2];
+          *reinterpret_cast<float4*>(p) = x;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const size_t o = (size_t)c * nv + kk[a];
+        if (ATOMIC) {
+          if (OPS & OP_FORCE) atomicAdd(io.f + o, fo[a][c]);
+          if (OPS & OP_KV) atomicAdd(io.Kw + o, ko[a][c]);
+          if (OPS & OP_DIAG) atomicAdd(io.d + o, dgo[a][c]);
+        } else {
+          if (OPS & OP_FORCE) io.f[o] += fo[a][c];
+          if (OPS & OP_KV) io.Kw[o] += ko[a][c];
+          if (OPS & OP_DIAG) io.d[o] += dgo[a][c];
+        }
       }
     }
   }
@@ -603,8 +649,16 @@ cudaError_t launch_range(int b, int e, int nt, int nv, const int4* keys, const i
   const int n = e - b;
   if (n <= 0) return cudaSuccess;
   const int grid = (n + kMapThreads - 1) / kMapThreads;
-  tet_map_kernel<T, MODEL, OPS, ATOMIC><<<grid, kMapThreads, 0, stream>>>(b, e, nt, nv, keys, perm, s, mu0, lam0,
-                                                                          io, active, err);
+  if (io.aos) {
+    if constexpr (sizeof(T) == 4) {
+      tet_map_kernel<T, MODEL, OPS, ATOMIC, true><<<grid, kMapThreads, 0, stream>>>(b, e, nt, nv, keys, perm, s, mu0,
+                                                                                    lam0, io, active, err);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
+  tet_map_kernel<T, MODEL, OPS, ATOMIC, false><<<grid, kMapThreads, 0, stream>>>(b, e, nt, nv, keys, perm, s, mu0,
+                                                                                 lam0, io, active, err);
   return cudaGetLastError();
 }
 
@@ -643,7 +697,6 @@ cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, 
     }
     return launch_tiles<T, MODEL, OPS, false>(rel, mu0, lam0, io, active, stream);
   }
-  if (io.aos) return cudaErrorInvalidValue;
   return launch_range<T, MODEL, OPS, true>(0, nt, nt, nv, rel->keys, rel->tet_perm, streams_of<T>(rel, false), mu0,
                                            lam0, io, active, err, stream);
 }

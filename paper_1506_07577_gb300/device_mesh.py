@@ -49,10 +49,19 @@ class DeviceTetMesh:
         self._tensors[name] = t
         return t
 
-    def vertex_field(self, name, dtype=torch.float64, ncomp=3, value=None):
+    def vertex_field(self, name, dtype=torch.float64, ncomp=3, value=None, x4=False):
         """Allocate (or upload) a vertex field of shape (ncomp, N_v), bind it
         under ``name`` and return the tensor.  ``value`` may be an (N_v, ncomp)
-        numpy array."""
+        numpy array.  With ``x4`` the field is an EBB_F32X4 field: a float32
+        tensor of shape (N_v, 4) whose first three columns hold the vectors."""
+        if x4:
+            t = torch.zeros((self.n_verts, 4), dtype=torch.float32, device=self.device)
+            if value is not None:
+                t[:, :3] = torch.from_numpy(np.ascontiguousarray(np.asarray(value, dtype=np.float32))).to(self.device)
+            torch.cuda.synchronize(self.device)
+            abi.ebb_field_bind(self.ctx, self.verts, name, t, x4=True)
+            self._tensors[name] = t
+            return t
         if value is not None:
             arr = np.asarray(value)
             arr = arr.T if arr.ndim == 2 else arr

@@ -33,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
     ap.add_argument("--permute", action="store_true")
+    ap.add_argument("--x4", action="store_true", help="FP32 vector fields as EBB_F32X4 elements")
     ap.add_argument("--iters", type=int, default=3)
     a = ap.parse_args(argv)
 
@@ -44,10 +45,11 @@ def main(argv=None):
     mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED, "colour": abi.EBB_REDUCE_COLOR}[a.variant]
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=(a.variant == "colour")) as dm:
-        dm.vertex_field("u", dt, value=u)
-        dm.vertex_field("w", dt, value=w)
-        dm.vertex_field("f", dt)
-        dm.vertex_field("k", dt)
+        x4 = a.x4 and a.prec == "f32"
+        dm.vertex_field("u", dt, value=u, x4=x4)
+        dm.vertex_field("w", dt, value=w, x4=x4)
+        dm.vertex_field("f", dt, x4=x4)
+        dm.vertex_field("k", dt, x4=x4)
         o = abi.map_opts(mdl, precision=abi.EBB_PREC_F32 if a.prec == "f32" else abi.EBB_PREC_F64, reduce=red,
                          flags=abi.EBB_MAP_ZERO_OUT)
         if a.ops == "step":

@@ -48,7 +48,7 @@ def test_binding_constants_match_header(abi):
             continue
         assert getattr(abi, k) == v, k
     src = open(HEADER).read()
-    for name, val in re.findall(r"(EBB_(?:F32|F64|I32|U8|STVK|NEOHOOKEAN|PREC_F64|PREC_F32|REDUCE_\w+))\s*=\s*(\d+)",
+    for name, val in re.findall(r"(EBB_(?:F32X4|F32|F64|I32|U8|STVK|NEOHOOKEAN|PREC_F64|PREC_F32|REDUCE_\w+))\s*=\s*(\d+)",
                                 src):
         assert getattr(abi, name) == int(val), name
 
