@@ -599,24 +599,32 @@ def permuted_sweep(abi, torch, local_rank, args, peak):
     t0 = time.perf_counter()
     dm = DeviceTetMesh(m.X, m.tets, device=local_rank, colour=True)
     setup_s = time.perf_counter() - t0
-    dm.vertex_field("u", torch.float32, value=u)
-    dm.vertex_field("w", torch.float32, value=w)
-    f = dm.vertex_field("f", torch.float32)
-    k = dm.vertex_field("k", torch.float32)
+    # 4-float vector elements (EBB_F32X4) as in the main line; "tiled_planes"
+    # repeats the tiled map on 3-plane fields
+    dm.vertex_field("u", value=u, x4=True)
+    dm.vertex_field("w", value=w, x4=True)
+    f = dm.vertex_field("f", x4=True)
+    k = dm.vertex_field("k", x4=True)
+    dm.vertex_field("up", torch.float32, value=u)
+    dm.vertex_field("wp", torch.float32, value=w)
+    fp = dm.vertex_field("fp", torch.float32)
+    kp = dm.vertex_field("kp", torch.float32)
     bpt = 16 + 36 + 4 + 4 * 12 * m.n_verts / m.n_tets
     out = {"n_tets": m.n_tets, "n_verts": m.n_verts, "finalize_with_colouring_s": setup_s,
            "algorithmic_bytes_per_tet": bpt}
     t0 = time.perf_counter()
     dmr = DeviceTetMesh(m.X, m.tets, device=local_rank, reorder_verts=True)
     out["finalize_with_vertex_reorder_s"] = time.perf_counter() - t0
-    dmr.vertex_field("u", torch.float32, value=u)
-    dmr.vertex_field("w", torch.float32, value=w)
-    fr = dmr.vertex_field("f", torch.float32)
-    kr = dmr.vertex_field("k", torch.float32)
-    for name, red, mesh, ff, kk in (("tiled", abi.EBB_REDUCE_TILED, dm, f, k),
-                                    ("tiled_vertex_reordered", abi.EBB_REDUCE_TILED, dmr, fr, kr),
-                                    ("atomic", abi.EBB_REDUCE_ATOMIC, dm, f, k),
-                                    ("colour", abi.EBB_REDUCE_COLOR, dm, f, k)):
+    dmr.vertex_field("u", value=u, x4=True)
+    dmr.vertex_field("w", value=w, x4=True)
+    fr = dmr.vertex_field("f", x4=True)
+    kr = dmr.vertex_field("k", x4=True)
+    names = ("u", "w", "f", "k")
+    for name, red, mesh, ff, kk, nm in (("tiled", abi.EBB_REDUCE_TILED, dm, f, k, names),
+                                        ("tiled_planes", abi.EBB_REDUCE_TILED, dm, fp, kp, ("up", "wp", "fp", "kp")),
+                                        ("tiled_vertex_reordered", abi.EBB_REDUCE_TILED, dmr, fr, kr, names),
+                                        ("atomic", abi.EBB_REDUCE_ATOMIC, dm, f, k, names),
+                                        ("colour", abi.EBB_REDUCE_COLOR, dm, f, k, names)):
         o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
         ts = []
         for it in range(3 + 5):
@@ -625,7 +633,7 @@ def permuted_sweep(abi, torch, local_rank, args, peak):
             kk.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            abi.ebb_map_tet_force_Kv(mesh.ctx, mesh.tets, "u", "w", "f", "k", o)
+            abi.ebb_map_tet_force_Kv(mesh.ctx, mesh.tets, *nm, o)
             b.record()
             b.synchronize()
             if it >= 3:
@@ -633,7 +641,8 @@ def permuted_sweep(abi, torch, local_rank, args, peak):
         t = statistics.median(ts)
         gbs = bpt * m.n_tets / t / 1e9
         out[name] = {"us": t * 1e6, "tets_per_s": m.n_tets / t, "algorithmic_GBps": gbs, "frac_of_peak": gbs / peak}
-    out["tiled_vertex_reordered"]["note"] = "includes gathering u, w into the internal order and scattering f, K*w back"
+    out["tiled_vertex_reordered"]["note"] = ("includes permuting u, w into the internal vertex order and adding "
+                                             "f, K*w back")
     dm.close()
     dmr.close()
     return out

@@ -120,7 +120,15 @@ __device__ __forceinline__ bool mesh_reduce_last(double& a, double& b, double* p
 
 __device__ __forceinline__ bool pinned_at(const unsigned char* pin, int v) { return pin != nullptr && pin[v] != 0; }
 
-template <typename T>
+// Element-precision arrays of the step (f, K v, diag, K p accumulators and
+// the FP32 copies of u and p) are vertex-interleaved in FP32 (AOS: 4 values
+// per vertex), 3 planes otherwise; the FP64 CG vectors are always planes.
+template <bool AOS>
+__device__ __forceinline__ size_t eidx(int nv, int v, int comp) {
+  return AOS ? 4 * (size_t)v + comp : (size_t)comp * nv + v;
+}
+
+template <typename T, bool AOS>
 __global__ void __launch_bounds__(kBT)
 batch_init_kernel(BatchConst c, BatchTable tb, const unsigned char* __restrict__ pin, const double* __restrict__ mass,
                   const T* __restrict__ acc_f, const T* __restrict__ acc_kv, const T* __restrict__ acc_d, double* r,
@@ -134,17 +142,18 @@ batch_init_kernel(BatchConst c, BatchTable tb, const unsigned char* __restrict__
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
       const int i = comp * c.nv + v;
+      const size_t ie = eidx<AOS>(c.nv, v, comp);
       double b = 0.0, di = 1.0;
       if (!pinned) {
-        b = c.dt * ((double)acc_f[i] + mv * c.g[comp] - c.dt * (double)acc_kv[i]);
-        di = 1.0 / (mv + c.dt * c.dt * (double)acc_d[i]);
+        b = c.dt * ((double)acc_f[ie] + mv * c.g[comp] - c.dt * (double)acc_kv[ie]);
+        di = 1.0 / (mv + c.dt * c.dt * (double)acc_d[ie]);
       }
       const double z = b * di;
       r[i] = b;
       p[i] = z;
       y[i] = 0.0;
       dinv[i] = di;
-      if (pe) pe[i] = (T)z;
+      if (pe) pe[ie] = (T)z;
       rz += b * z;
       rr += b * b;
     }
@@ -165,7 +174,7 @@ batch_init_kernel(BatchConst c, BatchTable tb, const unsigned char* __restrict__
   }
 }
 
-template <typename T>
+template <typename T, bool AOS>
 __global__ void __launch_bounds__(kBT)
 batch_pq_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restrict__ pin,
                 const double* __restrict__ mass, const double* __restrict__ p, const T* __restrict__ acc_kp,
@@ -182,7 +191,7 @@ batch_pq_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restr
     for (int comp = 0; comp < 3; ++comp) {
       const int i = comp * c.nv + v;
       const double pi = p[i];
-      const double q = fma(mv, pi, dt2_times(acc_kp[i], dt2));
+      const double q = fma(mv, pi, dt2_times(acc_kp[eidx<AOS>(c.nv, v, comp)], dt2));
       qz[i] = q;
       pq = fma(pi, q, pq);
     }
@@ -235,7 +244,7 @@ batch_update_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __r
   }
 }
 
-template <typename T>
+template <typename T, bool AOS>
 __global__ void __launch_bounds__(kBT)
 batch_pupdate_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __restrict__ pin,
                      const double* __restrict__ qz, double* __restrict__ p, T* __restrict__ pe,
@@ -254,22 +263,27 @@ batch_pupdate_kernel(BatchConst c, BatchTable tb, int s, const unsigned char* __
     for (int comp = 0; comp < 3; ++comp) {
       const int i = comp * c.nv + v;
       const double pi = pinned ? 0.0 : fma(beta, p[i], qz[i]);
+      const size_t ie = eidx<AOS>(c.nv, v, comp);
       p[i] = pi;
-      if (pe) pe[i] = (T)pi;
-      acc_kp[i] = T(0);
+      if (pe) pe[ie] = (T)pi;
+      acc_kp[ie] = T(0);
     }
   }
 }
 
-template <typename T>
-__global__ void batch_prep_kernel(int n, const double* __restrict__ u, const double* __restrict__ v, T* ue, T* ve,
+template <typename T, bool AOS>
+__global__ void batch_prep_kernel(int nv, const double* __restrict__ u, const double* __restrict__ v, T* ue, T* ve,
                                   T* acc_f, T* acc_kv, T* acc_d, T* acc_kp, bool copy) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (copy) {
-      ue[i] = (T)u[i];
-      ve[i] = (T)v[i];
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nv; x += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < (AOS ? 4 : 3); ++k) {
+      const size_t i = eidx<AOS>(nv, x, k);
+      if (copy) {
+        ue[i] = k < 3 ? (T)u[(size_t)k * nv + x] : T(0);
+        ve[i] = k < 3 ? (T)v[(size_t)k * nv + x] : T(0);
+      }
+      acc_f[i] = acc_kv[i] = acc_d[i] = acc_kp[i] = T(0);
     }
-    acc_f[i] = acc_kv[i] = acc_d[i] = acc_kp[i] = T(0);
   }
 }
 
@@ -455,7 +469,13 @@ ebb_status_t batch_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, c
   e = cudaMemsetAsync(s->sc, 0, (size_t)nmesh * sizeof(MeshCg), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->n_active, 0, sizeof(int), st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "batched CG reset");
-  batch_prep_kernel<T><<<4 * 152, 256, 0, st>>>(n, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
+  // FP32 element operands are vertex-interleaved (see eidx).
+  bool aos = false;
+  if constexpr (sizeof(T) == 4) aos = mixed;
+  if (aos)
+    batch_prep_kernel<T, true><<<4 * 152, 256, 0, st>>>(nv, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
+  else
+    batch_prep_kernel<T, false><<<4 * 152, 256, 0, st>>>(nv, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
   const T mu0 = (T)prm->mu, lam0 = (T)prm->lambda;
   MapIO<T> io;
   io.u = mixed ? ue : (const T*)u;
@@ -463,16 +483,22 @@ ebb_status_t batch_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, c
   io.f = acc_f;
   io.Kw = acc_kv;
   io.d = acc_d;
+  io.aos = aos;
   e = launch_tet_map<T>(tets, prm->model, OP_FORCE | OP_KV | OP_DIAG, prm->reduce, mu0, lam0, io, nullptr, st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "force/Kv/diag map");
-  batch_init_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, pin, s->mass, acc_f, acc_kv, acc_d, s->r, s->p, s->y, s->dinv,
-                                           mixed ? pe : nullptr, s->part, s->sc, s->n_active);
+  if (aos)
+    batch_init_kernel<T, true><<<nb, kBT, 0, st>>>(c, s->tb, pin, s->mass, acc_f, acc_kv, acc_d, s->r, s->p, s->y,
+                                                   s->dinv, pe, s->part, s->sc, s->n_active);
+  else
+    batch_init_kernel<T, false><<<nb, kBT, 0, st>>>(c, s->tb, pin, s->mass, acc_f, acc_kv, acc_d, s->r, s->p, s->y,
+                                                    s->dinv, mixed ? pe : nullptr, s->part, s->sc, s->n_active);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(ctx, e, "batched CG init");
 
   MapIO<T> kio;
   kio.u = io.u;
   kio.w = mixed ? pe : (const T*)s->p;
   kio.Kw = acc_kp;
+  kio.aos = aos;
   // Capture kChunk iterations once; re-capture when anything baked in changes.
   std::vector<unsigned char> key(sizeof(BatchConst) + 5 * sizeof(double) + 3 * sizeof(void*));
   {
@@ -495,12 +521,19 @@ ebb_status_t batch_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, c
     for (int k = 0; k < kChunk && le == cudaSuccess; ++k) {
       const int par = k & 1;
       le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, s->n_active, st);
-      batch_pq_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->mass, s->p, acc_kp, s->qz, s->part, s->sc,
-                                             s->n_active);
+      if (aos)
+        batch_pq_kernel<T, true><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->mass, s->p, acc_kp, s->qz, s->part, s->sc,
+                                                     s->n_active);
+      else
+        batch_pq_kernel<T, false><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->mass, s->p, acc_kp, s->qz, s->part,
+                                                      s->sc, s->n_active);
       batch_update_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->p, s->dinv, s->r, s->y, s->qz, s->part,
                                                  s->sc, s->n_active);
-      batch_pupdate_kernel<T><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->qz, s->p, mixed ? pe : nullptr, acc_kp,
-                                                  s->sc);
+      if (aos)
+        batch_pupdate_kernel<T, true><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->qz, s->p, pe, acc_kp, s->sc);
+      else
+        batch_pupdate_kernel<T, false><<<nb, kBT, 0, st>>>(c, s->tb, par, pin, s->qz, s->p, mixed ? pe : nullptr,
+                                                           acc_kp, s->sc);
       if (le == cudaSuccess) le = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;

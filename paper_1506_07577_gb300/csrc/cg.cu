@@ -111,11 +111,10 @@ __device__ __forceinline__ bool reduce_last(double& a, double& b, double* part, 
   return true;
 }
 
-// u32 = u, w32 = v (mixed precision), accumulators zeroed.
 // Element-precision operands of the step's maps are library-internal, so in
-// FP32 with the tiled reduction they are stored vertex-interleaved (AOS: nv
-// groups of x, y, z, padding), which lets the tiled map fetch a vertex with
-// one 16-byte copy and add into it with one vector atomic.
+// FP32 they are stored vertex-interleaved (AOS: nv groups of x, y, z,
+// padding), which lets the maps fetch a vertex with one 16-byte copy and add
+// into it with one vector atomic.
 template <bool AOS>
 __device__ __forceinline__ size_t vidx(int nv, int v, int k) {
   return AOS ? 4 * (size_t)v + k : (size_t)k * nv + v;
@@ -686,9 +685,9 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   // Arrival counters of the last-block reductions start at zero.
   e = cudaMemsetAsync(s->sc, 0, sizeof(CgScalars), st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "CG state reset");
-  // FP32 operands with the tiled reduction are vertex-interleaved (see vidx).
+  // FP32 operands are vertex-interleaved (see vidx).
   bool aos = false;
-  if constexpr (sizeof(T) == 4) aos = mixed && prm->reduce == EBB_REDUCE_TILED;
+  if constexpr (sizeof(T) == 4) aos = mixed;   // every reduction variant takes interleaved operands
   if (aos)
     step_prep_kernel<T, true><<<vgrid, 256, 0, st>>>(nv, u, v, ue, pe, acc_f, acc_kv, acc_d, acc_kp, mixed);
   else
