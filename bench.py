@@ -469,6 +469,7 @@ def batched_steps(abi, torch, local_rank, args):
         dm.vertex_field("tw", torch.float32, value=meshgen.random_field(b.X.shape[0], seed=5))
         out["autotune"] = tune_report(abi, abi.ebb_relation_autotune(
             dm.ctx, dm.tets, "tu", "tw", abi.map_opts(abi.EBB_NEOHOOKEAN, mu, lam, precision=abi.EBB_PREC_F32)))
+        vfinal = {}
         for name, prec in (("mixed", abi.EBB_PREC_F32), ("fp64", abi.EBB_PREC_F64)):
             prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, mu, lam, precision=prec, rtol=1e-8)
             ts = []
@@ -483,7 +484,10 @@ def batched_steps(abi, torch, local_rank, args):
             out[f"{name}_ms"] = 1e3 * min(ts[1:])
             its = [r.iters for r in reps]
             out[f"{name}_cg_iters_min_max"] = [min(its), max(its)]
+            vfinal[name] = vv.double().cpu().numpy()
         out["speedup_vs_fp64_form"] = out["fp64_ms"] / out["mixed_ms"]
+        out["v_rel_diff_mixed_vs_fp64_form"] = float(np.max(np.abs(vfinal["mixed"] - vfinal["fp64"]))
+                                                     / np.max(np.abs(vfinal["fp64"])))
     # one regular call per mesh (mixed), meshes resident, same workload
     meshes = []
     for m in range(len(sides)):
