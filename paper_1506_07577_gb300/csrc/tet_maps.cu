@@ -247,12 +247,13 @@ constexpr int kTileThreads = kTileTets + 32;
 
 template <typename T, int OPS>
 struct TileSmem {
-  // Ring depths: FP32 blobs are small enough for four stages at three CTAs
-  // per SM; FP64 blobs take two stages at two CTAs per SM.
-  static constexpr int RB = sizeof(T) == 4 ? 4 : 2;   // blob stages
+  // Ring depths (measured): FP32 runs three blob stages and one output
+  // buffer so that four CTAs fit an SM; FP64 blobs take two stages and two
+  // output buffers at two CTAs per SM.
+  static constexpr int RB = sizeof(T) == 4 ? 3 : 2;   // blob stages
   static constexpr int RV = 2;                        // slot-vector stages
-  static constexpr int LAG = sizeof(T) == 4 ? 2 : 1;  // gathers trail blob copies by LAG tiles
-  static constexpr int OB = 2;                        // per-corner output buffers
+  static constexpr int LAG = 1;                       // gathers trail blob copies by LAG tiles
+  static constexpr int OB = sizeof(T) == 4 ? 1 : 2;   // per-corner output buffers
   static_assert(LAG < RB, "the producer must not wait for a blob it has not issued");
   static constexpr bool FO = (OPS & OP_FORCE) != 0;
   static constexpr bool KV = (OPS & OP_KV) != 0;
@@ -318,7 +319,7 @@ __device__ __forceinline__ void add_out(const T* p, T* acc) {
 // vertex's 16 bytes with one cp.async, the reduction adds each vertex's three
 // components with one vector atomic.
 template <typename T, int MODEL, int OPS, bool AOS>
-__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
 tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, BlobLayout L,
                 const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err,
                 int drop_tile, long long wait_cycles) {
