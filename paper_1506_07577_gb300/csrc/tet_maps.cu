@@ -20,6 +20,7 @@
 #include "async_copy.cuh"
 #include "ebb_internal.h"
 #include "tet_math.cuh"
+#include "tet_math_x2.cuh"
 
 namespace ebb {
 
@@ -38,6 +39,25 @@ __device__ __forceinline__ void raise_error(int* err, int code, int index) {
 template <typename T, int MODEL, int OPS>
 __device__ __forceinline__ bool element_eval(const T* B, T V, T mu, T lam, const T* Du, const T* Dw, T (&fo)[4][3],
                                              T (&ko)[4][3], T (&dgo)[4][3]) {
+  if constexpr (sizeof(T) == 4 && OPS == (OP_FORCE | OP_KV)) {
+    // FP32 force / K w pairs on the paired FP32 instructions (measured: the
+    // K w map alone runs no faster paired, its force lane being idle work).
+    float2 D[9], out[4][3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) D[i] = make_float2(Du[i], Dw[i]);
+    if (MODEL == EBB_STVK)
+      stvk_eval_x2(B, V, mu, lam, D, out);
+    else if (!nh_eval_x2(B, V, mu, lam, D, out))
+      return false;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        fo[a][c] = out[a][c].x;
+        ko[a][c] = out[a][c].y;
+      }
+    return true;
+  }
   T G[9];
   mm(Du, B, G);
   StvkState<T> sv;
@@ -511,6 +531,51 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
     if (tid == 0) mbar_arrive(&empty_v[sv]);
 
     // Phase 2: one reduction unit per thread: kUnitEntries independent loads.
+    if constexpr (sizeof(T) == 4 && NF == 2) {
+      // FP32 force and K w together: each entry's (f, K w) pair is one
+      // 8-byte load and one paired add; same order of additions as below.
+      const uint32_t d = reinterpret_cast<const uint32_t*>(st + kBlobUnits)[tid];
+      const unsigned rem = (d >> 22) & 0xfu;
+      float2 acc[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] = make_float2(0.f, 0.f);
+      if (d & 1u) {
+        const uint4 codes = reinterpret_cast<const uint4*>(st + kBlobEnt)[tid];
+        const unsigned cw[4] = {codes.x, codes.y, codes.z, codes.w};
+#pragma unroll
+        for (int q = 0; q < kUnitEntries; ++q) {
+          const unsigned code = (cw[q >> 1] >> (16 * (q & 1))) & 0xffffu;
+          if (code != kEntryNone) {
+            const float* p = reinterpret_cast<const float*>(sob) + (size_t)code * 2;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              acc[c] = __fadd2_rn(acc[c], *reinterpret_cast<const float2*>(p + c * (TT + 1) * 2));
+          }
+        }
+      }
+      const unsigned maxrem = __reduce_max_sync(0xffffffffu, rem);
+      for (unsigned stp = 1; stp <= maxrem; stp <<= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 x = make_float2(__shfl_down_sync(0xffffffffu, acc[c].x, stp),
+                                       __shfl_down_sync(0xffffffffu, acc[c].y, stp));
+          if (rem >= stp) acc[c] = __fadd2_rn(acc[c], x);
+        }
+      }
+      if ((d >> 26) & 1u) {
+        const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
+        if constexpr (AOS) {
+          red_add_v4(reinterpret_cast<float*>(out_field[0]) + 4 * (size_t)v, acc[0].x, acc[1].x, acc[2].x);
+          red_add_v4(reinterpret_cast<float*>(out_field[1]) + 4 * (size_t)v, acc[0].y, acc[1].y, acc[2].y);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            atomicAdd(reinterpret_cast<float*>(out_field[0]) + (size_t)c * nv + v, acc[c].x);
+            atomicAdd(reinterpret_cast<float*>(out_field[1]) + (size_t)c * nv + v, acc[c].y);
+          }
+        }
+      }
+    } else
     {
       const uint32_t d = reinterpret_cast<const uint32_t*>(st + kBlobUnits)[tid];
       const unsigned rem = (d >> 22) & 0xfu;
