@@ -325,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- reduction variants of the fused map (kernel time only) ----------
     variants = {}
     for name, red in (("atomic", abi.EBB_REDUCE_ATOMIC), ("colour", abi.EBB_REDUCE_COLOR),
-                      ("tiled", abi.EBB_REDUCE_TILED)):
+                      ("gather", abi.EBB_REDUCE_GATHER), ("tiled", abi.EBB_REDUCE_TILED)):
         o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=red)
         ts = []
         with torch.cuda.stream(stream):
@@ -378,7 +378,9 @@ def run_ours(args, rank, world, local_rank):
             "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
             "kernel": {"tiled": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved>",
                        "atomic": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic, interleaved>",
-                       "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured, interleaved>"}[tune["reduce"]],
+                       "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured, interleaved>",
+                       "gather": "tet_corner_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved> + "
+                                 "vertex_sum_kernel<float, 2, interleaved>"}[tune["reduce"]],
             "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
 
     dm.close()
@@ -439,7 +441,7 @@ def implicit_steps(dm, m, abi, torch, stream, args):
             "v_rel_diff_mixed_vs_fp64_form": du}
 
 
-REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled"}
+REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather"}
 
 
 def tune_report(abi, rep):
@@ -636,6 +638,7 @@ def permuted_sweep(abi, torch, local_rank, args, peak):
                                         ("tiled_planes", abi.EBB_REDUCE_TILED, dm, fp, kp, ("up", "wp", "fp", "kp")),
                                         ("tiled_vertex_reordered", abi.EBB_REDUCE_TILED, dmr, fr, kr, names),
                                         ("atomic", abi.EBB_REDUCE_ATOMIC, dm, f, k, names),
+                                        ("gather", abi.EBB_REDUCE_GATHER, dm, f, k, names),
                                         ("colour", abi.EBB_REDUCE_COLOR, dm, f, k, names)):
         o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
         ts = []

@@ -95,12 +95,21 @@ typedef enum { EBB_PREC_F64 = 0, EBB_PREC_F32 = 1 } ebb_precision_t;
  *           distinct vertices into shared memory once, pre-reduces the
  *           per-corner results there and issues one atomic add per distinct
  *           vertex and component.
- *   AUTO:   the library's tuned choice (currently TILED). */
+ *   GATHER: per-corner results written to a library-owned buffer (one
+ *           thread per tet), then each vertex sums the entries that the
+ *           inverted key-field lists for it (Section 6.1's GroupBy index,
+ *           vertex -> (tet, corner) rows in increasing order), in that
+ *           order, and adds the sum into its field: no atomics, bitwise
+ *           reproducible run to run, no colouring needed.  The buffer
+ *           (36 values per tet in the map's precision) is allocated on
+ *           first use and kept with the relation.
+ *   AUTO:   the autotuned choice (ebb_relation_autotune), else TILED. */
 typedef enum {
   EBB_REDUCE_ATOMIC = 0,
   EBB_REDUCE_COLOR = 1,
   EBB_REDUCE_AUTO = 2,
-  EBB_REDUCE_TILED = 3
+  EBB_REDUCE_TILED = 3,
+  EBB_REDUCE_GATHER = 4
 } ebb_reduce_t;
 
 /* ebb_relation_finalize flags */
@@ -246,8 +255,8 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * also at the best of those with the operands staged vertex-interleaved
  * (library-owned copies that let a vertex be fetched with one 16-byte copy
  * and reduced with one vector atomic, at the price of a copy in and an add
- * back per call), the atomic variant, and the coloured variant if the
- * relation was finalized with EBB_FINALIZE_COLOR.
+ * back per call), the atomic variant, the gather variant, and the coloured
+ * variant if the relation was finalized with EBB_FINALIZE_COLOR.
  * Each candidate: 2 untimed launches, then the median of 7 launches timed
  * with CUDA events on the context's stream.  Afterwards the relation's tiles
  * use the fastest tile size (the blobs are rebuilt if it changed) and
@@ -259,7 +268,7 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * device errors of the timed maps (EBB_ERR_INVERTED) are returned. */
 #define EBB_AUTOTUNE_MAX_CAND 8
 typedef struct {
-  int32_t reduce;       /* EBB_REDUCE_TILED, _ATOMIC or _COLOR */
+  int32_t reduce;       /* EBB_REDUCE_TILED, _ATOMIC, _GATHER or _COLOR */
   int32_t tile_tets;    /* tets per tile for EBB_REDUCE_TILED, 0 otherwise */
   int32_t interleaved;  /* 1: FP32 operands staged vertex-interleaved */
   double us;            /* median duration of one K w map call, microseconds */
@@ -278,7 +287,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                    ebb_autotune_report_t* report);
 
 /* Set by hand what ebb_relation_autotune would choose: EBB_REDUCE_AUTO
- * resolves to `reduce` (TILED, ATOMIC or COLOR) for `model` and `precision`;
+ * resolves to `reduce` (TILED, ATOMIC, GATHER or COLOR) for `model` and `precision`;
  * the tiles are re-cut to at most `tile_tets` tets (1..128) if that differs;
  * `interleaved` (0/1) sets the FP32 vertex-interleaved staging of the tiled
  * maps.  Synchronous.  Errors: EBB_ERR_ARG (out-of-range value),

@@ -109,6 +109,10 @@ void free_tet_data(ebb_rel_s* r) {
     cudaFree(p);
     p = nullptr;
   }
+  for (void*& p : r->gather_corner) {
+    cudaFree(p);
+    p = nullptr;
+  }
   cudaFree(r->s64.B);
   cudaFree(r->s64.V);
   cudaFree(r->s64.mu);
@@ -158,6 +162,11 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
   const char* pa = (const char*)a;
   const char* pb = (const char*)b;
   return pa < pb + nb && pb < pa + na;
+}
+
+// A concrete reduction variant (AUTO resolved).
+bool valid_reduce(int r) {
+  return r == EBB_REDUCE_ATOMIC || r == EBB_REDUCE_COLOR || r == EBB_REDUCE_TILED || r == EBB_REDUCE_GATHER;
 }
 
 // EBB_REDUCE_AUTO: the autotuned variant for this model and precision, else
@@ -311,7 +320,7 @@ ebb_status_t run_map(ebb_ctx_t ctx, ebb_rel_t tets, const MapCall& mc, int ops, 
   if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
     return set_error(ctx, EBB_ERR_ARG, "unknown precision");
   const ebb_reduce_t reduce = resolve_reduce(tets, opts->reduce, opts->model, opts->precision);
-  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+  if (!valid_reduce(reduce))
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
@@ -684,7 +693,7 @@ ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t mode
   if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
   if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
   if ((model != EBB_STVK && model != EBB_NEOHOOKEAN) || (precision != EBB_PREC_F64 && precision != EBB_PREC_F32) ||
-      (reduce != EBB_REDUCE_TILED && reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR) || tile_tets < 1 ||
+      !valid_reduce(reduce) || tile_tets < 1 ||
       tile_tets > kTileTets || (interleaved != 0 && interleaved != 1))
     return set_error(ctx, EBB_ERR_ARG, "tuning value out of range");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
@@ -790,8 +799,8 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
       else tets->stage_interleaved = false;
     }
   }
-  const ebb_reduce_t others[2] = {EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR};
-  for (int oi = 0; oi < 2 && !s; ++oi) {
+  const ebb_reduce_t others[3] = {EBB_REDUCE_ATOMIC, EBB_REDUCE_GATHER, EBB_REDUCE_COLOR};
+  for (int oi = 0; oi < 3 && !s; ++oi) {
     if (others[oi] == EBB_REDUCE_COLOR && !tets->has_colour) continue;
     double us = 0.0;
     s = time_map(others[oi], &us);
@@ -834,7 +843,7 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
   ebb_reduce_t reduce = resolve_reduce(tets, params->reduce, params->model, params->precision);
-  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+  if (!valid_reduce(reduce))
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
@@ -875,7 +884,7 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
   ebb_reduce_t reduce = resolve_reduce(tets, params->reduce, params->model, params->precision);
-  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+  if (!valid_reduce(reduce))
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
@@ -933,7 +942,7 @@ ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const c
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
   ebb_reduce_t reduce = resolve_reduce(tets, params->reduce, params->model, params->precision);
-  if (reduce != EBB_REDUCE_ATOMIC && reduce != EBB_REDUCE_COLOR && reduce != EBB_REDUCE_TILED)
+  if (!valid_reduce(reduce))
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");

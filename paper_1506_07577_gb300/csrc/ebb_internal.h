@@ -142,6 +142,7 @@ struct ebb_rel_s {
   int test_drop_tile = -1;              // EBB_MAP_TEST_DROP_TILE: tile whose blob copy the next map skips
   bool stage_interleaved = false;       // FP32 tiled maps stage operands vertex-interleaved (autotuned)
   ebb::VertexIndex vindex;
+  void* gather_corner[2] = {nullptr, nullptr};  // EBB_REDUCE_GATHER per-corner buffers, [0] FP32, [1] FP64
 
   // ---- implicit-step scratch ----
   ebb::StepScratch* step = nullptr;

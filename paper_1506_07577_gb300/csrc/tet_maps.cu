@@ -140,22 +140,11 @@ __device__ __forceinline__ void load_tet(const TetStreams<T>& s, int nt, int t, 
   lam = s.lam ? s.lam[t] : lam0;
 }
 
-// ---- direct: one thread per tet -------------------------------------------
-// AOS: vertex-interleaved operands (MapIO::aos, FP32): one 16-byte load per
-// corner and field, one vector atomic (or one 16-byte read-modify-write)
-// per corner and output.
-template <typename T, int MODEL, int OPS, bool ATOMIC, bool AOS>
-__global__ void __launch_bounds__(kMapThreads)
-tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ keys, const int* __restrict__ perm,
-               TetStreams<T> s, T mu0, T lam0, MapIO<T> io, const int* active, int* err) {
-  if (active != nullptr && *active == 0) return;
-  const int t = t_begin + blockIdx.x * kMapThreads + threadIdx.x;
-  if (t >= t_end) return;
-  const int4 k4 = keys[t];
-  const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
-  T B[9], V, mu, lam;
-  load_tet(s, nt, t, mu0, lam0, B, V, mu, lam);
-  T Du[9], Dw[9];
+// Edge differences of u (and w) over one tet's corners kk: Du[c][j] =
+// u_c(x_{j+1}) - u_c(x_0).  AOS: vertex-interleaved operands, one 16-byte
+// load per corner and field.
+template <typename T, int OPS, bool AOS>
+__device__ __forceinline__ void load_edges(const MapIO<T>& io, int nv, const int (&kk)[4], T (&Du)[9], T (&Dw)[9]) {
   if constexpr (AOS) {
     float4 q[4], r[4];
 #pragma unroll
@@ -189,6 +178,25 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
       }
     }
   }
+}
+
+// ---- direct: one thread per tet -------------------------------------------
+// AOS: vertex-interleaved operands (MapIO::aos, FP32): one 16-byte load per
+// corner and field, one vector atomic (or one 16-byte read-modify-write)
+// per corner and output.
+template <typename T, int MODEL, int OPS, bool ATOMIC, bool AOS>
+__global__ void __launch_bounds__(kMapThreads)
+tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ keys, const int* __restrict__ perm,
+               TetStreams<T> s, T mu0, T lam0, MapIO<T> io, const int* active, int* err) {
+  if (active != nullptr && *active == 0) return;
+  const int t = t_begin + blockIdx.x * kMapThreads + threadIdx.x;
+  if (t >= t_end) return;
+  const int4 k4 = keys[t];
+  const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
+  T B[9], V, mu, lam;
+  load_tet(s, nt, t, mu0, lam0, B, V, mu, lam);
+  T Du[9], Dw[9];
+  load_edges<T, OPS, AOS>(io, nv, kk, Du, Dw);
   T fo[4][3], ko[4][3], dgo[4][3];
   if (!element_eval<T, MODEL, OPS>(B, V, mu, lam, Du, Dw, fo, ko, dgo)) {
     raise_error(err, EBB_ERR_INVERTED, perm[t]);
@@ -231,6 +239,112 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
           if (OPS & OP_DIAG) io.d[o] += dgo[a][c];
         }
       }
+    }
+  }
+}
+
+// ---- gather: per-corner outputs, then a per-vertex sum (GroupBy) ----------
+// Pass 1, one thread per tet: the element's outputs go to a per-relation
+// buffer instead of the vertex fields; entry 4 t + a (corner a of internal
+// tet t) holds its NF output fields x 3 components, component-major with the
+// fields interleaved, so that a tet's 4 entries are 12 NF contiguous values.
+// Pass 2, one thread per vertex: the entries that the vertex index lists
+// for vertex v (Section 6.1's GroupBy: the key-field tets.v inverted into
+// vertex -> (tet, corner) rows, in increasing row order) are summed in that
+// order and added into the output fields with a plain read-modify-write.
+// No atomics, and every run forms the same sums in the same order: the
+// result is bitwise reproducible.  An inverted element contributes zeros.
+template <int OPS>
+constexpr int ops_nf() {
+  return ((OPS & OP_FORCE) ? 1 : 0) + ((OPS & OP_KV) ? 1 : 0) + ((OPS & OP_DIAG) ? 1 : 0);
+}
+
+template <typename T, int MODEL, int OPS, bool AOS>
+__global__ void __launch_bounds__(kMapThreads)
+tet_corner_kernel(int nt, int nv, const int4* __restrict__ keys, const int* __restrict__ perm, TetStreams<T> s,
+                  T mu0, T lam0, MapIO<T> io, T* __restrict__ corner, const int* active, int* err) {
+  constexpr int NF = ops_nf<OPS>();
+  if (active != nullptr && *active == 0) return;
+  const int t = blockIdx.x * kMapThreads + threadIdx.x;
+  if (t >= nt) return;
+  const int4 k4 = keys[t];
+  const int kk[4] = {k4.x, k4.y, k4.z, k4.w};
+  T B[9], V, mu, lam;
+  load_tet(s, nt, t, mu0, lam0, B, V, mu, lam);
+  T Du[9], Dw[9];
+  load_edges<T, OPS, AOS>(io, nv, kk, Du, Dw);
+  T fo[4][3], ko[4][3], dgo[4][3];
+  T vals[12 * NF];
+  if (element_eval<T, MODEL, OPS>(B, V, mu, lam, Du, Dw, fo, ko, dgo)) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        int f = 0;
+        if (OPS & OP_FORCE) vals[(a * 3 + c) * NF + f++] = fo[a][c];
+        if (OPS & OP_KV) vals[(a * 3 + c) * NF + f++] = ko[a][c];
+        if (OPS & OP_DIAG) vals[(a * 3 + c) * NF + f++] = dgo[a][c];
+      }
+  } else {
+    raise_error(err, EBB_ERR_INVERTED, perm[t]);
+#pragma unroll
+    for (int i = 0; i < 12 * NF; ++i) vals[i] = T(0);
+  }
+  // 12 NF values = 48 NF (FP32) or 96 NF (FP64) bytes: whole 16-byte stores.
+  constexpr int PER16 = 16 / (int)sizeof(T);
+  T* dst = corner + (size_t)t * 12 * NF;
+#pragma unroll
+  for (int i = 0; i < 12 * NF; i += PER16) {
+    if constexpr (sizeof(T) == 4)
+      *reinterpret_cast<float4*>(dst + i) = make_float4((float)vals[i], (float)vals[i + 1], (float)vals[i + 2],
+                                                        (float)vals[i + 3]);
+    else
+      *reinterpret_cast<double2*>(dst + i) = make_double2((double)vals[i], (double)vals[i + 1]);
+  }
+}
+
+constexpr int kSumThreads = 256;
+
+template <typename T, int NF, bool AOS>
+__global__ void __launch_bounds__(kSumThreads)
+vertex_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ ent, const T* __restrict__ corner,
+                  T* out0, T* out1, T* out2, const int* active) {
+  if (active != nullptr && *active == 0) return;
+  const int v = blockIdx.x * kSumThreads + threadIdx.x;
+  if (v >= nv) return;
+  T acc[3 * NF];
+#pragma unroll
+  for (int k = 0; k < 3 * NF; ++k) acc[k] = T(0);
+  const int e0 = off[v], e1 = off[v + 1];
+#pragma unroll 4
+  for (int e = e0; e < e1; ++e) {
+    const T* p = corner + (size_t)__ldg(ent + e) * 3 * NF;
+    if constexpr (NF == 2 && sizeof(T) == 4) {
+      // (f, K w) pairs: one 8-byte load per component
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(p) + c);
+        acc[2 * c] += (T)q.x;
+        acc[2 * c + 1] += (T)q.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3 * NF; ++k) acc[k] += __ldg(p + k);
+    }
+  }
+  T* outs[3] = {out0, out1, out2};
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if constexpr (AOS) {
+      float4* o = reinterpret_cast<float4*>(outs[f]) + v;
+      float4 x = *o;
+      x.x += (float)acc[f];
+      x.y += (float)acc[NF + f];
+      x.z += (float)acc[2 * NF + f];
+      *o = x;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) outs[f][(size_t)c * nv + v] += acc[c * NF + f];
     }
   }
 }
@@ -739,6 +853,49 @@ const TetStreams<float>& streams_of<float>(const ebb_rel_s* rel, bool coloured) 
   return coloured ? rel->colour.s32 : rel->s32;
 }
 
+// Per-corner buffer of the gather variant: 12 x 3 values per tet (room for
+// all three outputs), allocated at first use and kept with the relation.
+// Never allocated inside a stream capture: the implicit steps' first map
+// (force, K v and diag together) runs before their capture.
+template <typename T>
+cudaError_t gather_buffer(ebb_rel_s* rel, cudaStream_t stream, T** out) {
+  void*& buf = rel->gather_corner[sizeof(T) == 4 ? 0 : 1];
+  if (buf == nullptr) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+    e = cudaMalloc(&buf, (size_t)rel->size * 36 * sizeof(T));
+    if (e != cudaSuccess) {
+      buf = nullptr;
+      return e;
+    }
+  }
+  *out = static_cast<T*>(buf);
+  return cudaSuccess;
+}
+
+template <typename T, int MODEL, int OPS, bool AOS>
+cudaError_t launch_gather(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, const int* active, cudaStream_t stream) {
+  constexpr int NF = ops_nf<OPS>();
+  const int nt = (int)rel->size, nv = (int)rel->verts->size;
+  T* corner = nullptr;
+  cudaError_t e = gather_buffer<T>(rel, stream, &corner);
+  if (e != cudaSuccess) return e;
+  tet_corner_kernel<T, MODEL, OPS, AOS><<<(nt + kMapThreads - 1) / kMapThreads, kMapThreads, 0, stream>>>(
+      nt, nv, rel->keys, rel->tet_perm, streams_of<T>(rel, false), mu0, lam0, io, corner, active, rel->ctx->d_err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || nv == 0) return e;
+  T* outs[3] = {nullptr, nullptr, nullptr};
+  int f = 0;
+  if (OPS & OP_FORCE) outs[f++] = io.f;
+  if (OPS & OP_KV) outs[f++] = io.Kw;
+  if (OPS & OP_DIAG) outs[f++] = io.d;
+  vertex_sum_kernel<T, NF, AOS><<<(nv + kSumThreads - 1) / kSumThreads, kSumThreads, 0, stream>>>(
+      nv, rel->vindex.off, rel->vindex.ent, corner, outs[0], outs[1], outs[2], active);
+  return cudaGetLastError();
+}
+
 template <typename T, int MODEL, int OPS>
 cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, const MapIO<T>& io,
                             const int* active, cudaStream_t stream) {
@@ -754,6 +911,13 @@ cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, 
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+  }
+  if (reduce == EBB_REDUCE_GATHER) {
+    if (io.aos) {
+      if constexpr (sizeof(T) == 4) return launch_gather<T, MODEL, OPS, true>(rel, mu0, lam0, io, active, stream);
+      return cudaErrorInvalidValue;
+    }
+    return launch_gather<T, MODEL, OPS, false>(rel, mu0, lam0, io, active, stream);
   }
   if (reduce == EBB_REDUCE_TILED) {
     if (io.aos) {

@@ -30,8 +30,11 @@ def test_autotune_report_and_parity(prec):
         dm.vertex_field("w", dt, value=w)
         rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(abi.EBB_NEOHOOKEAN, precision=p))
         cands = [(rep.cand[i].reduce, rep.cand[i].tile_tets, rep.cand[i].us) for i in range(rep.ncand)]
-        # tiled at 3 tile sizes (FP32: staged interleaved, plus in place at the best size), atomic, colour
-        assert rep.ncand == (6 if prec == "f32" else 5)
+        # tiled at 3 tile sizes (FP32: staged interleaved, plus in place at the best size), atomic, gather,
+        # colour
+        assert rep.ncand == (7 if prec == "f32" else 6)
+        assert {c[0] for c in cands} == {abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_GATHER,
+                                         abi.EBB_REDUCE_COLOR}
         staged = [rep.cand[i].us for i in range(rep.ncand) if rep.cand[i].interleaved]
         assert len(staged) == (1 if prec == "f32" else 0)
         in_place = [rep.cand[i].us for i in range(rep.ncand)

@@ -18,7 +18,7 @@ def _abi():
     return abi
 
 
-def _batched(b, mu, lam, model, precision, max_iters, rtol, v0=None, steps=1):
+def _batched(b, mu, lam, model, precision, max_iters, rtol, v0=None, steps=1, reduce=None):
     abi = _abi()
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
     with DeviceTetMesh(b.X, b.tets, batch=b.batch) as dm:
@@ -26,7 +26,8 @@ def _batched(b, mu, lam, model, precision, max_iters, rtol, v0=None, steps=1):
         dm.vertex_field("v", torch.float64, value=np.zeros_like(b.X) if v0 is None else v0)
         dm.bind("pinned", torch.from_numpy(b.pinned.astype(np.uint8)).to(dm.device))
         prm = abi.step_params(abi.EBB_STVK if model == "stvk" else abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, mu, lam, G,
-                              precision, max_iters=max_iters, rtol=rtol)
+                              precision, max_iters=max_iters, rtol=rtol,
+                              reduce=abi.EBB_REDUCE_AUTO if reduce is None else reduce)
         reps = []
         for _ in range(steps):
             reps.append(abi.ebb_cg_implicit_step_batched(dm.ctx, dm.tets, "u", "v", "pinned", "batch",
@@ -71,11 +72,13 @@ def test_batched_fp64_equals_single_mesh_steps(model):
     assert len(iters) > 1          # meshes really converge at different iterations
 
 
-def test_batched_mixed_matches_oracle_per_mesh():
+@pytest.mark.parametrize("reduce", ["auto", "gather"])
+def test_batched_mixed_matches_oracle_per_mesh(reduce):
     abi = _abi()
     b = meshgen.cube_grid_batch([3, 6, 4], jitter=0.01, seed=21)
     mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
-    ub, vb, reps = _batched(b, mu, lam, "nh", abi.EBB_PREC_F32, 1000, 1e-8)
+    red = abi.EBB_REDUCE_AUTO if reduce == "auto" else abi.EBB_REDUCE_GATHER
+    ub, vb, reps = _batched(b, mu, lam, "nh", abi.EBB_PREC_F32, 1000, 1e-8, reduce=red)
     for m in range(len(b.sides)):
         X, tets, pinned = b.mesh(m)
         B, V = fem.rest_shape(X, tets)

@@ -46,13 +46,14 @@ def _run_maps(dm, u, w, model, prec, reduce, mu, lam):
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather"])
 @pytest.mark.parametrize("per_tet", [True, False])
 def test_maps_match_oracle(model, prec, reduce, per_tet):
     abi = _abi()
     m, mu, lam, u, w = problem(6 if per_tet else 7, model, seed=13, per_tet=per_tet)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
-    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED}[reduce]
+    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
+           "gather": abi.EBB_REDUCE_GATHER}[reduce]
     with _mesh(m, mu, lam) as dm:
         got = _run_maps(dm, u, w, model, prec, red, mu, lam)
     tol = TOL[prec]
@@ -77,14 +78,33 @@ def test_small_strain_fp32_relative_accuracy():
                 assert rel_err(got["Kw"], Kw) < 1e-5
 
 
-def test_colour_variant_is_bitwise_deterministic():
+@pytest.mark.parametrize("reduce", ["colour", "gather"])
+def test_atomic_free_variants_are_bitwise_deterministic(reduce):
     abi = _abi()
+    red = {"colour": abi.EBB_REDUCE_COLOR, "gather": abi.EBB_REDUCE_GATHER}[reduce]
     m, mu, lam, u, w = problem(7, "nh", seed=3)
     with _mesh(m, mu, lam) as dm:
-        a = _run_maps(dm, u, w, "nh", "f32", abi.EBB_REDUCE_COLOR, mu, lam)
-        b = _run_maps(dm, u, w, "nh", "f32", abi.EBB_REDUCE_COLOR, mu, lam)
-    for k in ("f", "Kw", "d"):
+        a = _run_maps(dm, u, w, "nh", "f32", red, mu, lam)
+        b = _run_maps(dm, u, w, "nh", "f32", red, mu, lam)
+    for k in ("f", "Kw", "d", "f2", "Kw2"):
         assert np.array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gather_needs_no_colouring(prec):
+    """The gather variant on a relation finalized without a colouring (its
+    order comes from the vertex index alone): it matches the oracle and
+    repeats bit for bit, in both precisions."""
+    abi = _abi()
+    m, mu, lam, u, w = problem(3, "stvk", seed=17)
+    f, Kw, d = oracle_maps(m, mu, lam, u, w, "stvk")
+    with _mesh(m, mu, lam, colour=False) as dm:
+        got = _run_maps(dm, u, w, "stvk", prec, abi.EBB_REDUCE_GATHER, mu, lam)
+        again = _run_maps(dm, u, w, "stvk", prec, abi.EBB_REDUCE_GATHER, mu, lam)
+    tol = TOL[prec]
+    assert rel_err(got["f"], f) < tol and rel_err(got["Kw"], Kw) < tol and rel_err(got["d"], d) < tol
+    for k in got:
+        assert np.array_equal(got[k], again[k])
 
 
 def test_permuted_ids_match_oracle():
@@ -92,14 +112,17 @@ def test_permuted_ids_match_oracle():
     m, mu, lam, u, w = problem(5, "stvk", seed=8, permute=True)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, "stvk")
     with _mesh(m, mu, lam) as dm:
-        for red in (abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_COLOR):
+        for red in (abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_COLOR, abi.EBB_REDUCE_GATHER):
             got = _run_maps(dm, u, w, "stvk", "f32", red, mu, lam)
             assert rel_err(got["f"], f) < 1e-5 and rel_err(got["Kw"], Kw) < 1e-5
 
 
-@pytest.mark.parametrize("n,model,prec,reorder", [(64, "nh", "f32", False), (128, "stvk", "f32", False),
-                                                  (128, "stvk", "f32", True), (32, "stvk", "f64", False)])
-def test_full_size_sampled_vertices(n, model, prec, reorder):
+@pytest.mark.parametrize("n,model,prec,reorder,reduce", [(64, "nh", "f32", False, "tiled"),
+                                                         (64, "nh", "f32", False, "gather"),
+                                                         (128, "stvk", "f32", False, "tiled"),
+                                                         (128, "stvk", "f32", True, "tiled"),
+                                                         (32, "stvk", "f64", False, "tiled")])
+def test_full_size_sampled_vertices(n, model, prec, reorder, reduce):
     """At the benchmark sizes the oracle checks sampled vertices: each is
     recomputed exactly from its incident tets only."""
     abi = _abi()
@@ -119,7 +142,8 @@ def test_full_size_sampled_vertices(n, model, prec, reorder):
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
     with DeviceTetMesh(m.X, m.tets, mu if np.ndim(mu) else None, lam if np.ndim(lam) else None,
                        reorder_verts=reorder) as dm:
-        got = _run_maps(dm, u, w, model, prec, abi.EBB_REDUCE_TILED, mu, lam)
+        red = abi.EBB_REDUCE_TILED if reduce == "tiled" else abi.EBB_REDUCE_GATHER
+        got = _run_maps(dm, u, w, model, prec, red, mu, lam)
     tol = TOL[prec]
     assert rel_err(got["f"][sample], f) < tol
     assert rel_err(got["Kw"][sample], Kw) < tol

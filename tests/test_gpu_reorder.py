@@ -18,14 +18,15 @@ def _abi():
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather"])
 def test_reordered_maps_match_oracle(prec, reduce):
     abi = _abi()
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
     m, mu, lam, u, w = problem(6, "nh", seed=17, permute=True)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, "nh")
     dt = torch.float64 if prec == "f64" else torch.float32
-    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED}[reduce]
+    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
+           "gather": abi.EBB_REDUCE_GATHER}[reduce]
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=True, reorder_verts=True) as dm:
         dm.vertex_field("u", dt, value=u)
         dm.vertex_field("w", dt, value=w)

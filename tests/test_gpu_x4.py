@@ -21,14 +21,15 @@ def _got(t):
 
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
-@pytest.mark.parametrize("reduce", ["tiled", "atomic", "colour"])
+@pytest.mark.parametrize("reduce", ["tiled", "atomic", "colour", "gather"])
 @pytest.mark.parametrize("reorder", [False, True])
 def test_x4_maps_match_oracle(model, reduce, reorder):
     abi = _abi()
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
     m, mu, lam, u, w = problem(6, model, seed=41, permute=reorder)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
-    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED}[reduce]
+    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
+           "gather": abi.EBB_REDUCE_GATHER}[reduce]
     mdl = abi.EBB_STVK if model == "stvk" else abi.EBB_NEOHOOKEAN
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=True, reorder_verts=reorder) as dm:
         dm.vertex_field("u", value=u, x4=True)
@@ -77,7 +78,7 @@ def test_x4_layout_rules_and_autotune():
         assert ei.value.status == abi.EBB_ERR_ARG
         rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(abi.EBB_NEOHOOKEAN,
                                                                                precision=abi.EBB_PREC_F32))
-        assert rep.interleaved == 1 and rep.ncand == 4   # tiled x3 (fields already interleaved), atomic
+        assert rep.interleaved == 1 and rep.ncand == 5   # tiled x3 (fields already interleaved), atomic, gather
         abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
         abi.ebb_ctx_sync(dm.ctx)
         assert rel_err(_got(tf), f) < 1e-5
