@@ -54,7 +54,8 @@ L2_FLUSH_BYTES = 256 << 20
 # only while the kernel's sources are the ones captured; otherwise reported
 # as null.
 NCU_TRAFFIC = {"sources_sha256_16": "270d59bc2abe3f81", "bytes_per_launch": 121.67e6}
-KERNEL_SOURCES = ["tet_maps.cu", "tet_math.cuh", "tet_math_x2.cuh", "async_copy.cuh", "ebb_internal.h", "layout.cu"]
+KERNEL_SOURCES = ["tet_maps.cu", "tet_io.cuh", "tet_math.cuh", "tet_math_x2.cuh", "async_copy.cuh", "ebb_internal.h",
+                  "layout.cu"]
 
 
 def kernel_sources_hash():
@@ -241,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
 
     m, mu, lam, u, w = workload()
     stream = torch.cuda.Stream(device=dev)
-    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream, colour=True)
+    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream, colour=True, edges=True)
     # Vector fields stored element by element (EBB_F32X4: x, y, z, padding), the
     # per-field contiguous vec3 storage of Section 6.1 padded to 16 bytes; the
     # same map on 3-plane fields is reported under "layouts".
@@ -362,6 +363,9 @@ def run_ours(args, rank, world, local_rank):
     for v in layouts.values():
         v["tets_per_s"] = nt / (v["us"] * 1e-6)
 
+    # ---- assembled K on the edge relation vs the matrix-free K w map ------
+    asm = assembled_compare(dm, abi, torch, stream, args, flush)
+
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
     bat = batched_steps(abi, torch, local_rank, args) if args.batch_meshes > 0 else None
@@ -398,6 +402,7 @@ def run_ours(args, rank, world, local_rank):
             "autotune": tune,
             "reduction_variants": variants,
             "layouts": layouts,
+            "assembled_K": asm,
             "e2e": {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -412,17 +417,54 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def assembled_compare(dm, abi, torch, stream, args, flush):
+    """K(u) assembled on the edge relation (FP32 blocks) and its block-sparse
+    product with w, against the matrix-free K w map (tiled), on the bench's
+    4-float fields; L2 flushed before every timed launch."""
+    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32)
+    o_kv = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
+    Kw = dm._tensors["Kw"]
+    calls = {"assemble": lambda: abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u32", o),
+             "spmv": lambda: abi.ebb_spmv_tet_K(dm.ctx, dm.tets, "w32", "Kw", o),
+             "kv_map_tiled": lambda: abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u32", "w32", "Kw", o_kv)}
+    res = {}
+    with torch.cuda.stream(stream):
+        for name, call in calls.items():
+            ts = []
+            for k in range(args.warmup + 5):
+                flush.fill_(float(k))
+                Kw.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                call()
+                b.record(stream)
+                b.synchronize()
+                if k >= args.warmup:
+                    ts.append(a.elapsed_time(b) * 1e3)
+            res[name + "_us"] = statistics.median(ts)
+    return res
+
+
 def implicit_steps(dm, m, abi, torch, stream, args):
-    """10 implicit steps from rest under gravity, mixed form and FP64 form."""
+    """10 implicit steps from rest under gravity: the mixed form, the same with
+    K assembled once per step (block-sparse CG products), and the FP64 form.
+    One untimed step first (graph capture), then the state is reset."""
     uu = dm.vertex_field("u_state", torch.float64)
     vv = dm.vertex_field("v_state", torch.float64)
     dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(uu.device))
     out = {}
     res = {}
-    for name, prec in (("mixed", abi.EBB_PREC_F32), ("fp64", abi.EBB_PREC_F64)):
+    for name, prec, flags in (("mixed", abi.EBB_PREC_F32, 0), ("mixed_assembled", abi.EBB_PREC_F32,
+                                                              abi.EBB_STEP_ASSEMBLED),
+                              ("fp64", abi.EBB_PREC_F64, 0)):
+        prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, precision=prec, max_iters=1000, rtol=1e-8,
+                              flags=flags)
         uu.zero_()
         vv.zero_()
-        prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, precision=prec, max_iters=1000, rtol=1e-8)
+        with torch.cuda.stream(stream):
+            abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u_state", "v_state", "pinned", prm)
+        uu.zero_()
+        vv.zero_()
         times, iters = [], []
         with torch.cuda.stream(stream):
             for s in range(args.implicit_steps):
@@ -433,12 +475,17 @@ def implicit_steps(dm, m, abi, torch, stream, args):
                 iters.append(rep.iters)
         res[name] = (uu.clone(), vv.clone())
         out[name] = {"ms_per_step": 1e3 * sum(times) / len(times), "cg_iters": iters}
-    du = (res["mixed"][1] - res["fp64"][1]).abs().max().item() / res["fp64"][1].abs().max().item()
+    vmax = res["fp64"][1].abs().max().item()
+    du = (res["mixed"][1] - res["fp64"][1]).abs().max().item() / vmax
+    da = (res["mixed_assembled"][1] - res["fp64"][1]).abs().max().item() / vmax
     return {"steps": args.implicit_steps, "dt": 1e-3, "rtol": 1e-8,
             "mixed_ms_per_step": out["mixed"]["ms_per_step"], "fp64_ms_per_step": out["fp64"]["ms_per_step"],
             "speedup_vs_fp64_form": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
             "cg_iters_mixed": out["mixed"]["cg_iters"], "cg_iters_fp64": out["fp64"]["cg_iters"],
-            "v_rel_diff_mixed_vs_fp64_form": du}
+            "v_rel_diff_mixed_vs_fp64_form": du,
+            "mixed_assembled_ms_per_step": out["mixed_assembled"]["ms_per_step"],
+            "cg_iters_mixed_assembled": out["mixed_assembled"]["cg_iters"],
+            "v_rel_diff_mixed_assembled_vs_fp64_form": da}
 
 
 REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather"}

@@ -122,6 +122,11 @@ typedef enum {
                                           implicit step does so once per call.  Not
                                           combinable with verts.batch; the batched step
                                           and the step VJP refuse such relations. */
+#define EBB_FINALIZE_EDGES    4u  /* build the edge relation with self-loops and the
+                                     per-tet key-field tets.e[4][4] into it (Section
+                                     5.2's tetmesh domain), needed by
+                                     ebb_assemble_tet_K / ebb_spmv_tet_K and
+                                     EBB_STEP_ASSEMBLED */
 
 /* map flags */
 #define EBB_MAP_ZERO_OUT      1u  /* zero the output fields before reducing into them */
@@ -154,7 +159,16 @@ typedef struct {
   double rtol;                  /* stop when ||r||_2 <= rtol ||b||_2 */
   int32_t fail_on_max_iters;    /* nonzero: hitting max_iters above rtol
                                    returns EBB_ERR_NOT_CONVERGED */
+  uint32_t flags;               /* EBB_STEP_* */
 } ebb_step_params_t;
+
+/* ebb_step_params_t flags */
+#define EBB_STEP_ASSEMBLED    1u  /* ebb_cg_implicit_step assembles K(x_n) once on the
+                                     edge relation (EBB_FINALIZE_EDGES) and runs
+                                     every CG product K p as a block-sparse product
+                                     instead of the matrix-free K w map (Section
+                                     7.2's Vega data layout); the other step entry
+                                     points refuse it with EBB_ERR_ARG */
 
 typedef struct {
   int32_t iters;                /* PCG iterations performed */
@@ -238,6 +252,23 @@ ebb_status_t ebb_map_tet_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
 ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                   const char* w, const char* f_out,
                                   const char* Kw_out, const ebb_map_opts_t* opts);
+
+/* Assembled stiffness on the edge relation (needs EBB_FINALIZE_EDGES).
+ * ebb_assemble_tet_K forms K(u) in opts->precision (replacing any K
+ * assembled before in that precision): one 3x3 block per edge and self-loop,
+ * the sum over the tets that contain both vertices of the element blocks
+ * K_ab[c][d] = V (dP(e_d b_b^T) b_a)_c -- the dP of ebb_map_tet_Kv applied to
+ * one displacement component at one corner -- added with atomics (the block
+ * sums are not bitwise reproducible).  The blocks are library-owned (9 values
+ * per block in the assembly precision).  ebb_spmv_tet_K adds K w into Kw_out
+ * with the K last assembled in opts->precision (8 lanes per vertex row,
+ * fixed summation order); opts->model and ->reduce are not used by the
+ * product, opts->flags may hold EBB_MAP_ZERO_OUT.  Fields as for the maps.
+ * Errors: as for the maps; EBB_ERR_STATE without EBB_FINALIZE_EDGES, or for
+ * a product before any assembly in that precision. */
+ebb_status_t ebb_assemble_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const ebb_map_opts_t* opts);
+ebb_status_t ebb_spmv_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* w, const char* Kw_out,
+                            const ebb_map_opts_t* opts);
 
 /* d += diag(K(u)) (closed form per tet corner and component): the Jacobi
  * preconditioner of Section 7.2. */

@@ -41,6 +41,8 @@ EBB_PREC_F64, EBB_PREC_F32 = 0, 1
 EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED, EBB_REDUCE_GATHER = 0, 1, 2, 3, 4
 EBB_FINALIZE_COLOR = 1
 EBB_FINALIZE_REORDER_VERTS = 2
+EBB_FINALIZE_EDGES = 4
+EBB_STEP_ASSEMBLED = 1
 EBB_MAP_ZERO_OUT = 1
 EBB_MAP_TEST_DROP_TILE = 0x80000000
 EBB_NOALLOC_MAX_VERTS = 4096
@@ -60,7 +62,7 @@ class ebb_step_params_t(C.Structure):
     _fields_ = [("model", C.c_int), ("mu", C.c_double), ("lambda_", C.c_double),
                 ("precision", C.c_int), ("reduce", C.c_int), ("dt", C.c_double),
                 ("gravity", C.c_double * 3), ("rho", C.c_double), ("max_iters", C.c_int32),
-                ("rtol", C.c_double), ("fail_on_max_iters", C.c_int32)]
+                ("rtol", C.c_double), ("fail_on_max_iters", C.c_int32), ("flags", C.c_uint32)]
 
 
 EBB_AUTOTUNE_MAX_CAND = 8
@@ -93,6 +95,8 @@ _SIGS = {
     "ebb_map_tet_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_force_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_assemble_tet_K": ([ebb_ctx_t, ebb_rel_t, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_spmv_tet_K": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_relation_autotune": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t),
                                C.POINTER(ebb_autotune_report_t)], ebb_status_t),
     "ebb_relation_set_tuning": ([ebb_ctx_t, ebb_rel_t, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
@@ -217,6 +221,14 @@ def ebb_map_tet_diagK(ctx, tets, u, d_out, opts):
     return _check(ctx, _lib.ebb_map_tet_diagK(ctx, tets, _b(u), _b(d_out), C.byref(opts)))
 
 
+def ebb_assemble_tet_K(ctx, tets, u, opts):
+    return _check(ctx, _lib.ebb_assemble_tet_K(ctx, tets, _b(u), C.byref(opts)))
+
+
+def ebb_spmv_tet_K(ctx, tets, w, Kw_out, opts):
+    return _check(ctx, _lib.ebb_spmv_tet_K(ctx, tets, _b(w), _b(Kw_out), C.byref(opts)))
+
+
 def ebb_relation_autotune(ctx, tets, u, w, opts):
     """Pick the tile size and reduction variant of `tets` by timing the K w
     map; returns the report (chosen variant, tile size, timed candidates)."""
@@ -231,10 +243,10 @@ def ebb_relation_set_tuning(ctx, tets, model, precision, reduce, tile_tets, inte
 
 
 def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,
-                reduce=EBB_REDUCE_AUTO, max_iters=1000, rtol=1e-8, fail_on_max_iters=False):
+                reduce=EBB_REDUCE_AUTO, max_iters=1000, rtol=1e-8, fail_on_max_iters=False, flags=0):
     g = (C.c_double * 3)(*[float(x) for x in gravity])
     return ebb_step_params_t(int(model), float(mu), float(lam), int(precision), int(reduce), float(dt), g,
-                             float(rho), int(max_iters), float(rtol), int(bool(fail_on_max_iters)))
+                             float(rho), int(max_iters), float(rtol), int(bool(fail_on_max_iters)), int(flags))
 
 
 def ebb_cg_implicit_step(ctx, tets, u, v, pinned, params):

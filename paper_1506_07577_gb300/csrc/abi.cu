@@ -124,6 +124,7 @@ void free_tet_data(ebb_rel_s* r) {
   r->s64 = TetStreams<double>();
   r->s32 = TetStreams<float>();
   free_colouring(r);
+  free_edges(r);
   free_layout(r);
   free_step_scratch(r);
   free_batch_scratch(r);
@@ -276,7 +277,7 @@ ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int mod
     io.u = (const double*)in[0];
     io.w = (const double*)in[1];
     if (ops & OP_FORCE) io.f = (double*)out[oi++];
-    if (ops & OP_KV) io.Kw = (double*)out[oi++];
+    if (ops & (OP_KV | OP_SPMV)) io.Kw = (double*)out[oi++];
     if (ops & OP_DIAG) io.d = (double*)out[oi++];
     tets->test_drop_tile = drop ? 0 : -1;
     e = launch_tet_map<double>(tets, model, ops, reduce, mu, lambda, io, nullptr, ctx->stream);
@@ -286,7 +287,7 @@ ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int mod
     io.u = (const float*)in[0];
     io.w = (const float*)in[1];
     if (ops & OP_FORCE) io.f = (float*)out[oi++];
-    if (ops & OP_KV) io.Kw = (float*)out[oi++];
+    if (ops & (OP_KV | OP_SPMV)) io.Kw = (float*)out[oi++];
     if (ops & OP_DIAG) io.d = (float*)out[oi++];
     io.aos = stage || x4;
     tets->test_drop_tile = drop ? 0 : -1;
@@ -486,6 +487,7 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     std::vector<unsigned char> prefix;
     ebb_status_t ls =
         build_layout(ctx, tets, none, std::vector<double>((size_t)3 * nv, 0.0), nullptr, perm, sorted, prefix);
+    if (!ls && (flags & EBB_FINALIZE_EDGES)) ls = build_edges(ctx, tets, none);
     if (ls) return ls;
     tets->finalized = true;
     return EBB_OK;
@@ -638,6 +640,13 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
       return s;
     }
   }
+  if (flags & EBB_FINALIZE_EDGES) {
+    s = build_edges(ctx, tets, packed);
+    if (s) {
+      free_tet_data(tets);
+      return s;
+    }
+  }
   tets->finalized = true;
   return EBB_OK;
 }
@@ -683,6 +692,32 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, con
   mc.out[0] = d_out;
   mc.nout = 1;
   return run_map(ctx, tets, mc, OP_DIAG, opts);
+}
+
+ebb_status_t ebb_assemble_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const ebb_map_opts_t* opts) {
+  if (ctx && tets && tets->ctx == ctx && tets->finalized && tets->edges.row_off == nullptr)
+    return set_error(ctx, EBB_ERR_STATE, "relation finalized without EBB_FINALIZE_EDGES");
+  MapCall mc;
+  mc.in[0] = u;
+  mc.nin = 1;
+  mc.nout = 0;
+  return run_map(ctx, tets, mc, OP_ASSEMBLE, opts);
+}
+
+ebb_status_t ebb_spmv_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* w, const char* Kw_out,
+                            const ebb_map_opts_t* opts) {
+  if (ctx && tets && opts && tets->ctx == ctx && tets->finalized) {
+    if (tets->edges.row_off == nullptr)
+      return set_error(ctx, EBB_ERR_STATE, "relation finalized without EBB_FINALIZE_EDGES");
+    if (!tets->edges.assembled[opts->precision == EBB_PREC_F64 ? 1 : 0])
+      return set_error(ctx, EBB_ERR_STATE, "no stiffness assembled in this precision (call ebb_assemble_tet_K)");
+  }
+  MapCall mc;
+  mc.in[0] = w;
+  mc.nin = 1;
+  mc.out[0] = Kw_out;
+  mc.nout = 1;
+  return run_map(ctx, tets, mc, OP_SPMV, opts);
 }
 
 ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t model, int32_t precision,
@@ -847,6 +882,9 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
+  if (params->flags & ~EBB_STEP_ASSEMBLED) return set_error(ctx, EBB_ERR_ARG, "unknown EBB_STEP_* flag");
+  if ((params->flags & EBB_STEP_ASSEMBLED) && tets->edges.row_off == nullptr)
+    return set_error(ctx, EBB_ERR_STATE, "EBB_STEP_ASSEMBLED needs a relation finalized with EBB_FINALIZE_EDGES");
   void *pu = nullptr, *pv = nullptr;
   ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
   if (s) return s;
@@ -880,6 +918,7 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
   if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
   if (params->model != EBB_STVK || params->precision != EBB_PREC_F64)
     return set_error(ctx, EBB_ERR_ARG, "the step VJP supports StVK in FP64 only");
+  if (params->flags != 0) return set_error(ctx, EBB_ERR_ARG, "the step VJP takes no EBB_STEP_* flags");
   if (tets->vperm) return set_error(ctx, EBB_ERR_STATE, "the step VJP does not support EBB_FINALIZE_REORDER_VERTS");
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return set_error(ctx, EBB_ERR_ARG, "need dt > 0, rho > 0, max_iters >= 0, rtol >= 0");
@@ -948,6 +987,7 @@ ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const c
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
   if (tets->verts->size == 0) return set_error(ctx, EBB_ERR_ARG, "empty vertex relation");
   if (tets->vperm) return set_error(ctx, EBB_ERR_STATE, "the batched step does not support EBB_FINALIZE_REORDER_VERTS");
+  if (params->flags != 0) return set_error(ctx, EBB_ERR_ARG, "the batched step takes no EBB_STEP_* flags");
   void *pu = nullptr, *pv = nullptr, *pb = nullptr;
   ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
   if (s) return s;

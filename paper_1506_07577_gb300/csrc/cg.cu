@@ -545,7 +545,7 @@ __global__ void step_finish_kernel(int n, double dt, const double* __restrict__ 
 // Everything a captured CG chunk bakes into its kernel arguments; a change
 // of any field re-captures the graph.
 struct ChunkKey {
-  int elem_bytes, pin_bytes, model, reduce;
+  int elem_bytes, pin_bytes, model, reduce, assembled;
   unsigned layout_gen;  // tile blobs baked into the captured map launches
   double mu0, lam0;
   StepConst c;
@@ -705,6 +705,13 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   io.aos = aos;
   e = launch_tet_map<T>(tets, prm->model, OP_FORCE | OP_KV | OP_DIAG, prm->reduce, mu0, lam0, io, nullptr, st);
   if (e != cudaSuccess) return cuda_check(ctx, e, "force/Kv/diag map");
+  // EBB_STEP_ASSEMBLED: K(x_n) on the edge relation, once per step; the CG
+  // products below read it instead of re-evaluating the elements.
+  const bool assembled = (prm->flags & EBB_STEP_ASSEMBLED) != 0;
+  if (assembled) {
+    e = launch_assemble<T>(tets, prm->model, mu0, lam0, io, st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "stiffness assembly");
+  }
 
   double* part_a = s->part;
   double* part_b = s->part + 2 * kVecBlocks;
@@ -732,6 +739,7 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
   key.pin_bytes = (int)sizeof(PT);
   key.model = prm->model;
   key.reduce = prm->reduce;
+  key.assembled = assembled ? 1 : 0;
   key.layout_gen = tets->layout_gen;
   key.mu0 = prm->mu;
   key.lam0 = prm->lambda;
@@ -747,7 +755,8 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < kChunk && le == cudaSuccess; ++k) {
       const int par = k & 1;
-      le = launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
+      le = assembled ? launch_spmv<T>(tets, kio.w, acc_kp, aos, &s->sc->active[par], st)
+                     : launch_tet_map<T>(tets, prm->model, OP_KV, prm->reduce, mu0, lam0, kio, &s->sc->active[par], st);
       if (le == cudaSuccess)
         le = aos ? launch_cg_iter<T, PT, true>(iter_grid<T, PT, true>(), st, c, par, pin, s->mass, s->p, acc_kp,
                                                s->dinv, s->r, s->y, s->qz, pe, part_a, part_b, s->sc)

@@ -102,6 +102,21 @@ struct VertexIndex {
   int* ent = nullptr;
 };
 
+// Edge relation with self-loops (Section 5.2) as block CSR over internal
+// vertices: row r's blocks are (r, col[k]), k in [row_off[r], row_off[r+1]),
+// columns increasing; tet_blk[16 t + 4 a + b] is the block of corners (a, b)
+// of internal tet t (the key-field tets.e[4][4]).  blocks[p]: the assembled
+// stiffness as 9 planes of nnzb, entry (c, d) of block k at [(3 c + d) nnzb
+// + k] ([0] FP32, [1] FP64).
+struct EdgeIndex {
+  int nnzb = 0;
+  int* row_off = nullptr;
+  int* col = nullptr;
+  int* tet_blk = nullptr;
+  void* blocks[2] = {nullptr, nullptr};
+  bool assembled[2] = {false, false};
+};
+
 struct StepScratch;   // defined in cg.cu
 struct BatchScratch;  // defined in batched.cu
 
@@ -143,6 +158,7 @@ struct ebb_rel_s {
   bool stage_interleaved = false;       // FP32 tiled maps stage operands vertex-interleaved (autotuned)
   ebb::VertexIndex vindex;
   void* gather_corner[2] = {nullptr, nullptr};  // EBB_REDUCE_GATHER per-corner buffers, [0] FP32, [1] FP64
+  ebb::EdgeIndex edges;                 // built with EBB_FINALIZE_EDGES
 
   // ---- implicit-step scratch ----
   ebb::StepScratch* step = nullptr;
@@ -156,7 +172,7 @@ ebb_status_t set_error(ebb_ctx_s* ctx, ebb_status_t code, const std::string& msg
 ebb_status_t cuda_check(ebb_ctx_s* ctx, cudaError_t e, const char* what);
 
 // Element map launch (tet_maps.cu).
-enum MapOps { OP_FORCE = 1, OP_KV = 2, OP_DIAG = 4 };
+enum MapOps { OP_FORCE = 1, OP_KV = 2, OP_DIAG = 4, OP_ASSEMBLE = 8, OP_SPMV = 16 };
 
 template <typename T>
 struct MapIO {
@@ -245,6 +261,16 @@ template <typename PT>
 cudaError_t gather_pinned(int nv, const int* vperm, const PT* src, unsigned char* dst, cudaStream_t st);
 // Morton order of vertex positions (X as 3 planes of nv): perm[i] = vertex at internal row i.
 void vertex_morton_order(const std::vector<double>& X, std::vector<int>& perm);
+
+// Edge relation, assembled stiffness and its product (edges.cu).  `keys`:
+// the internal keys.  launch_assemble zeroes and assembles K(u) (u = io.u)
+// in T; launch_spmv adds K w into y (3 planes, or interleaved when aos).
+ebb_status_t build_edges(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys);
+void free_edges(ebb_rel_s* tets);
+template <typename T>
+cudaError_t launch_assemble(ebb_rel_s* rel, int model, T mu0, T lam0, const MapIO<T>& io, cudaStream_t st);
+template <typename T>
+cudaError_t launch_spmv(ebb_rel_s* rel, const T* w, T* y, bool aos, const int* active, cudaStream_t st);
 
 // Build the colouring (colour.cu).
 ebb_status_t build_colouring(ebb_ctx_s* ctx, ebb_rel_s* tets);

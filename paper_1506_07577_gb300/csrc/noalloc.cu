@@ -516,7 +516,8 @@ extern "C" ebb_status_t ebb_cg_implicit_step_noalloc(void* cuda_stream, int32_t 
   }
   if (!params || n_verts < 0 || n_tets < 0 || n_verts > EBB_NOALLOC_MAX_VERTS || n_tets > EBB_NOALLOC_MAX_TETS)
     return EBB_ERR_ARG;
-  if (params->precision != EBB_PREC_F64 || (params->model != EBB_STVK && params->model != EBB_NEOHOOKEAN))
+  if (params->precision != EBB_PREC_F64 || (params->model != EBB_STVK && params->model != EBB_NEOHOOKEAN) ||
+      params->flags != 0)
     return EBB_ERR_ARG;
   if (!(params->dt > 0.0) || !(params->rho > 0.0) || params->max_iters < 0 || !(params->rtol >= 0.0))
     return EBB_ERR_ARG;

@@ -19,6 +19,7 @@
 
 #include "async_copy.cuh"
 #include "ebb_internal.h"
+#include "tet_io.cuh"
 #include "tet_math.cuh"
 #include "tet_math_x2.cuh"
 
@@ -27,10 +28,6 @@ namespace ebb {
 namespace {
 
 constexpr int kMapThreads = 128;
-
-__device__ __forceinline__ void raise_error(int* err, int code, int index) {
-  if (atomicCAS(err + ERRW_CODE, 0, code) == 0) err[ERRW_INDEX] = index;
-}
 
 // Evaluate one tet.  Du, Dw: edge differences [x1-x0, x2-x0, x3-x0] of the
 // displacement and of the direction (3x3 row-major, row = component).  Outputs
@@ -130,55 +127,6 @@ __device__ __forceinline__ bool element_eval(const T* B, T V, T mu, T lam, const
   return true;
 }
 
-template <typename T>
-__device__ __forceinline__ void load_tet(const TetStreams<T>& s, int nt, int t, T mu0, T lam0, T* B, T& V, T& mu,
-                                         T& lam) {
-#pragma unroll
-  for (int i = 0; i < 9; ++i) B[i] = s.B[(size_t)i * nt + t];
-  V = s.V[t];
-  mu = s.mu ? s.mu[t] : mu0;
-  lam = s.lam ? s.lam[t] : lam0;
-}
-
-// Edge differences of u (and w) over one tet's corners kk: Du[c][j] =
-// u_c(x_{j+1}) - u_c(x_0).  AOS: vertex-interleaved operands, one 16-byte
-// load per corner and field.
-template <typename T, int OPS, bool AOS>
-__device__ __forceinline__ void load_edges(const MapIO<T>& io, int nv, const int (&kk)[4], T (&Du)[9], T (&Dw)[9]) {
-  if constexpr (AOS) {
-    float4 q[4], r[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      q[a] = reinterpret_cast<const float4*>(io.u)[kk[a]];
-      if (OPS & OP_KV) r[a] = reinterpret_cast<const float4*>(io.w)[kk[a]];
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      Du[0 * 3 + j] = q[j + 1].x - q[0].x;
-      Du[1 * 3 + j] = q[j + 1].y - q[0].y;
-      Du[2 * 3 + j] = q[j + 1].z - q[0].z;
-      if (OPS & OP_KV) {
-        Dw[0 * 3 + j] = r[j + 1].x - r[0].x;
-        Dw[1 * 3 + j] = r[j + 1].y - r[0].y;
-        Dw[2 * 3 + j] = r[j + 1].z - r[0].z;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const T* uc = io.u + (size_t)c * nv;
-      const T u0 = uc[kk[0]];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) Du[c * 3 + j] = uc[kk[j + 1]] - u0;
-      if (OPS & OP_KV) {
-        const T* wc = io.w + (size_t)c * nv;
-        const T w0 = wc[kk[0]];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Dw[c * 3 + j] = wc[kk[j + 1]] - w0;
-      }
-    }
-  }
-}
 
 // ---- direct: one thread per tet -------------------------------------------
 // AOS: vertex-interleaved operands (MapIO::aos, FP32): one 16-byte load per
@@ -961,6 +909,9 @@ cudaError_t prepare_map_kernels() {
 template <typename T>
 cudaError_t launch_tet_map(ebb_rel_s* rel, int model, int ops, ebb_reduce_t reduce, T mu0, T lam0,
                            const MapIO<T>& io, const int* active, cudaStream_t stream) {
+  // The assembled-stiffness operations share the maps' field handling.
+  if (ops == OP_ASSEMBLE) return launch_assemble<T>(rel, model, mu0, lam0, io, stream);
+  if (ops == OP_SPMV) return launch_spmv<T>(rel, io.u, io.Kw, io.aos, active, stream);
   if (rel->size == 0) return cudaSuccess;
   if (model == EBB_STVK) return dispatch_ops<T, EBB_STVK>(rel, ops, reduce, mu0, lam0, io, active, stream);
   return dispatch_ops<T, EBB_NEOHOOKEAN>(rel, ops, reduce, mu0, lam0, io, active, stream);

@@ -19,7 +19,7 @@ class DeviceTetMesh:
     bound, finalized on construction."""
 
     def __init__(self, X, tets, mu=None, lam=None, device=0, stream=None, colour=False, batch=None,
-                 reorder_verts=False):
+                 reorder_verts=False, edges=False):
         self.device = torch.device("cuda", device)
         self.ctx = abi.ebb_ctx_create(device, stream)
         self.n_verts = int(X.shape[0])
@@ -40,7 +40,8 @@ class DeviceTetMesh:
             self.batch = self._put("batch", np.asarray(batch, np.int32), self.verts)
         # uploads ran on torch's current stream; the library may use another
         torch.cuda.synchronize(self.device)
-        flags = (abi.EBB_FINALIZE_COLOR if colour else 0) | (abi.EBB_FINALIZE_REORDER_VERTS if reorder_verts else 0)
+        flags = ((abi.EBB_FINALIZE_COLOR if colour else 0) | (abi.EBB_FINALIZE_REORDER_VERTS if reorder_verts else 0) |
+                 (abi.EBB_FINALIZE_EDGES if edges else 0))
         abi.ebb_relation_finalize(self.ctx, self.tets, flags)
 
     def _put(self, name, arr, rel):
