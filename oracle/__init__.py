@@ -24,6 +24,8 @@ Pins.  The paper prints no worked example, so each function is pinned in
 and under rigid motions, balance of net force and torque, force = -dE/dx by
 central differences of the energy, analytic uniform-stretch patch tests, K
 symmetry and finite-difference consistency, a dense direct solve for PCG, and
-free fall for the integrator.
+free fall for the integrator.  ``springs.py`` is the spring-mass example of
+Section 4.1 on the mesh's edges, pinned by physics (rest state, Newton's third
+law, momentum, a two-mass harmonic oscillator).
 """
-from . import fem, implicit  # noqa: F401
+from . import fem, implicit, springs  # noqa: F401
