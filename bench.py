@@ -365,6 +365,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- assembled K on the edge relation vs the matrix-free K w map ------
     asm = assembled_compare(dm, abi, torch, stream, args, flush)
+    spr = springs_leg(dm, m, abi, torch, stream)
 
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
@@ -403,6 +404,7 @@ def run_ours(args, rank, world, local_rank):
             "reduction_variants": variants,
             "layouts": layouts,
             "assembled_K": asm,
+            "spring_mass": spr,
             "e2e": {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -443,6 +445,49 @@ def assembled_compare(dm, abi, torch, stream, args, flush):
                     ts.append(a.elapsed_time(b) * 1e3)
             res[name + "_us"] = statistics.median(ts)
     return res
+
+
+def springs_leg(dm, m, abi, torch, stream, steps=200):
+    """The paper's spring-mass example (Section 4.1, Figure 1) on the 64^3
+    mesh's edges: `steps` explicit steps per timed call, K = 1, dt = 1e-4,
+    equal masses of density 1000 over the unit cube, from a perturbed rest
+    state; FP32 (the figure's floats) and FP64.  Per-step time with CUDA
+    events after warm-up."""
+    rng = np.random.default_rng(7)
+    q0 = m.X + 0.002 * rng.normal(size=m.X.shape)
+    mass = np.full(m.n_verts, 1000.0 / m.n_verts)
+    out = {"steps_per_call": steps, "k": 1.0, "dt": 1e-4}
+    for name, dt_ in (("f32", torch.float32), ("f64", torch.float64)):
+        dm.vertex_field("spos_" + name, dt_, value=m.X)
+        dm.vertex_field("sq_" + name, dt_, value=q0)
+        dm.vertex_field("sqd_" + name, dt_)
+        dm.vertex_field("sm_" + name, dt_, ncomp=1, value=mass)
+        with torch.cuda.stream(stream):
+            abi.ebb_springs_init(dm.ctx, dm.tets, "spos_" + name)
+            for _ in range(3):
+                abi.ebb_springs_run(dm.ctx, dm.tets, "sq_" + name, "sqd_" + name, "sm_" + name, 1.0, 1e-4, 10)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            abi.ebb_springs_run(dm.ctx, dm.tets, "sq_" + name, "sqd_" + name, "sm_" + name, 1.0, 1e-4, steps)
+            b.record(stream)
+            b.synchronize()
+            energy = abi.ebb_springs_run(dm.ctx, dm.tets, "sq_" + name, "sqd_" + name, "sm_" + name, 1.0, 1e-4, 0,
+                                         energy=True)
+        us = a.elapsed_time(b) * 1e3 / steps
+        out[name + "_us_per_step"] = us
+        out[name + "_kinetic_energy_after"] = energy
+    nsprings = int(springs_directed_count(m))
+    out["directed_springs"] = nsprings
+    out["f32_springs_per_s"] = nsprings / (out["f32_us_per_step"] * 1e-6)
+    return out
+
+
+def springs_directed_count(m):
+    """Directed edges of the mesh (pairs of distinct vertices sharing a tet)."""
+    t = m.tets.astype(np.int64)
+    n = np.int64(m.n_verts)
+    keys = [t[:, a] * n + t[:, b] for a in range(4) for b in range(4) if a != b]
+    return np.unique(np.concatenate(keys)).size
 
 
 def implicit_steps(dm, m, abi, torch, stream, args):

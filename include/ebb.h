@@ -270,6 +270,31 @@ ebb_status_t ebb_assemble_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, co
 ebb_status_t ebb_spmv_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* w, const char* Kw_out,
                             const ebb_map_opts_t* opts);
 
+/* ---- spring-mass system on the edges (Section 4.1, Figure 1) ---------- */
+/* The paper's introductory example as a second workload on the same runtime;
+ * the springs are the mesh's edges (needs EBB_FINALIZE_EDGES; relations
+ * finalized with EBB_FINALIZE_REORDER_VERTS are refused with EBB_ERR_STATE).
+ * ebb_springs_init sets every spring's rest length to the distance between
+ * its ends in the vertex field `pos` (F64 or F32, 3 components), kept by the
+ * library in both precisions.  ebb_springs_run advances the vertex fields q
+ * (positions) and qd (velocities) by `steps` explicit steps, in place: per
+ * vertex v, f_v = sum over its springs (v, h) of K (L dir - dq) with
+ * dq = q_v - q_h and dir = dq / |dq| (the restoring reading of the figure,
+ * whose printed dq = q_h - q_v would push a stretched spring's ends apart; a
+ * zero-length dq adds nothing), then qdd = f_v / m_v, q_v += qd_v dt +
+ * qdd dt^2 / 2, qd_v += qdd dt (a vertex with m <= 0 stays).  Every step
+ * takes its forces from the positions at its start; each vertex sums its
+ * springs in a fixed order (no atomics: bitwise reproducible).  q, qd and
+ * the one-component `mass` are planes of one dtype (F64 or F32); the step's
+ * arithmetic is in that dtype.  `energy` (host pointer, may be NULL)
+ * receives sum m |qd|^2 / 2 after the steps (the figure's
+ * measureTotalEnergy; FP64, fixed order) and makes the call synchronous.
+ * Errors: EBB_ERR_ARG (fields, steps < 0, dt < 0), EBB_ERR_STATE (no edge
+ * relation, no ebb_springs_init), EBB_ERR_PHASE (q, qd, mass overlap). */
+ebb_status_t ebb_springs_init(ebb_ctx_t ctx, ebb_rel_t tets, const char* pos);
+ebb_status_t ebb_springs_run(ebb_ctx_t ctx, ebb_rel_t tets, const char* q, const char* qd, const char* mass,
+                             double k, double dt, int32_t steps, double* energy);
+
 /* d += diag(K(u)) (closed form per tet corner and component): the Jacobi
  * preconditioner of Section 7.2. */
 ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,

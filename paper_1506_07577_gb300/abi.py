@@ -97,6 +97,9 @@ _SIGS = {
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_assemble_tet_K": ([ebb_ctx_t, ebb_rel_t, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_spmv_tet_K": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_springs_init": ([ebb_ctx_t, ebb_rel_t, _P], ebb_status_t),
+    "ebb_springs_run": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.c_double, C.c_double, C.c_int32,
+                         C.POINTER(C.c_double)], ebb_status_t),
     "ebb_relation_autotune": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t),
                                C.POINTER(ebb_autotune_report_t)], ebb_status_t),
     "ebb_relation_set_tuning": ([ebb_ctx_t, ebb_rel_t, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
@@ -227,6 +230,19 @@ def ebb_assemble_tet_K(ctx, tets, u, opts):
 
 def ebb_spmv_tet_K(ctx, tets, w, Kw_out, opts):
     return _check(ctx, _lib.ebb_spmv_tet_K(ctx, tets, _b(w), _b(Kw_out), C.byref(opts)))
+
+
+def ebb_springs_init(ctx, tets, pos):
+    return _check(ctx, _lib.ebb_springs_init(ctx, tets, _b(pos)))
+
+
+def ebb_springs_run(ctx, tets, q, qd, mass, k, dt, steps, energy=False):
+    """`steps` spring-mass steps in place; returns the kinetic energy after
+    them when `energy` is true (synchronous), else None."""
+    e = C.c_double(0.0)
+    _check(ctx, _lib.ebb_springs_run(ctx, tets, _b(q), _b(qd), _b(mass), float(k), float(dt), int(steps),
+                                     C.byref(e) if energy else None))
+    return e.value if energy else None
 
 
 def ebb_relation_autotune(ctx, tets, u, w, opts):

@@ -9,6 +9,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -692,6 +693,61 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, con
   mc.out[0] = d_out;
   mc.nout = 1;
   return run_map(ctx, tets, mc, OP_DIAG, opts);
+}
+
+// Spring-mass system (Section 4.1, Figure 1) on the edge relation.
+namespace {
+ebb_status_t springs_checks(ebb_ctx_t ctx, ebb_rel_t tets) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!tets) return set_error(ctx, EBB_ERR_ARG, "null relation");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (tets->edges.row_off == nullptr)
+    return set_error(ctx, EBB_ERR_STATE, "relation finalized without EBB_FINALIZE_EDGES");
+  if (tets->vperm) return set_error(ctx, EBB_ERR_STATE, "springs do not support EBB_FINALIZE_REORDER_VERTS");
+  return EBB_OK;
+}
+}  // namespace
+
+ebb_status_t ebb_springs_init(ebb_ctx_t ctx, ebb_rel_t tets, const char* pos) {
+  ebb_status_t s = springs_checks(ctx, tets);
+  if (s) return s;
+  const Field* f = pos ? find_field(tets->verts, pos) : nullptr;
+  if (!f || f->ncomp != 3 || (f->dtype != EBB_F64 && f->dtype != EBB_F32))
+    return set_error(ctx, EBB_ERR_ARG, "pos must name an F64 or F32 vertex field with 3 components");
+  cudaError_t e = springs_init(tets, f->ptr, f->dtype == EBB_F64, ctx->stream);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the springs failed");
+  }
+  return cuda_check(ctx, e, "spring rest lengths");
+}
+
+ebb_status_t ebb_springs_run(ebb_ctx_t ctx, ebb_rel_t tets, const char* q, const char* qd, const char* mass,
+                             double k, double dt, int32_t steps, double* energy) {
+  ebb_status_t s = springs_checks(ctx, tets);
+  if (s) return s;
+  if (!tets->edges.springs_ready) return set_error(ctx, EBB_ERR_STATE, "call ebb_springs_init first");
+  if (steps < 0 || !(dt >= 0.0) || !std::isfinite(k)) return set_error(ctx, EBB_ERR_ARG, "need steps >= 0, dt >= 0");
+  const Field* fq = q ? find_field(tets->verts, q) : nullptr;
+  if (!fq || fq->ncomp != 3 || (fq->dtype != EBB_F64 && fq->dtype != EBB_F32))
+    return set_error(ctx, EBB_ERR_ARG, "q must name an F64 or F32 vertex field with 3 components");
+  void *pqd = nullptr, *pm = nullptr;
+  s = vertex_field(ctx, tets, qd, fq->dtype, 3, &pqd);
+  if (!s) s = vertex_field(ctx, tets, mass, fq->dtype, 1, &pm);
+  if (s) return s;
+  const size_t es = fq->dtype == EBB_F64 ? 8 : 4;
+  const size_t nv = (size_t)tets->verts->size;
+  if (ranges_overlap(fq->ptr, 3 * nv * es, pqd, 3 * nv * es) || ranges_overlap(fq->ptr, 3 * nv * es, pm, nv * es) ||
+      ranges_overlap(pqd, 3 * nv * es, pm, nv * es))
+    return set_error(ctx, EBB_ERR_PHASE, "q, qd and mass must be three distinct fields");
+  cudaError_t e = springs_run(tets, fq->ptr, pqd, pm, fq->dtype == EBB_F64, k, dt, steps, energy, ctx->stream);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the springs failed");
+  }
+  return cuda_check(ctx, e, "spring steps");
 }
 
 ebb_status_t ebb_assemble_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const ebb_map_opts_t* opts) {

@@ -115,6 +115,12 @@ struct EdgeIndex {
   int* tet_blk = nullptr;
   void* blocks[2] = {nullptr, nullptr};
   bool assembled[2] = {false, false};
+  // Spring-mass system on the edges: rest length per entry (the self-loop's
+  // unused), double-buffered positions, energy partial sums.
+  void* rest[2] = {nullptr, nullptr};
+  void* qbuf[2] = {nullptr, nullptr};
+  double* epart = nullptr;
+  bool springs_ready = false;
 };
 
 struct StepScratch;   // defined in cg.cu
@@ -271,6 +277,14 @@ template <typename T>
 cudaError_t launch_assemble(ebb_rel_s* rel, int model, T mu0, T lam0, const MapIO<T>& io, cudaStream_t st);
 template <typename T>
 cudaError_t launch_spmv(ebb_rel_s* rel, const T* w, T* y, bool aos, const int* active, cudaStream_t st);
+
+// Spring-mass system on the edge relation (springs.cu): rest lengths from
+// the positions X (3 planes, FP64 or FP32), then `steps` steps in place on
+// q, qd (3 planes) with per-vertex mass; *energy (host, may be null)
+// receives the kinetic energy afterwards.
+cudaError_t springs_init(ebb_rel_s* tets, const void* X, bool f64, cudaStream_t st);
+cudaError_t springs_run(ebb_rel_s* tets, void* q, void* qd, const void* mass, bool f64, double k, double dt, int steps,
+                        double* energy, cudaStream_t st);
 
 // Build the colouring (colour.cu).
 ebb_status_t build_colouring(ebb_ctx_s* ctx, ebb_rel_s* tets);

@@ -282,6 +282,11 @@ void free_edges(ebb_rel_s* tets) {
   cudaFree(E.tet_blk);
   cudaFree(E.blocks[0]);
   cudaFree(E.blocks[1]);
+  for (int p = 0; p < 2; ++p) {
+    cudaFree(E.rest[p]);
+    cudaFree(E.qbuf[p]);
+  }
+  cudaFree(E.epart);
   E = EdgeIndex();
 }
 
