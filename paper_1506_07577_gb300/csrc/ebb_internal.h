@@ -63,9 +63,14 @@ struct Colouring {
 //                                    lane of that run (adds the sum into the
 //                                    field)
 //   vtx     int[kTileSlots]          vertex id of each slot
-//   B       T[9][kTileTets]          Dm^-1, entry (r,c) in plane 3r+c
-//   V       T[kTileTets]             rest volume
-//   mu,lam  T[kTileTets] each        per-tet Lame parameters (if bound)
+//   rec     T[kTileTets][rec_len<T>] one row-oriented record per tet (the
+//                                    fields one element uses together):
+//                                    Dm^-1 entries (r,c) at 3r+c, rest
+//                                    volume at 9, Lame mu, lambda at 10, 11
+//                                    (zero without per-tet material), then
+//                                    padding; 48 B (FP32) or 112 B (FP64),
+//                                    strides at which a thread's 16-byte
+//                                    loads stay free of bank conflicts
 // Unused tail entries are zero.
 constexpr int kTileTets = 128;   // tets per tile (= threads per CTA)
 constexpr int kTileSlots = 128;  // distinct vertices per tile (u8 slots)
@@ -80,11 +85,17 @@ constexpr int kBlobPrefix = kBlobVtx + 4 * kTileSlots;
 static_assert(kBlobPrefix % 16 == 0, "blob prefix must keep 16-byte alignment");
 static_assert(kTileTets < 256 && kTileSlots <= 256, "entry code and unit descriptor field widths");
 
+// Per-tet record length of the tile blobs, in elements.
+template <typename T>
+constexpr int rec_len() {
+  return sizeof(T) == 4 ? 12 : 14;
+}
+
 struct BlobLayout {
   int bytes = 0;           // per tile (multiple of 128)
   int copy = 0;            // bytes a kernel copies per tile (multiple of 16, <= bytes)
-  int B = 0, V = 0;        // byte offsets of the element-precision arrays
-  int mu = -1, lam = -1;   // -1: uniform material
+  int rec = 0;             // byte offset of the per-tet records
+  bool material = false;   // records carry per-tet Lame parameters
 };
 
 struct Tiles {

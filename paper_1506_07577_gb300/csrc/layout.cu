@@ -118,21 +118,18 @@ cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
 
 BlobLayout make_layout(size_t elem, bool material) {
   BlobLayout L;
-  L.B = kBlobPrefix;
-  L.V = L.B + (int)(9 * kTileTets * elem);
-  int end = L.V + (int)(kTileTets * elem);
-  if (material) {
-    L.mu = end;
-    L.lam = L.mu + (int)(kTileTets * elem);
-    end = L.lam + (int)(kTileTets * elem);
-  }
+  L.rec = kBlobPrefix;
+  L.material = material;
+  const int rl = elem == 4 ? rec_len<float>() : rec_len<double>();
+  const int end = L.rec + (int)(kTileTets * rl * elem);
   L.copy = (end + 15) / 16 * 16;
   L.bytes = (end + 127) / 128 * 128;
   return L;
 }
 
 // One CTA per tile: copy the integer prefix, then gather the tile's per-tet
-// element-precision values from the planar streams (zero past the tile end).
+// element-precision values from the planar streams into the tets' records
+// (zero past the tile end).
 template <typename T>
 __global__ void pack_blob_kernel(int nt, const unsigned char* __restrict__ prefix, TetStreams<T> s, BlobLayout L,
                                  unsigned char* blob) {
@@ -143,19 +140,17 @@ __global__ void pack_blob_kernel(int nt, const unsigned char* __restrict__ prefi
   for (int i = threadIdx.x; i < kBlobPrefix / 16; i += blockDim.x) dst[i] = src[i];
   const int4 hdr = src[0];
   const int ntets = hdr.x, tb = hdr.z;
-  T* B = reinterpret_cast<T*>(b + L.B);
-  T* V = reinterpret_cast<T*>(b + L.V);
-  T* mu = L.mu >= 0 ? reinterpret_cast<T*>(b + L.mu) : nullptr;
-  T* lam = L.lam >= 0 ? reinterpret_cast<T*>(b + L.lam) : nullptr;
+  constexpr int RL = rec_len<T>();
+  T* R = reinterpret_cast<T*>(b + L.rec);
   for (int i = threadIdx.x; i < kTileTets; i += blockDim.x) {
     const bool in = i < ntets;
     const int t = tb + i;
-    for (int k = 0; k < 9; ++k) B[k * kTileTets + i] = in ? s.B[(size_t)k * nt + t] : T(0);
-    V[i] = in ? s.V[t] : T(0);
-    if (mu) {
-      mu[i] = in ? s.mu[t] : T(0);
-      lam[i] = in ? s.lam[t] : T(0);
-    }
+    T* r = R + (size_t)RL * i;
+    for (int k = 0; k < 9; ++k) r[k] = in ? s.B[(size_t)k * nt + t] : T(0);
+    r[9] = in ? s.V[t] : T(0);
+    r[10] = (in && L.material) ? s.mu[t] : T(0);
+    r[11] = (in && L.material) ? s.lam[t] : T(0);
+    for (int k = 12; k < RL; ++k) r[k] = T(0);
   }
 }
 

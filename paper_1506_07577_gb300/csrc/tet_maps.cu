@@ -557,13 +557,34 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
           }
         }
       }
-      T Bm[9];
-      const T* Bs = reinterpret_cast<const T*>(st + L.B);
+      // The tet's record: Dm^-1, V, mu, lambda in three (FP32) or six (FP64)
+      // 16-byte loads.
+      T rec[12];
+      if constexpr (sizeof(T) == 4) {
+        const float4* R = reinterpret_cast<const float4*>(st + L.rec) + 3 * tid;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) Bm[i] = Bs[i * TT + tid];
-      const T V = reinterpret_cast<const T*>(st + L.V)[tid];
-      const T mu = L.mu >= 0 ? reinterpret_cast<const T*>(st + L.mu)[tid] : mu0;
-      const T lam = L.lam >= 0 ? reinterpret_cast<const T*>(st + L.lam)[tid] : lam0;
+        for (int k = 0; k < 3; ++k) {
+          const float4 q = R[k];
+          rec[4 * k] = q.x;
+          rec[4 * k + 1] = q.y;
+          rec[4 * k + 2] = q.z;
+          rec[4 * k + 3] = q.w;
+        }
+      } else {
+        const double2* R = reinterpret_cast<const double2*>(st + L.rec) + (rec_len<T>() / 2) * tid;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const double2 q = R[k];
+          rec[2 * k] = q.x;
+          rec[2 * k + 1] = q.y;
+        }
+      }
+      T Bm[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Bm[i] = rec[i];
+      const T V = rec[9];
+      const T mu = L.material ? rec[10] : mu0;
+      const T lam = L.material ? rec[11] : lam0;
       good = element_eval<T, MODEL, OPS>(Bm, V, mu, lam, Du, Dw, fo, ko, dgo);
       if (!good) raise_error(err, EBB_ERR_INVERTED, perm[h.z + tid]);
     }
