@@ -108,9 +108,13 @@ struct Tiles {
 // Inverse of the key-field (Section 6.1 GroupBy): for vertex v the entries
 // ent[off[v] .. off[v+1]) are 4*t + a for every internal tet row t whose
 // corner a is v, in increasing order.
+// `order` lists the vertices by their first entry (the vertices of tet 0
+// first, ...): a per-vertex pass walked in this order reads the per-corner
+// data of nearby tets together, whatever the vertex numbering.
 struct VertexIndex {
   int* off = nullptr;
   int* ent = nullptr;
+  int* order = nullptr;
 };
 
 // Edge relation with self-loops (Section 5.2) as block CSR over internal

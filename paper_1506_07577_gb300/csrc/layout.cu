@@ -348,6 +348,7 @@ void free_layout(ebb_rel_s* tets) {
   tets->tiles = Tiles();
   cudaFree(tets->vindex.off);
   cudaFree(tets->vindex.ent);
+  cudaFree(tets->vindex.order);
   tets->vindex = VertexIndex();
   cudaFree(tets->tet_perm);
   tets->tet_perm = nullptr;
@@ -410,10 +411,19 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     }
   }
 
+  std::vector<int> vorder(nv);
+  for (int v = 0; v < nv; ++v) vorder[v] = v;
+  std::stable_sort(vorder.begin(), vorder.end(), [&](int a, int b) {
+    const int ea = voff[a] < voff[a + 1] ? vent[voff[a]] : 0x7fffffff;
+    const int eb = voff[b] < voff[b + 1] ? vent[voff[b]] : 0x7fffffff;
+    return ea < eb;
+  });
+
   const int ntiles = tile_prefix(sorted, nv, tets->tile_cap, prefix);
 
   cudaError_t e = upload(&tets->vindex.off, voff, st);
   if (e == cudaSuccess) e = upload(&tets->vindex.ent, vent, st);
+  if (e == cudaSuccess) e = upload(&tets->vindex.order, vorder, st);
   if (e == cudaSuccess) e = upload(&tets->tet_perm, perm, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {

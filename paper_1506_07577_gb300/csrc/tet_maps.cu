@@ -196,10 +196,11 @@ tet_map_kernel(int t_begin, int t_end, int nt, int nv, const int4* __restrict__ 
 // buffer instead of the vertex fields; entry 4 t + a (corner a of internal
 // tet t) holds its NF output fields x 3 components, component-major with the
 // fields interleaved, so that a tet's 4 entries are 12 NF contiguous values.
-// Pass 2, one thread per vertex: the entries that the vertex index lists
-// for vertex v (Section 6.1's GroupBy: the key-field tets.v inverted into
-// vertex -> (tet, corner) rows, in increasing row order) are summed in that
-// order and added into the output fields with a plain read-modify-write.
+// Pass 2, one thread per vertex (vertices taken in the order of their first
+// tet, for locality): the entries that the vertex index lists for vertex v
+// (Section 6.1's GroupBy: the key-field tets.v inverted into vertex ->
+// (tet, corner) rows, in increasing row order) are summed in that order and
+// added into the output fields with a plain read-modify-write.
 // No atomics, and every run forms the same sums in the same order: the
 // result is bitwise reproducible.  An inverted element contributes zeros.
 template <int OPS>
@@ -255,11 +256,12 @@ constexpr int kSumThreads = 256;
 
 template <typename T, int NF, bool AOS>
 __global__ void __launch_bounds__(kSumThreads)
-vertex_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ ent, const T* __restrict__ corner,
-                  T* out0, T* out1, T* out2, const int* active) {
+vertex_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ ent, const int* __restrict__ order,
+                  const T* __restrict__ corner, T* out0, T* out1, T* out2, const int* active) {
   if (active != nullptr && *active == 0) return;
-  const int v = blockIdx.x * kSumThreads + threadIdx.x;
-  if (v >= nv) return;
+  const int i = blockIdx.x * kSumThreads + threadIdx.x;
+  if (i >= nv) return;
+  const int v = order[i];
   T acc[3 * NF];
 #pragma unroll
   for (int k = 0; k < 3 * NF; ++k) acc[k] = T(0);
@@ -861,7 +863,7 @@ cudaError_t launch_gather(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, con
   if (OPS & OP_KV) outs[f++] = io.Kw;
   if (OPS & OP_DIAG) outs[f++] = io.d;
   vertex_sum_kernel<T, NF, AOS><<<(nv + kSumThreads - 1) / kSumThreads, kSumThreads, 0, stream>>>(
-      nv, rel->vindex.off, rel->vindex.ent, corner, outs[0], outs[1], outs[2], active);
+      nv, rel->vindex.off, rel->vindex.ent, rel->vindex.order, corner, outs[0], outs[1], outs[2], active);
   return cudaGetLastError();
 }
 
