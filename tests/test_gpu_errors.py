@@ -152,6 +152,36 @@ def test_empty_relations():
         assert rep.iters <= 1
 
 
+def test_empty_relations_gather_assembled_springs():
+    """The gather variant, the assembled K and the springs on relations
+    without tets (and without vertices): no error, zero products, free
+    flight of the vertices."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    tets = np.zeros((0, 4), np.int32)
+    o = abi.map_opts(abi.EBB_STVK, 1.0, 1.0, reduce=abi.EBB_REDUCE_GATHER)
+    for nv in (0, 5):
+        X = np.random.default_rng(1).normal(size=(nv, 3))
+        with DeviceTetMesh(X, tets, edges=True) as dm:
+            w = np.random.default_rng(2).normal(size=(nv, 3))
+            dm.vertex_field("u", torch.float64)
+            dm.vertex_field("w", torch.float64, value=w)
+            f = dm.vertex_field("f", torch.float64)
+            k = dm.vertex_field("k", torch.float64)
+            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+            abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u", o)
+            abi.ebb_spmv_tet_K(dm.ctx, dm.tets, "w", "k", o)
+            abi.ebb_ctx_sync(dm.ctx)
+            assert not f.any() and not k.any()
+            abi.ebb_springs_init(dm.ctx, dm.tets, "X")
+            q = dm.vertex_field("q", torch.float64, value=X)
+            qd = dm.vertex_field("qd", torch.float64, value=w)
+            dm.vertex_field("mass", torch.float64, ncomp=1, value=np.ones(nv))
+            e = abi.ebb_springs_run(dm.ctx, dm.tets, "q", "qd", "mass", 1.0, 0.01, 3, energy=True)
+            assert np.allclose(q.cpu().numpy().T, X + 0.03 * w, rtol=0, atol=1e-14)
+            assert abs(e - 0.5 * float(np.sum(w * w))) <= 1e-14 * max(1.0, e)
+
+
 def test_single_tet_matches_hand_derived_forces():
     import json, os
     abi = _abi()
