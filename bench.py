@@ -54,8 +54,8 @@ L2_FLUSH_BYTES = 256 << 20
 # only while the kernel's sources are the ones captured; otherwise reported
 # as null.
 NCU_TRAFFIC = {"sources_sha256_16": "252a86bcdbd333ba", "bytes_per_launch": 121.60e6}
-KERNEL_SOURCES = ["tet_maps.cu", "tet_io.cuh", "tet_math.cuh", "tet_math_x2.cuh", "async_copy.cuh", "ebb_internal.h",
-                  "layout.cu"]
+KERNEL_SOURCES = ["tet_maps.cu", "tile_map.cuh", "element.cuh", "tet_io.cuh", "tet_math.cuh", "tet_math_x2.cuh",
+                  "async_copy.cuh", "ebb_internal.h", "layout.cu"]
 
 
 def kernel_sources_hash():
