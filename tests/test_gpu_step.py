@@ -159,3 +159,41 @@ def test_breakdown_detected_on_device():
         with pytest.raises(abi.EbbError) as ei:
             abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", None, prm)
         assert ei.value.status == abi.EBB_ERR_CG_BREAKDOWN
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_full_size_step_residual_sampled(prec):
+    """At the benchmark size (64^3, neo-Hookean, E log-uniform, from a moving
+    deformed state) the step's linear system is checked at sampled free
+    vertices: the oracle forms b_i and (A dv)_i exactly from the tets around
+    vertex i (A = M + dt^2 K(x_n), b = dt (f + M g - dt K v)), with dv the
+    GPU's velocity change; the residual there is bounded by the solve's
+    tolerance (|r_i| <= ||r||_2 <= rtol ||b||_2), and u' = u + dt v'."""
+    from _problems import submesh_for_vertices
+    n, dt, rho, rtol = 64, 1e-3, 1000.0, 1e-8
+    m, mu, lam = _setup(n, "nh", True, seed=2)
+    u0 = meshgen.random_displacement(m.X, n, amp=0.02, seed=7, smooth=0.01)
+    v0 = 0.05 * meshgen.random_field(m.n_verts, seed=8)
+    v0[m.pinned] = 0.0
+    ug, vg, rg = _gpu_steps(m, mu, lam, "nh", 1, dt, rho, 1000, rtol, prec, u0=u0, v0=v0)
+    assert rg[0].rel_residual <= rtol
+    free = np.flatnonzero(~m.pinned)
+    sample = np.random.default_rng(0).choice(free, size=64, replace=False)
+    sel = np.isin(m.tets, sample).any(axis=1)
+    sub = m.tets[sel]
+    B, V = fem.rest_shape(m.X, sub)
+    x = m.X + u0
+    dv = vg - v0
+    mdl = fem.NEOHOOKEAN
+    f = fem.tet_forces(x, sub, B, V, mu[sel], lam[sel], mdl, m.n_verts)[sample]
+    kv = fem.tet_Kv(x, v0, sub, B, V, mu[sel], lam[sel], mdl, m.n_verts)[sample]
+    kdv = fem.tet_Kv(x, dv, sub, B, V, mu[sel], lam[sel], mdl, m.n_verts)[sample]
+    mass = fem.lumped_mass(V, sub, rho, m.n_verts)[sample][:, None]
+    b = dt * (f + mass * np.array(G) - dt * kv)
+    Adv = mass * dv[sample] + dt * dt * kdv
+    # ||b||_2 over all free rows from the oracle would need the whole mesh;
+    # bound it by sqrt(3 N_free) times the sampled maximum's scale instead
+    bound = rtol * np.sqrt(3 * free.size) * np.max(np.abs(b))
+    assert np.max(np.abs(Adv - b)) <= 10 * bound
+    assert np.max(np.abs(Adv - b)) <= 1e-4 * np.max(np.abs(b))
+    np.testing.assert_allclose(ug[sample], u0[sample] + dt * vg[sample], rtol=0, atol=1e-15)
