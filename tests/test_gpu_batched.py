@@ -115,3 +115,26 @@ def test_batched_rejects_bad_batch_fields():
         with pytest.raises(abi.EbbError) as ei:
             abi.ebb_cg_implicit_step_batched(dm.ctx, dm.tets, "u", "v", None, "batch2", 2, prm)
         assert ei.value.status == abi.EBB_ERR_ARG
+
+
+def test_full_size_batch_sampled_meshes_match_oracle():
+    """The benchmark's batch (256 cube grids, side log-uniform in [4, 24],
+    3.4 M tets), one mixed step in one batched call; the smallest, a middle
+    and the largest mesh are recomputed by the oracle on their own."""
+    abi = _abi()
+    sides = meshgen.batched_sizes(256, 4, 24, seed=4)
+    b = meshgen.cube_grid_batch(sides, jitter=0.01, seed=400)
+    mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+    ub, vb, reps = _batched(b, mu, lam, "nh", abi.EBB_PREC_F32, 1000, 1e-8)
+    order = np.argsort(sides, kind="stable")
+    for mi in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        X, tets, pinned = b.mesh(mi)
+        B, V = fem.rest_shape(X, tets)
+        mass = fem.lumped_mass(V, tets, 1000.0, X.shape[0])
+        uo, vo, info = implicit.implicit_step(X, np.zeros_like(X), np.zeros_like(X), tets, B, V, mass, mu, lam,
+                                              fem.NEOHOOKEAN, 1e-3, np.array(G), pinned, 1000, 1e-8)
+        a, e = b.vert_off[mi], b.vert_off[mi + 1]
+        assert rel_err(vb[a:e], vo) < 1e-5, mi
+        assert rel_err(ub[a:e], uo) < 1e-5, mi
+        assert reps[0][mi].rel_residual <= 1e-8
+        assert abs(reps[0][mi].iters - info["iters"]) <= 2
