@@ -85,7 +85,7 @@ def _rollout_grad_gpu(m, mu, lam, steps, every, u0, v0):
         uT, vT = rollout(dm, tu0, tv0, tmu, tlam, steps, _params(), checkpoint_every=every)
         loss = (uT ** 2).sum()
         loss.backward()
-        return (float(loss), tu0.grad.cpu().numpy().T, tv0.grad.cpu().numpy().T, tmu.grad.cpu().numpy(),
+        return (float(loss.detach()), tu0.grad.cpu().numpy().T, tv0.grad.cpu().numpy().T, tmu.grad.cpu().numpy(),
                 tlam.grad.cpu().numpy())
 
 
@@ -145,6 +145,52 @@ def test_rollout_gradient_matches_gpu_finite_differences():
               - forward_loss(u0 - h * du, v0 - h * dv, mu - h * dmu, lam - h * dlam)) / (2 * h)
         an = np.sum(gu * du) + np.sum(gv * dv) + np.sum(gmu * dmu) + np.sum(glam * dlam)
         assert abs(fd - an) < 1e-4 * abs(an), (trial, fd, an)
+
+
+def test_full_size_rollout_gradient_matches_finite_differences():
+    """The benchmark's differentiable workload at full size (32^3 StVK,
+    per-tet Lame within 20%, 20 steps, checkpoints every 5, dt = 1e-3):
+    the autograd gradient against central differences of the GPU forward
+    rollout along one random direction in (u0, v0, mu, lambda)."""
+    abi = _abi()
+    from paper_1506_07577_gb300.autograd import rollout
+    n, steps, every, dt = 32, 20, 5, 1e-3
+    m = meshgen.cube_grid(n, jitter=0.01, seed=3)
+    mu, lam = meshgen.material_perturbed_lame(m.n_tets, 1e5, 0.45, 0.2, seed=3)
+    prm = abi.step_params(abi.EBB_STVK, dt, 1000.0, precision=abi.EBB_PREC_F64, max_iters=4000, rtol=1e-12)
+    v0 = 0.05 * meshgen.random_field(m.n_verts, seed=3)
+    v0[m.pinned] = 0.0
+
+    def loss_of(mu_, lam_, u0_, v0_):
+        with _mesh(m, mu_, lam_) as dm:
+            dm.vertex_field("fu", torch.float64, value=u0_)
+            dm.vertex_field("fv", torch.float64, value=v0_)
+            for _ in range(steps):
+                abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "fu", "fv", "pinned", prm)
+            return float((dm._tensors["fu"] ** 2).sum())
+
+    with _mesh(m, mu, lam) as dm:
+        tu0 = torch.zeros((3, m.n_verts), dtype=torch.float64, device="cuda", requires_grad=True)
+        tv0 = _dev(v0).requires_grad_(True)
+        tmu = torch.from_numpy(mu).cuda().requires_grad_(True)
+        tlam = torch.from_numpy(lam).cuda().requires_grad_(True)
+        uT, _ = rollout(dm, tu0, tv0, tmu, tlam, steps, prm, checkpoint_every=every)
+        (uT ** 2).sum().backward()
+        gu, gv = tu0.grad.cpu().numpy().T, tv0.grad.cpu().numpy().T
+        gmu, glam = tmu.grad.cpu().numpy(), tlam.grad.cpu().numpy()
+    rng = np.random.default_rng(0)
+    du = rng.normal(size=m.X.shape) * 1e-3
+    du[m.pinned] = 0.0
+    dv = rng.normal(size=m.X.shape) * 1e-2
+    dv[m.pinned] = 0.0
+    dmu = rng.normal(size=mu.shape) * 1e3
+    dlam = rng.normal(size=lam.shape) * 1e3
+    h = 1e-6
+    u0 = np.zeros_like(m.X)
+    fd = (loss_of(mu + h * dmu, lam + h * dlam, u0 + h * du, v0 + h * dv)
+          - loss_of(mu - h * dmu, lam - h * dlam, u0 - h * du, v0 - h * dv)) / (2 * h)
+    an = float(np.sum(gu * du) + np.sum(gv * dv) + np.sum(gmu * dmu) + np.sum(glam * dlam))
+    assert abs(fd - an) < 1e-4 * abs(an), (fd, an)
 
 
 def test_vjp_rejects_unsupported_forms():
