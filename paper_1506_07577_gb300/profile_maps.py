@@ -1,4 +1,5 @@
-"""Run one element map a few times on a cube-grid workload (for profilers).
+"""Run one element map (or the assembled K, or the spring-mass steps) a few
+times on a cube-grid workload (for profilers).
 
     python -m paper_1506_07577_gb300.profile_maps --n 64 --variant tiled --ops fused
 
@@ -28,8 +29,8 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--variant", choices=["atomic", "tiled", "colour"], default="tiled")
-    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step"], default="fused")
+    ap.add_argument("--variant", choices=["atomic", "tiled", "colour", "gather"], default="tiled")
+    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step", "spmv", "springs"], default="fused")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
     ap.add_argument("--permute", action="store_true")
@@ -43,8 +44,10 @@ def main(argv=None):
     w = meshgen.random_field(m.n_verts, seed=2)
     dt = torch.float32 if a.prec == "f32" else torch.float64
     mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
-    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED, "colour": abi.EBB_REDUCE_COLOR}[a.variant]
-    with DeviceTetMesh(m.X, m.tets, mu, lam, colour=(a.variant == "colour")) as dm:
+    red = {"atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED, "colour": abi.EBB_REDUCE_COLOR,
+           "gather": abi.EBB_REDUCE_GATHER}[a.variant]
+    with DeviceTetMesh(m.X, m.tets, mu, lam, colour=(a.variant == "colour"),
+                       edges=a.ops in ("spmv", "springs")) as dm:
         x4 = a.x4 and a.prec == "f32"
         dm.vertex_field("u", dt, value=u, x4=x4)
         dm.vertex_field("w", dt, value=w, x4=x4)
@@ -61,7 +64,20 @@ def main(argv=None):
                                   reduce=red, rtol=1e-8)
             for _ in range(a.iters):
                 abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "uu", "vv", "pinned", prm)
-        for _ in range(a.iters if a.ops != "step" else 0):
+        if a.ops == "spmv":
+            # K(u) assembled once, then the block-sparse product K w
+            abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u", o)
+            for _ in range(a.iters):
+                abi.ebb_spmv_tet_K(dm.ctx, dm.tets, "w", "k", o)
+        elif a.ops == "springs":
+            # spring-mass steps (K = 1, dt = 1e-4, equal masses) from a perturbed rest state
+            dm.vertex_field("pos", dt, value=m.X)
+            dm.vertex_field("q", dt, value=m.X + 0.002 * np.asarray(w))
+            dm.vertex_field("qd", dt)
+            dm.vertex_field("mass", dt, ncomp=1, value=np.full(m.n_verts, 1000.0 / m.n_verts))
+            abi.ebb_springs_init(dm.ctx, dm.tets, "pos")
+            abi.ebb_springs_run(dm.ctx, dm.tets, "q", "qd", "mass", 1.0, 1e-4, a.iters)
+        for _ in range(a.iters if a.ops not in ("step", "spmv", "springs") else 0):
             if a.ops == "fused":
                 abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
             elif a.ops == "kv":
