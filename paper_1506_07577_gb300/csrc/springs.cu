@@ -27,12 +27,16 @@ namespace {
 constexpr int kSpringThreads = 256;
 constexpr int kEnergyBlocks = 304;
 
+// 1 / |dq| from |dq|^2 (CUDA's reciprocal square roots: within 2 ulp in
+// FP32 and 1 ulp in FP64, one call where a square root and a division
+// would be two; FP64 division and square root are long sequences on GB300's
+// FP64 pipe).
 template <typename T>
 __device__ __forceinline__ T inv_len(T n2);
 template <>
-__device__ __forceinline__ float inv_len<float>(float n2) { return 1.0f / sqrtf(n2); }
+__device__ __forceinline__ float inv_len<float>(float n2) { return rsqrtf(n2); }
 template <>
-__device__ __forceinline__ double inv_len<double>(double n2) { return 1.0 / sqrt(n2); }
+__device__ __forceinline__ double inv_len<double>(double n2) { return rsqrt(n2); }
 
 template <typename T>
 __global__ void __launch_bounds__(kSpringThreads)
