@@ -53,7 +53,7 @@ L2_FLUSH_BYTES = 256 << 20
 # (profiles/tet_tile_kernel_fused_nh64.md).  Valid
 # only while the kernel's sources are the ones captured; otherwise reported
 # as null.
-NCU_TRAFFIC = {"sources_sha256_16": "237fb0ff4ba3fabb", "bytes_per_launch": 121.69e6}
+NCU_TRAFFIC = {"sources_sha256_16": "77a71dbb3d417ce1", "bytes_per_launch": 121.93e6}
 KERNEL_SOURCES = ["tet_maps.cu", "tile_map.cuh", "element.cuh", "tet_io.cuh", "tet_math.cuh", "tet_math_x2.cuh",
                   "async_copy.cuh", "ebb_internal.h", "layout.cu"]
 
@@ -326,7 +326,8 @@ def run_ours(args, rank, world, local_rank):
     # ---- reduction variants of the fused map (kernel time only) ----------
     variants = {}
     for name, red in (("atomic", abi.EBB_REDUCE_ATOMIC), ("colour", abi.EBB_REDUCE_COLOR),
-                      ("gather", abi.EBB_REDUCE_GATHER), ("tiled", abi.EBB_REDUCE_TILED)):
+                      ("gather", abi.EBB_REDUCE_GATHER), ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED),
+                      ("tiled", abi.EBB_REDUCE_TILED)):
         o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=red)
         ts = []
         with torch.cuda.stream(stream):
@@ -385,7 +386,9 @@ def run_ours(args, rank, world, local_rank):
                        "atomic": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic, interleaved>",
                        "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured, interleaved>",
                        "gather": "tet_corner_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved> + "
-                                 "vertex_sum_kernel<float, 2, interleaved>"}[tune["reduce"]],
+                                 "vertex_sum_kernel<float, 2, interleaved>",
+                       "tiled_ordered": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved> + "
+                                        "partial_sum_kernel<float, 2, interleaved>"}[tune["reduce"]],
             "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
 
     dm.close()
@@ -492,18 +495,21 @@ def springs_directed_count(m):
 
 def implicit_steps(dm, m, abi, torch, stream, args):
     """10 implicit steps from rest under gravity: the mixed form, the same with
-    K assembled once per step (block-sparse CG products), and the FP64 form.
-    One untimed step first (graph capture), then the state is reset."""
+    K assembled once per step (block-sparse CG products), the same with the
+    ordered tiled reduction (the whole step bitwise reproducible), and the
+    FP64 form.  One untimed step first (graph capture), then the state is
+    reset."""
     uu = dm.vertex_field("u_state", torch.float64)
     vv = dm.vertex_field("v_state", torch.float64)
     dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(uu.device))
     out = {}
     res = {}
-    for name, prec, flags in (("mixed", abi.EBB_PREC_F32, 0), ("mixed_assembled", abi.EBB_PREC_F32,
-                                                              abi.EBB_STEP_ASSEMBLED),
-                              ("fp64", abi.EBB_PREC_F64, 0)):
-        prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, precision=prec, max_iters=1000, rtol=1e-8,
-                              flags=flags)
+    for name, prec, flags, red in (("mixed", abi.EBB_PREC_F32, 0, abi.EBB_REDUCE_AUTO),
+                                   ("mixed_assembled", abi.EBB_PREC_F32, abi.EBB_STEP_ASSEMBLED, abi.EBB_REDUCE_AUTO),
+                                   ("mixed_ordered", abi.EBB_PREC_F32, 0, abi.EBB_REDUCE_TILED_ORDERED),
+                                   ("fp64", abi.EBB_PREC_F64, 0, abi.EBB_REDUCE_AUTO)):
+        prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, precision=prec, reduce=red, max_iters=1000,
+                              rtol=1e-8, flags=flags)
         uu.zero_()
         vv.zero_()
         with torch.cuda.stream(stream):
@@ -530,10 +536,14 @@ def implicit_steps(dm, m, abi, torch, stream, args):
             "v_rel_diff_mixed_vs_fp64_form": du,
             "mixed_assembled_ms_per_step": out["mixed_assembled"]["ms_per_step"],
             "cg_iters_mixed_assembled": out["mixed_assembled"]["cg_iters"],
-            "v_rel_diff_mixed_assembled_vs_fp64_form": da}
+            "v_rel_diff_mixed_assembled_vs_fp64_form": da,
+            "mixed_ordered_ms_per_step": out["mixed_ordered"]["ms_per_step"],
+            "cg_iters_mixed_ordered": out["mixed_ordered"]["cg_iters"],
+            "v_rel_diff_mixed_ordered_vs_fp64_form":
+                (res["mixed_ordered"][1] - res["fp64"][1]).abs().max().item() / vmax}
 
 
-REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather"}
+REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather", 5: "tiled_ordered"}
 
 
 def tune_report(abi, rep):
@@ -731,6 +741,7 @@ def permuted_sweep(abi, torch, local_rank, args, peak):
                                         ("tiled_vertex_reordered", abi.EBB_REDUCE_TILED, dmr, fr, kr, names),
                                         ("atomic", abi.EBB_REDUCE_ATOMIC, dm, f, k, names),
                                         ("gather", abi.EBB_REDUCE_GATHER, dm, f, k, names),
+                                        ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED, dm, f, k, names),
                                         ("colour", abi.EBB_REDUCE_COLOR, dm, f, k, names)):
         o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
         ts = []

@@ -103,13 +103,21 @@ typedef enum { EBB_PREC_F64 = 0, EBB_PREC_F32 = 1 } ebb_precision_t;
  *           reproducible run to run, no colouring needed.  The buffer
  *           (36 values per tet in the map's precision) is allocated on
  *           first use and kept with the relation.
+ *   TILED_ORDERED: TILED, except that each tile stores every per-vertex
+ *           sum to a partial row of its own (a library-owned buffer, 12
+ *           values per tile slot in the map's precision, allocated on first
+ *           use and kept with the tiles) instead of adding it atomically;
+ *           then each vertex adds its partial rows in tile order into its
+ *           field.  No floating-point atomics: bitwise reproducible run to
+ *           run, no colouring needed.
  *   AUTO:   the autotuned choice (ebb_relation_autotune), else TILED. */
 typedef enum {
   EBB_REDUCE_ATOMIC = 0,
   EBB_REDUCE_COLOR = 1,
   EBB_REDUCE_AUTO = 2,
   EBB_REDUCE_TILED = 3,
-  EBB_REDUCE_GATHER = 4
+  EBB_REDUCE_GATHER = 4,
+  EBB_REDUCE_TILED_ORDERED = 5
 } ebb_reduce_t;
 
 /* ebb_relation_finalize flags */
@@ -343,7 +351,8 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                    ebb_autotune_report_t* report);
 
 /* Set by hand what ebb_relation_autotune would choose: EBB_REDUCE_AUTO
- * resolves to `reduce` (TILED, ATOMIC, GATHER or COLOR) for `model` and `precision`;
+ * resolves to `reduce` (TILED, TILED_ORDERED, ATOMIC, GATHER or COLOR) for `model` and
+ * `precision`;
  * the tiles are re-cut to at most `tile_tets` tets (1..128) if that differs;
  * `interleaved` (0/1) sets the FP32 vertex-interleaved staging of the tiled
  * maps.  Synchronous.  Errors: EBB_ERR_ARG (out-of-range value),

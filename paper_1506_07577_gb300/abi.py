@@ -39,6 +39,7 @@ EBB_F32, EBB_F64, EBB_I32, EBB_U8, EBB_F32X4 = 1, 2, 3, 4, 5
 EBB_STVK, EBB_NEOHOOKEAN = 0, 1
 EBB_PREC_F64, EBB_PREC_F32 = 0, 1
 EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED, EBB_REDUCE_GATHER = 0, 1, 2, 3, 4
+EBB_REDUCE_TILED_ORDERED = 5
 EBB_FINALIZE_COLOR = 1
 EBB_FINALIZE_REORDER_VERTS = 2
 EBB_FINALIZE_EDGES = 4

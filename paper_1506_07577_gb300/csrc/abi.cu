@@ -168,7 +168,8 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 
 // A concrete reduction variant (AUTO resolved).
 bool valid_reduce(int r) {
-  return r == EBB_REDUCE_ATOMIC || r == EBB_REDUCE_COLOR || r == EBB_REDUCE_TILED || r == EBB_REDUCE_GATHER;
+  return r == EBB_REDUCE_ATOMIC || r == EBB_REDUCE_COLOR || r == EBB_REDUCE_TILED || r == EBB_REDUCE_GATHER ||
+         r == EBB_REDUCE_TILED_ORDERED;
 }
 
 // EBB_REDUCE_AUTO: the autotuned variant for this model and precision, else
@@ -234,8 +235,8 @@ ebb_status_t launch_map_staged(ebb_ctx_s* ctx, ebb_rel_s* tets, int ops, int mod
   const size_t bytes = (size_t)nv * (x4 ? 16 : 3 * (f64 ? 8 : 4));
   // Reordered vertices are staged anyway, so their FP32 tiled maps always
   // stage interleaved.  EBB_F32X4 fields are interleaved already.
-  const bool stage =
-      !x4 && !f64 && reduce == EBB_REDUCE_TILED && (tets->stage_interleaved || tets->vperm != nullptr);
+  const bool stage = !x4 && !f64 && (reduce == EBB_REDUCE_TILED || reduce == EBB_REDUCE_TILED_ORDERED) &&
+                     (tets->stage_interleaved || tets->vperm != nullptr);
   void* in[2] = {in_user[0], nin > 1 ? in_user[1] : nullptr};
   void* out[3] = {nullptr, nullptr, nullptr};
   for (int i = 0; i < nout; ++i) out[i] = out_user[i];

@@ -98,11 +98,21 @@ struct BlobLayout {
   bool material = false;   // records carry per-tet Lame parameters
 };
 
+// Partial-sum index of the ordered tiled variant (EBB_REDUCE_TILED_ORDERED):
+// reduction unit i of tile t that adds a vertex's run total (the run's first
+// lane) owns partial row t * kTileTets + i; vertex v's rows are
+// vp_ent[vp_off[v] .. vp_off[v+1]), in increasing row (= tile, then unit)
+// order.
 struct Tiles {
   int ntiles = 0;
   unsigned char* blob32 = nullptr;
   unsigned char* blob64 = nullptr;
   BlobLayout L32, L64;
+  int* vp_off = nullptr;
+  int* vp_ent = nullptr;
+  // Partial rows (ntiles * kTileTets rows of 3 fields x 4 values), [0] FP32,
+  // [1] FP64; allocated at first use.
+  void* partial[2] = {nullptr, nullptr};
 };
 
 // Inverse of the key-field (Section 6.1 GroupBy): for vertex v the entries
@@ -202,6 +212,9 @@ struct MapIO {
   T* f = nullptr;          // force accumulator
   T* Kw = nullptr;         // K w accumulator
   T* d = nullptr;          // diag(K) accumulator
+  // Tiled reduction only: when set, each run total is stored to its partial
+  // row (NF groups of 4 values: x, y, z, 0) instead of added to the fields.
+  T* part = nullptr;
   // Vertex-interleaved operands (library-internal fields only): every field
   // above is nv groups of 4 (x, y, z, padding) instead of 3 planes; FP32 and
   // the tiled reduction only.

@@ -342,9 +342,21 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
 
 }  // namespace
 
+// Free the tile blobs and the partial index (not the tile count).
+void free_tiles(Tiles& tl) {
+  cudaFree(tl.blob32);
+  cudaFree(tl.blob64);
+  cudaFree(tl.vp_off);
+  cudaFree(tl.vp_ent);
+  cudaFree(tl.partial[0]);
+  cudaFree(tl.partial[1]);
+  const int n = tl.ntiles;
+  tl = Tiles();
+  tl.ntiles = n;
+}
+
 void free_layout(ebb_rel_s* tets) {
-  cudaFree(tets->tiles.blob32);
-  cudaFree(tets->tiles.blob64);
+  free_tiles(tets->tiles);
   tets->tiles = Tiles();
   cudaFree(tets->vindex.off);
   cudaFree(tets->vindex.ent);
@@ -446,8 +458,7 @@ ebb_status_t rebuild_tiles(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap) {
   if (e != cudaSuccess) return cuda_check(ctx, e, "reading internal keys");
   std::vector<unsigned char> prefix;
   const int ntiles = tile_prefix(sorted, nv, cap, prefix);
-  cudaFree(tets->tiles.blob32);
-  cudaFree(tets->tiles.blob64);
+  free_tiles(tets->tiles);
   tets->tiles = Tiles();
   tets->tiles.ntiles = ntiles;
   tets->tile_cap = cap;
@@ -460,6 +471,39 @@ ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector
   const int ntiles = tl.ntiles;
   if (ntiles == 0) return EBB_OK;
   cudaStream_t st = ctx->stream;
+  {
+    // Partial index of the ordered tiled variant: each run-head unit owns
+    // the row tile * kTileTets + unit; a vertex lists its rows in row order.
+    const int nv = (int)tets->verts->size;
+    std::vector<int> vp_off((size_t)nv + 1, 0), vp_ent;
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<int> fill;
+      if (pass == 1) {
+        for (int v = 0; v < nv; ++v) vp_off[v + 1] += vp_off[v];
+        vp_ent.resize(vp_off[nv]);
+        fill.assign(vp_off.begin(), vp_off.end() - 1);
+      }
+      for (int t = 0; t < ntiles; ++t) {
+        const unsigned char* b = prefix.data() + (size_t)t * kBlobPrefix;
+        const uint32_t* units = reinterpret_cast<const uint32_t*>(b + kBlobUnits);
+        const int* bvtx = reinterpret_cast<const int*>(b + kBlobVtx);
+        for (int i = 0; i < kTileTets; ++i) {
+          if (!((units[i] >> 26) & 1u)) continue;
+          const int v = bvtx[(units[i] >> 14) & 0xffu];
+          if (pass == 0)
+            ++vp_off[(size_t)v + 1];
+          else
+            vp_ent[fill[v]++] = t * kTileTets + i;
+        }
+      }
+    }
+    cudaError_t e = upload(&tl.vp_off, vp_off, st);
+    if (e == cudaSuccess) e = upload(&tl.vp_ent, vp_ent, st);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the tile partial index failed");
+    }
+  }
   const bool material = tets->s64.mu != nullptr;
   tl.L32 = make_layout(sizeof(float), material);
   tl.L64 = make_layout(sizeof(double), material);

@@ -15,6 +15,9 @@
 //           distinct vertex sums its entries in a fixed order (no
 //           shared-memory atomics) and gets one global atomic add per
 //           component (CTA machinery in tile_map.cuh);
+//   tiled ordered  the tiled map with each vertex run total stored to a
+//           partial row of its own instead of added atomically, then one
+//           thread per vertex adds its rows in tile order (deterministic);
 //   gather  per-corner outputs to a buffer, then one thread per vertex sums
 //           its entries in index order (below).
 #include <cstdint>
@@ -202,6 +205,57 @@ vertex_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ e
   }
 }
 
+// Second pass of the ordered tiled variant: vertex order[i] adds its partial
+// rows (NF groups of x, y, z, 0) in row order, i.e. tile by tile, into the
+// fields.
+template <typename T, int NF, bool AOS>
+__global__ void __launch_bounds__(kSumThreads)
+partial_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ ent, const int* __restrict__ order,
+                   const T* __restrict__ part, T* out0, T* out1, T* out2, const int* active) {
+  if (active != nullptr && *active == 0) return;
+  const int i = blockIdx.x * kSumThreads + threadIdx.x;
+  if (i >= nv) return;
+  const int v = order[i];
+  T acc[NF][3];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) acc[f][0] = acc[f][1] = acc[f][2] = T(0);
+  const int e0 = off[v], e1 = off[v + 1];
+#pragma unroll 2
+  for (int e = e0; e < e1; ++e) {
+    const T* p = part + (size_t)__ldg(ent + e) * (4 * NF);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p) + f);
+        acc[f][0] += q.x;
+        acc[f][1] += q.y;
+        acc[f][2] += q.z;
+      } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p + 4 * f));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p + 4 * f) + 1);
+        acc[f][0] += a.x;
+        acc[f][1] += a.y;
+        acc[f][2] += b.x;
+      }
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    T* out = f == 0 ? out0 : (f == 1 ? out1 : out2);
+    if constexpr (AOS) {
+      float4* o = reinterpret_cast<float4*>(out) + v;
+      float4 x = *o;
+      x.x += (float)acc[f][0];
+      x.y += (float)acc[f][1];
+      x.z += (float)acc[f][2];
+      *o = x;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[(size_t)c * nv + v] += acc[f][c];
+    }
+  }
+}
+
 // ---- tiled (machinery in tile_map.cuh) ------------------------------------
 // The standalone map: one pass over fresh rings.
 template <typename T, int MODEL, int OPS, bool AOS>
@@ -308,6 +362,52 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
   return cudaGetLastError();
 }
 
+// Partial rows of the ordered tiled variant (room for three outputs),
+// allocated at first use and kept with the tiles; like the gather buffer,
+// never allocated inside a stream capture.
+template <typename T>
+cudaError_t partial_buffer(ebb_rel_s* rel, cudaStream_t stream, T** out) {
+  void*& buf = rel->tiles.partial[sizeof(T) == 4 ? 0 : 1];
+  if (buf == nullptr) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(stream, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+    e = cudaMalloc(&buf, (size_t)rel->tiles.ntiles * kTileTets * 12 * sizeof(T));
+    if (e != cudaSuccess) {
+      buf = nullptr;
+      return e;
+    }
+  }
+  *out = static_cast<T*>(buf);
+  return cudaSuccess;
+}
+
+// The ordered tiled variant: the tiled map stores each run total to its
+// partial row, then one thread per vertex adds its rows in tile order.  No
+// floating-point atomics, so results repeat bit for bit.
+template <typename T, int MODEL, int OPS, bool AOS>
+cudaError_t launch_tiles_ordered(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, const int* active,
+                                 cudaStream_t stream) {
+  constexpr int NF = ops_nf<OPS>();
+  const Tiles& tl = rel->tiles;
+  const int nv = (int)rel->verts->size;
+  if (tl.ntiles == 0 || nv == 0) return cudaSuccess;
+  MapIO<T> pio = io;
+  cudaError_t e = partial_buffer<T>(rel, stream, &pio.part);
+  if (e != cudaSuccess) return e;
+  e = launch_tiles<T, MODEL, OPS, AOS>(rel, mu0, lam0, pio, active, stream);
+  if (e != cudaSuccess) return e;
+  T* outs[3] = {nullptr, nullptr, nullptr};
+  int f = 0;
+  if (OPS & OP_FORCE) outs[f++] = io.f;
+  if (OPS & OP_KV) outs[f++] = io.Kw;
+  if (OPS & OP_DIAG) outs[f++] = io.d;
+  partial_sum_kernel<T, NF, AOS><<<(nv + kSumThreads - 1) / kSumThreads, kSumThreads, 0, stream>>>(
+      nv, tl.vp_off, tl.vp_ent, rel->vindex.order, pio.part, outs[0], outs[1], outs[2], active);
+  return cudaGetLastError();
+}
+
 template <typename T, int MODEL, int OPS, bool ATOMIC>
 cudaError_t launch_range(int b, int e, int nt, int nv, const int4* keys, const int* perm, const TetStreams<T>& s,
                          T mu0, T lam0, const MapIO<T>& io, const int* active, int* err, cudaStream_t stream) {
@@ -411,6 +511,14 @@ cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, 
       return cudaErrorInvalidValue;
     }
     return launch_tiles<T, MODEL, OPS, false>(rel, mu0, lam0, io, active, stream);
+  }
+  if (reduce == EBB_REDUCE_TILED_ORDERED) {
+    if (io.aos) {
+      if constexpr (sizeof(T) == 4)
+        return launch_tiles_ordered<T, MODEL, OPS, true>(rel, mu0, lam0, io, active, stream);
+      return cudaErrorInvalidValue;
+    }
+    return launch_tiles_ordered<T, MODEL, OPS, false>(rel, mu0, lam0, io, active, stream);
   }
   return launch_range<T, MODEL, OPS, true>(0, nt, nt, nv, rel->keys, rel->tet_perm, streams_of<T>(rel, false), mu0,
                                            lam0, io, active, err, stream);

@@ -169,6 +169,20 @@ __device__ __forceinline__ void tile_init(const TileView<T, OPS>& V) {
 // copies).  AOS: vertex-interleaved operands (MapIO::aos): the producer
 // copies each vertex's 16 bytes with one cp.async, the reduction adds each
 // vertex's three components with one vector atomic.
+// Partial row of reduction unit `unit` in this CTA's j-th tile (ordered
+// tiled variant).
+__device__ __forceinline__ size_t part_row(int j, int G, int unit) {
+  return ((size_t)blockIdx.x + (size_t)j * G) * kTileTets + unit;
+}
+
+__device__ __forceinline__ void st_part4(float* p, float x, float y, float z) {
+  *reinterpret_cast<float4*>(p) = make_float4(x, y, z, 0.f);
+}
+__device__ __forceinline__ void st_part4(double* p, double x, double y, double z) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(x, y);
+  reinterpret_cast<double2*>(p)[1] = make_double2(z, 0.0);
+}
+
 template <typename T, int MODEL, int OPS, bool AOS>
 __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_my, int jbase, int nv,
                                               const unsigned char* __restrict__ blobs, const BlobLayout& L,
@@ -399,7 +413,11 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
       }
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
-        if constexpr (AOS) {
+        if (io.part != nullptr) {
+          float* row = reinterpret_cast<float*>(io.part) + part_row(j, G, tid) * 8;
+          *reinterpret_cast<float4*>(row) = make_float4(acc[0].x, acc[1].x, acc[2].x, 0.f);
+          *reinterpret_cast<float4*>(row + 4) = make_float4(acc[0].y, acc[1].y, acc[2].y, 0.f);
+        } else if constexpr (AOS) {
           red_add_v4(reinterpret_cast<float*>(out_field[0]) + 4 * (size_t)v, acc[0].x, acc[1].x, acc[2].x);
           red_add_v4(reinterpret_cast<float*>(out_field[1]) + 4 * (size_t)v, acc[0].y, acc[1].y, acc[2].y);
         } else {
@@ -440,7 +458,11 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
       }
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
-        if constexpr (AOS) {
+        if (io.part != nullptr) {
+          T* row = io.part + part_row(j, G, tid) * (4 * NF);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) st_part4(row + 4 * f, acc[f], acc[NF + f], acc[2 * NF + f]);
+        } else if constexpr (AOS) {
 #pragma unroll
           for (int f = 0; f < NF; ++f)
             red_add_v4(out_field[f] + 4 * (size_t)v, acc[f], acc[NF + f], acc[2 * NF + f]);

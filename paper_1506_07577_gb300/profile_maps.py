@@ -29,7 +29,7 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--variant", choices=["atomic", "tiled", "colour", "gather"], default="tiled")
+    ap.add_argument("--variant", choices=["atomic", "tiled", "colour", "gather", "ordered"], default="tiled")
     ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step", "spmv", "springs"], default="fused")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
@@ -45,7 +45,7 @@ def main(argv=None):
     dt = torch.float32 if a.prec == "f32" else torch.float64
     mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED, "colour": abi.EBB_REDUCE_COLOR,
-           "gather": abi.EBB_REDUCE_GATHER}[a.variant]
+           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[a.variant]
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=(a.variant == "colour"),
                        edges=a.ops in ("spmv", "springs")) as dm:
         x4 = a.x4 and a.prec == "f32"

@@ -153,9 +153,9 @@ def test_empty_relations():
 
 
 def test_empty_relations_gather_assembled_springs():
-    """The gather variant, the assembled K and the springs on relations
-    without tets (and without vertices): no error, zero products, free
-    flight of the vertices."""
+    """The gather and ordered tiled variants, the assembled K and the
+    springs on relations without tets (and without vertices): no error, zero
+    products, free flight of the vertices."""
     abi = _abi()
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
     tets = np.zeros((0, 4), np.int32)
@@ -169,6 +169,8 @@ def test_empty_relations_gather_assembled_springs():
             f = dm.vertex_field("f", torch.float64)
             k = dm.vertex_field("k", torch.float64)
             abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k",
+                                     abi.map_opts(abi.EBB_STVK, 1.0, 1.0, reduce=abi.EBB_REDUCE_TILED_ORDERED))
             abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u", o)
             abi.ebb_spmv_tet_K(dm.ctx, dm.tets, "w", "k", o)
             abi.ebb_ctx_sync(dm.ctx)

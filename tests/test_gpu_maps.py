@@ -46,14 +46,14 @@ def _run_maps(dm, u, w, model, prec, reduce, mu, lam):
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered"])
 @pytest.mark.parametrize("per_tet", [True, False])
 def test_maps_match_oracle(model, prec, reduce, per_tet):
     abi = _abi()
     m, mu, lam, u, w = problem(6 if per_tet else 7, model, seed=13, per_tet=per_tet)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
-           "gather": abi.EBB_REDUCE_GATHER}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
     with _mesh(m, mu, lam) as dm:
         got = _run_maps(dm, u, w, model, prec, red, mu, lam)
     tol = TOL[prec]
@@ -78,10 +78,11 @@ def test_small_strain_fp32_relative_accuracy():
                 assert rel_err(got["Kw"], Kw) < 1e-5
 
 
-@pytest.mark.parametrize("reduce", ["colour", "gather"])
+@pytest.mark.parametrize("reduce", ["colour", "gather", "ordered"])
 def test_atomic_free_variants_are_bitwise_deterministic(reduce):
     abi = _abi()
-    red = {"colour": abi.EBB_REDUCE_COLOR, "gather": abi.EBB_REDUCE_GATHER}[reduce]
+    red = {"colour": abi.EBB_REDUCE_COLOR, "gather": abi.EBB_REDUCE_GATHER,
+           "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
     m, mu, lam, u, w = problem(7, "nh", seed=3)
     with _mesh(m, mu, lam) as dm:
         a = _run_maps(dm, u, w, "nh", "f32", red, mu, lam)
@@ -107,18 +108,40 @@ def test_gather_needs_no_colouring(prec):
         assert np.array_equal(got[k], again[k])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_ordered_tiles_repeat_at_every_tile_size(prec):
+    """The ordered tiled variant without a colouring: at tiles of 128, 61 and
+    1 tet (the partial index is rebuilt with the tiles) it matches the oracle
+    and repeats bit for bit."""
+    abi = _abi()
+    m, mu, lam, u, w = problem(4, "nh", seed=19)
+    f, Kw, d = oracle_maps(m, mu, lam, u, w, "nh")
+    tol = TOL[prec]
+    p = abi.EBB_PREC_F64 if prec == "f64" else abi.EBB_PREC_F32
+    with _mesh(m, mu, lam, colour=False) as dm:
+        for cap in (128, 61, 1):
+            abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_NEOHOOKEAN, p, abi.EBB_REDUCE_TILED, cap, 0)
+            got = _run_maps(dm, u, w, "nh", prec, abi.EBB_REDUCE_TILED_ORDERED, mu, lam)
+            again = _run_maps(dm, u, w, "nh", prec, abi.EBB_REDUCE_TILED_ORDERED, mu, lam)
+            assert rel_err(got["f"], f) < tol and rel_err(got["Kw"], Kw) < tol and rel_err(got["d"], d) < tol
+            for k in got:
+                assert np.array_equal(got[k], again[k])
+
+
 def test_permuted_ids_match_oracle():
     abi = _abi()
     m, mu, lam, u, w = problem(5, "stvk", seed=8, permute=True)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, "stvk")
     with _mesh(m, mu, lam) as dm:
-        for red in (abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_COLOR, abi.EBB_REDUCE_GATHER):
+        for red in (abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_COLOR, abi.EBB_REDUCE_GATHER,
+                    abi.EBB_REDUCE_TILED_ORDERED):
             got = _run_maps(dm, u, w, "stvk", "f32", red, mu, lam)
             assert rel_err(got["f"], f) < 1e-5 and rel_err(got["Kw"], Kw) < 1e-5
 
 
 @pytest.mark.parametrize("n,model,prec,reorder,reduce", [(64, "nh", "f32", False, "tiled"),
                                                          (64, "nh", "f32", False, "gather"),
+                                                         (64, "nh", "f32", False, "ordered"),
                                                          (128, "stvk", "f32", False, "tiled"),
                                                          (128, "stvk", "f32", True, "tiled"),
                                                          (32, "stvk", "f64", False, "tiled")])
@@ -142,7 +165,8 @@ def test_full_size_sampled_vertices(n, model, prec, reorder, reduce):
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
     with DeviceTetMesh(m.X, m.tets, mu if np.ndim(mu) else None, lam if np.ndim(lam) else None,
                        reorder_verts=reorder) as dm:
-        red = abi.EBB_REDUCE_TILED if reduce == "tiled" else abi.EBB_REDUCE_GATHER
+        red = {"tiled": abi.EBB_REDUCE_TILED, "gather": abi.EBB_REDUCE_GATHER,
+               "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
         got = _run_maps(dm, u, w, model, prec, red, mu, lam)
     tol = TOL[prec]
     assert rel_err(got["f"][sample], f) < tol

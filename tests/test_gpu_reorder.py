@@ -18,7 +18,7 @@ def _abi():
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered"])
 def test_reordered_maps_match_oracle(prec, reduce):
     abi = _abi()
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
@@ -26,7 +26,7 @@ def test_reordered_maps_match_oracle(prec, reduce):
     f, Kw, d = oracle_maps(m, mu, lam, u, w, "nh")
     dt = torch.float64 if prec == "f64" else torch.float32
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
-           "gather": abi.EBB_REDUCE_GATHER}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=True, reorder_verts=True) as dm:
         dm.vertex_field("u", dt, value=u)
         dm.vertex_field("w", dt, value=w)

@@ -55,7 +55,8 @@ def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, re
                               0.0 if per_tet else mu, 0.0 if per_tet else lam, G,
                               abi.EBB_PREC_F64 if precision == "f64" else abi.EBB_PREC_F32,
                               {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR,
-                               "tiled": abi.EBB_REDUCE_TILED, "gather": abi.EBB_REDUCE_GATHER}[reduce],
+                               "tiled": abi.EBB_REDUCE_TILED, "gather": abi.EBB_REDUCE_GATHER,
+                               "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce],
                               max_iters, rtol, fail_on_max)
         reps = []
         for _ in range(steps):
@@ -65,7 +66,7 @@ def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, re
     return u, v, reps
 
 
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered"])
 def test_stvk_fp64_step_n8_matches_oracle(reduce):
     """8x8x8 StVK FP64 workload: one step, dt = 1e-3, 50 CG iterations
     (early stop at 1e-14 relative residual)."""
@@ -90,7 +91,7 @@ def test_fp64_multistep_matches_oracle(model):
 
 
 @pytest.mark.parametrize("pin_dtype,reduce", [(torch.uint8, "tiled"), (torch.int32, "tiled"),
-                                              (torch.uint8, "gather")])
+                                              (torch.uint8, "gather"), (torch.uint8, "ordered")])
 def test_mixed_nh_steps_match_oracle(pin_dtype, reduce):
     """Mixed precision (FP32 element maps, FP64 CG) neo-Hookean with E
     log-uniform in [1e4, 1e6]: error against the FP64 oracle after 4 steps
@@ -104,7 +105,7 @@ def test_mixed_nh_steps_match_oracle(pin_dtype, reduce):
     assert rel_err(ug, uo) < 1e-5
 
 
-@pytest.mark.parametrize("reduce", ["colour", "gather"])
+@pytest.mark.parametrize("reduce", ["colour", "gather", "ordered"])
 def test_atomic_free_step_is_bitwise_deterministic(reduce):
     m, mu, lam = _setup(6, "nh", True, seed=9)
     a = _gpu_steps(m, mu, lam, "nh", 2, 1e-3, 1000.0, 200, 1e-10, "f32", reduce)

@@ -21,7 +21,7 @@ def _got(t):
 
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
-@pytest.mark.parametrize("reduce", ["tiled", "atomic", "colour", "gather"])
+@pytest.mark.parametrize("reduce", ["tiled", "atomic", "colour", "gather", "ordered"])
 @pytest.mark.parametrize("reorder", [False, True])
 def test_x4_maps_match_oracle(model, reduce, reorder):
     abi = _abi()
@@ -29,7 +29,7 @@ def test_x4_maps_match_oracle(model, reduce, reorder):
     m, mu, lam, u, w = problem(6, model, seed=41, permute=reorder)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
-           "gather": abi.EBB_REDUCE_GATHER}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
     mdl = abi.EBB_STVK if model == "stvk" else abi.EBB_NEOHOOKEAN
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=True, reorder_verts=reorder) as dm:
         dm.vertex_field("u", value=u, x4=True)
