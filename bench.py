@@ -54,14 +54,24 @@ L2_FLUSH_BYTES = 256 << 20
 # only while the kernel's sources are the ones captured; otherwise reported
 # as null.
 NCU_TRAFFIC = {"sources_sha256_16": "77a71dbb3d417ce1", "bytes_per_launch": 121.93e6}
+# FP64 arithmetic of the FP64 kernels, counted by ncu (2 x DFMA + DADD + DMUL
+# thread instructions per unit, sm__pipe_fp64_cycles_active) on the 64^3
+# workload, valid while the map and spring sources hash to the same value.
+NCU_FP64 = {"sources_sha256_16": "dc32b4c70d73aa62", "kv_map_nh_flops_per_tet": 454.8,
+            "kv_map_nh_pipe_active": 0.882, "spring_flops_per_directed_spring": 32.15,
+            "spring_pipe_active": 0.858}
+# FP64 peak of the part, derived: 2 DFMA (4 flops) per clock per SM x 152 SMs
+# x the maximum SM clock.
+FP64_PEAK_TFLOPS = 4 * 152 * 2070e6 / 1e12
 KERNEL_SOURCES = ["tet_maps.cu", "tile_map.cuh", "element.cuh", "tet_io.cuh", "tet_math.cuh", "tet_math_x2.cuh",
                   "async_copy.cuh", "ebb_internal.h", "layout.cu"]
+FP64_SOURCES = KERNEL_SOURCES + ["springs.cu"]
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(files=None):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files or KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1506_07577_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -367,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- assembled K on the edge relation vs the matrix-free K w map ------
     asm = assembled_compare(dm, abi, torch, stream, args, flush)
     spr = springs_leg(dm, m, abi, torch, stream)
+    f64map = fp64_map_leg(dm, u, w, abi, torch, stream, flush)
 
     # ---- implicit step: mixed form vs plain FP64 form -------------------
     imp = implicit_steps(dm, m, abi, torch, stream, args)
@@ -408,6 +419,7 @@ def run_ours(args, rank, world, local_rank):
             "layouts": layouts,
             "assembled_K": asm,
             "spring_mass": spr,
+            "fp64_kv_map": f64map,
             "e2e": {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -482,6 +494,46 @@ def springs_leg(dm, m, abi, torch, stream, steps=200):
     nsprings = int(springs_directed_count(m))
     out["directed_springs"] = nsprings
     out["f32_springs_per_s"] = nsprings / (out["f32_us_per_step"] * 1e-6)
+    if kernel_sources_hash(FP64_SOURCES) == NCU_FP64["sources_sha256_16"]:
+        # FP64 steps are bound by the FP64 pipe: flops counted by ncu
+        fl = NCU_FP64["spring_flops_per_directed_spring"] * nsprings
+        out["f64_achieved_tflops"] = fl / (out["f64_us_per_step"] * 1e-6) / 1e12
+        out["f64_frac_of_fp64_peak"] = out["f64_achieved_tflops"] / FP64_PEAK_TFLOPS
+        out["f64_pipe_active_ncu"] = NCU_FP64["spring_pipe_active"]
+    return out
+
+
+def fp64_map_leg(dm, u, w, abi, torch, stream, flush):
+    """The FP64 K w map (neo-Hookean, tiled, 3-plane FP64 fields) that the
+    FP64 form of the implicit step runs once per CG iteration: CUDA-event
+    median of 5 launches after 3 untimed ones, L2 flushed before each,
+    against GB300's FP64 arithmetic peak (the kernel is bound by the FP64
+    pipe, not by HBM)."""
+    nt = dm.n_tets
+    dm.vertex_field("u64", torch.float64, value=u)
+    dm.vertex_field("w64", torch.float64, value=w)
+    kk = dm.vertex_field("k64", torch.float64)
+    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64, reduce=abi.EBB_REDUCE_TILED)
+    ts = []
+    with torch.cuda.stream(stream):
+        for it in range(3 + 5):
+            flush.fill_(float(it))
+            kk.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u64", "w64", "k64", o)
+            b.record(stream)
+            b.synchronize()
+            if it >= 3:
+                ts.append(a.elapsed_time(b) * 1e3)
+    us = statistics.median(ts)
+    out = {"kernel": "tet_tile_kernel<double, NEOHOOKEAN, KV>", "us": us, "tets_per_s": nt / (us * 1e-6),
+           "bound": "alu", "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2070 MHz"}
+    if kernel_sources_hash(FP64_SOURCES) == NCU_FP64["sources_sha256_16"]:
+        fl = NCU_FP64["kv_map_nh_flops_per_tet"]
+        out.update({"fp64_flops_per_tet": fl, "achieved_tflops": fl * nt / (us * 1e-6) / 1e12,
+                    "fp64_pipe_active_ncu": NCU_FP64["kv_map_nh_pipe_active"]})
+        out["frac"] = out["achieved_tflops"] / FP64_PEAK_TFLOPS
     return out
 
 
