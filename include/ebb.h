@@ -261,6 +261,24 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                   const char* w, const char* f_out,
                                   const char* Kw_out, const ebb_map_opts_t* opts);
 
+/* The fused map on host memory (Section 4.3: interop through raw memory
+ * views, here on the host side).  Copies u_host and w_host into the bound
+ * vertex fields u and w, runs ebb_map_tet_force_Kv(u, w, f_out, Kw_out) --
+ * accumulating, or into zeroed fields with EBB_MAP_ZERO_OUT -- copies the
+ * fields f_out and Kw_out into f_host and Kw_host, and returns when the
+ * copies are complete.  Each host buffer holds exactly its field's bytes in
+ * the field's layout (3 planes of N_v values, or N_v EBB_F32X4 elements);
+ * page-locked host memory lets the copies run at full speed, pageable memory
+ * works more slowly.  The host buffers are borrowed for the call only; the
+ * device fields keep the copied and computed values afterwards.  Errors: as
+ * ebb_map_tet_force_Kv (checked before anything is copied); EBB_ERR_ARG for
+ * a null host buffer (with N_v > 0); EBB_ERR_CUDA if a copy fails. */
+ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                       const char* w, const char* f_out,
+                                       const char* Kw_out, const void* u_host,
+                                       const void* w_host, void* f_host, void* Kw_host,
+                                       const ebb_map_opts_t* opts);
+
 /* Assembled stiffness on the edge relation (needs EBB_FINALIZE_EDGES).
  * ebb_assemble_tet_K forms K(u) in opts->precision (replacing any K
  * assembled before in that precision): one 3x3 block per edge and self-loop,

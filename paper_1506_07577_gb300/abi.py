@@ -95,6 +95,8 @@ _SIGS = {
     "ebb_map_tet_forces": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_force_Kv": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
+    "ebb_map_tet_force_Kv_host": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_map_tet_diagK": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_assemble_tet_K": ([ebb_ctx_t, ebb_rel_t, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
     "ebb_spmv_tet_K": ([ebb_ctx_t, ebb_rel_t, _P, _P, C.POINTER(ebb_map_opts_t)], ebb_status_t),
@@ -219,6 +221,27 @@ def ebb_map_tet_Kv(ctx, tets, u, w, Kw_out, opts):
 
 def ebb_map_tet_force_Kv(ctx, tets, u, w, f_out, Kw_out, opts):
     return _check(ctx, _lib.ebb_map_tet_force_Kv(ctx, tets, _b(u), _b(w), _b(f_out), _b(Kw_out), C.byref(opts)))
+
+
+def _host_ptr(buf):
+    """Address of a contiguous host buffer: a CPU torch tensor or a numpy array
+    (None passes a null pointer)."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        if buf.is_cuda or not buf.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+        return buf.data_ptr()
+    if not buf.flags["C_CONTIGUOUS"]:
+        raise ValueError("host buffers must be C-contiguous arrays")
+    return buf.ctypes.data
+
+
+def ebb_map_tet_force_Kv_host(ctx, tets, u, w, f_out, Kw_out, u_host, w_host, f_host, Kw_host, opts):
+    """The fused map on host buffers (each the exact bytes of its field)."""
+    return _check(ctx, _lib.ebb_map_tet_force_Kv_host(ctx, tets, _b(u), _b(w), _b(f_out), _b(Kw_out),
+                                                       _host_ptr(u_host), _host_ptr(w_host), _host_ptr(f_host),
+                                                       _host_ptr(Kw_host), C.byref(opts)))
 
 
 def ebb_map_tet_diagK(ctx, tets, u, d_out, opts):

@@ -686,6 +686,51 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
   return run_map(ctx, tets, mc, OP_FORCE | OP_KV, opts);
 }
 
+ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* w,
+                                       const char* f_out, const char* Kw_out, const void* u_host,
+                                       const void* w_host, void* f_host, void* Kw_host,
+                                       const ebb_map_opts_t* opts) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!tets || !opts) return set_error(ctx, EBB_ERR_ARG, "null relation or options");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  if (opts->precision != EBB_PREC_F64 && opts->precision != EBB_PREC_F32)
+    return set_error(ctx, EBB_ERR_ARG, "unknown precision");
+  // Resolve the fields and apply the map's checks before copying anything.
+  const bool f64 = opts->precision == EBB_PREC_F64;
+  const char* names[4] = {u, w, f_out, Kw_out};
+  void* dev[4];
+  bool x4 = false;
+  ebb_status_t s = map_fields(ctx, tets, names, 4, f64, dev, &x4);
+  if (s) return s;
+  const size_t bytes = (size_t)tets->verts->size * (x4 ? 16 : 3 * (f64 ? 8 : 4));
+  for (int o = 2; o < 4; ++o) {
+    if (ranges_overlap(dev[o], bytes, dev[0], bytes) || ranges_overlap(dev[o], bytes, dev[1], bytes))
+      return set_error(ctx, EBB_ERR_PHASE, std::string("field '") + names[o] +
+                                               "' is both reduced into and read by one map");
+  }
+  if (ranges_overlap(dev[2], bytes, dev[3], bytes))
+    return set_error(ctx, EBB_ERR_PHASE, "two reduce targets of one map overlap");
+  if (bytes > 0 && (!u_host || !w_host || !f_host || !Kw_host))
+    return set_error(ctx, EBB_ERR_ARG, "null host buffer");
+  cudaError_t e = cudaSuccess;
+  if (bytes > 0) {
+    e = cudaMemcpyAsync(dev[0], u_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dev[1], w_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "copying u, w to the device");
+  }
+  s = ebb_map_tet_force_Kv(ctx, tets, u, w, f_out, Kw_out, opts);
+  if (s) return s;
+  if (bytes > 0) {
+    e = cudaMemcpyAsync(f_host, dev[2], bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Kw_host, dev[3], bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "copying f, Kw to the host");
+  }
+  // Waits for the copies and reports any device-detected error of the map.
+  return read_device_error(ctx);
+}
+
 ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* d_out,
                                const ebb_map_opts_t* opts) {
   MapCall mc;

@@ -1,0 +1,90 @@
+"""The fused map on host buffers (ebb_map_tet_force_Kv_host): against the
+FP64 oracle and bit for bit against the device-buffer call (ordered tiled
+reduction), in every field layout; accumulation and refusals."""
+import numpy as np
+import pytest
+import torch
+
+from _problems import oracle_maps, problem, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _abi():
+    from paper_1506_07577_gb300 import abi
+    return abi
+
+
+def _host(arr, layout):
+    """Host copy of an (N_v, 3) array in a field's layout, page-locked."""
+    if layout == "x4":
+        t = torch.zeros((arr.shape[0], 4), dtype=torch.float32)
+        t[:, :3] = torch.from_numpy(arr.astype(np.float32))
+    else:
+        dt = torch.float64 if layout == "f64" else torch.float32
+        t = torch.from_numpy(np.ascontiguousarray(arr.T)).to(dt)
+    return t.pin_memory()
+
+
+def _vec(t, layout):
+    return (t[:, :3] if layout == "x4" else t.T).double().cpu().numpy()
+
+
+@pytest.mark.parametrize("layout", ["x4", "f32", "f64"])
+def test_host_map_matches_oracle_and_device_call(layout):
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(6, "nh", seed=47)
+    f, Kw, _ = oracle_maps(m, mu, lam, u, w, "nh")
+    x4 = layout == "x4"
+    dt = torch.float64 if layout == "f64" else torch.float32
+    prec = abi.EBB_PREC_F64 if layout == "f64" else abi.EBB_PREC_F32
+    tol = 1e-12 if layout == "f64" else 1e-5
+    with DeviceTetMesh(m.X, m.tets, mu, lam) as dm:
+        for name in ("u", "w", "f", "k", "ud", "wd", "fd", "kd"):
+            dm.vertex_field(name, dt, x4=x4)
+        uh, wh = _host(u, layout), _host(w, layout)
+        fh, kh = torch.zeros_like(uh).pin_memory(), torch.zeros_like(uh).pin_memory()
+        o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=prec, reduce=abi.EBB_REDUCE_TILED_ORDERED,
+                         flags=abi.EBB_MAP_ZERO_OUT)
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
+        # the same map through device buffers
+        dm._tensors["ud"].copy_(uh)
+        dm._tensors["wd"].copy_(wh)
+        torch.cuda.synchronize()
+        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "ud", "wd", "fd", "kd", o)
+        abi.ebb_ctx_sync(dm.ctx)
+        assert torch.equal(fh, dm._tensors["fd"].cpu()) and torch.equal(kh, dm._tensors["kd"].cpu())
+        assert torch.equal(dm._tensors["f"].cpu(), fh)       # device fields keep the results
+        # accumulation without EBB_MAP_ZERO_OUT
+        o.flags = 0
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
+    assert rel_err(_vec(fh, layout), 2 * f) < tol
+    assert rel_err(_vec(kh, layout), 2 * Kw) < tol
+
+
+def test_host_map_refusals_leave_fields_untouched():
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(3, "stvk", seed=48)
+    with DeviceTetMesh(m.X, m.tets, mu, lam) as du:
+        tu = du.vertex_field("u", torch.float64, value=u)
+        du.vertex_field("w", torch.float64, value=w)
+        du.vertex_field("f", torch.float64)
+        du.vertex_field("k", torch.float64)
+        du.vertex_field("k32", torch.float32)
+        before = tu.clone()
+        uh = _host(np.zeros_like(u), "f64")
+        wh, fh, kh = uh.clone(), uh.clone(), uh.clone()
+        o = abi.map_opts(abi.EBB_STVK, precision=abi.EBB_PREC_F64)
+        with pytest.raises(abi.EbbError) as ei:              # u is also a reduce target
+            abi.ebb_map_tet_force_Kv_host(du.ctx, du.tets, "u", "w", "u", "k", uh, wh, fh, kh, o)
+        assert ei.value.status == abi.EBB_ERR_PHASE
+        with pytest.raises(abi.EbbError) as ei:              # null host buffer
+            abi.ebb_map_tet_force_Kv_host(du.ctx, du.tets, "u", "w", "f", "k", uh, None, fh, kh, o)
+        assert ei.value.status == abi.EBB_ERR_ARG
+        with pytest.raises(abi.EbbError) as ei:              # an FP32 field in an FP64 map
+            abi.ebb_map_tet_force_Kv_host(du.ctx, du.tets, "u", "w", "f", "k32", uh, wh, fh, kh, o)
+        assert ei.value.status == abi.EBB_ERR_ARG
+        torch.cuda.synchronize()
+        assert torch.equal(tu, before)                       # nothing was copied in
