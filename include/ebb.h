@@ -104,12 +104,15 @@ typedef enum { EBB_PREC_F64 = 0, EBB_PREC_F32 = 1 } ebb_precision_t;
  *           (36 values per tet in the map's precision) is allocated on
  *           first use and kept with the relation.
  *   TILED_ORDERED: TILED, except that each tile stores every per-vertex
- *           sum to a partial row of its own (a library-owned buffer, 12
- *           values per tile slot in the map's precision, allocated on first
- *           use and kept with the tiles) instead of adding it atomically;
- *           then each vertex adds its partial rows in tile order into its
- *           field.  No floating-point atomics: bitwise reproducible run to
- *           run, no colouring needed.
+ *           sum to a partial row of its own instead of adding it atomically
+ *           (a library-owned buffer of 128 rows of 12 values per tile in
+ *           the map's precision, allocated on first use and kept with the
+ *           tiles; a first use inside a stream capture fails with
+ *           EBB_ERR_CUDA, like GATHER's); then each vertex adds
+ *           its partial rows in tile order into its field.  No
+ *           floating-point atomics: bitwise reproducible run to run, no
+ *           colouring needed.  Not an autotuner candidate (it is the tiled
+ *           pass plus a second pass).
  *   AUTO:   the autotuned choice (ebb_relation_autotune), else TILED. */
 typedef enum {
   EBB_REDUCE_ATOMIC = 0,
