@@ -423,7 +423,10 @@ def run_ours(args, rank, world, local_rank):
                     "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "call": "ebb_map_tet_force_Kv_host on page-locked host buffers (EBB_MAP_ZERO_OUT)"},
-            "gpu_launches": args.steps,
+            # library kernels per timed step: the map's launches for the
+            # autotuned variant (the zeroing of f, K w is torch's fill)
+            "gpu_launches": args.steps * {"tiled": 1, "atomic": 1, "gather": 2, "tiled_ordered": 2}.get(
+                tune["reduce"], 1),
             "clocks": clk,
             "implicit_step": imp,
             "batched_step": bat,
