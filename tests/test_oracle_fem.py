@@ -207,3 +207,42 @@ def test_single_tet_closed_form_golden():
         x = X @ F.T
         f = fem.tet_forces(x, tets, B, V, case["mu"], case["lam"], case["model"])
         assert np.max(np.abs(f - np.array(case["f"]))) < 1e-13, case["name"]
+
+
+def test_lumped_mass_of_one_tet_is_a_quarter_at_each_vertex():
+    """A single rest tet: each of its four vertices carries rho V / 4, and a
+    vertex outside the tet carries nothing (per vertex, not just the total)."""
+    rng = np.random.default_rng(5)
+    P = rng.normal(size=(5, 3))
+    tets = np.array([[4, 2, 0, 3]])
+    if np.linalg.det(np.stack([P[2] - P[4], P[0] - P[4], P[3] - P[4]], 1)) < 0:
+        tets = np.array([[4, 2, 3, 0]])
+    _, V = fem.rest_shape(P, tets)
+    m = fem.lumped_mass(V, tets, 1000.0, 5)
+    vol = abs(np.linalg.det(np.stack([P[2] - P[4], P[0] - P[4], P[3] - P[4]], 1))) / 6.0
+    assert np.array_equal(m == 0, np.array([False, True, False, False, False]))
+    assert np.allclose(m[[0, 2, 3, 4]], 1000.0 * vol / 4.0, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_lumped_mass_per_vertex_on_an_unjittered_grid(n):
+    """Closed form on an unjittered grid of spacing h = 1/n.  In the 5-tet
+    split of a cube the central tet has volume h^3/3 and each corner tet
+    h^3/6.  A cube corner of the central tet lies in it and in three corner
+    tets (5 h^3/6 in all), a cube corner of a corner tet lies in that tet
+    alone (h^3/6).  The central tet takes the corners whose global index sum
+    i + j + k is odd in both cube parities, so every vertex gets rho h^3/24
+    per adjacent cube, times 5 if i + j + k is odd."""
+    m = meshgen.cube_grid(n, jitter=0.0)
+    _, V = fem.rest_shape(m.X, m.tets)
+    rho = 1000.0
+    mass = fem.lumped_mass(V, m.tets, rho, m.n_verts)
+    h = 1.0 / n
+    idx = np.arange(m.n_verts)
+    i, j, k = idx % (n + 1), (idx // (n + 1)) % (n + 1), idx // (n + 1) ** 2
+    assert np.allclose(m.X, np.stack([i, j, k], 1) * h, atol=1e-15)
+    cubes = np.ones(m.n_verts)
+    for g in (i, j, k):
+        cubes *= np.where((g == 0) | (g == n), 1, 2)
+    want = rho * h ** 3 / 24.0 * cubes * np.where((i + j + k) % 2 == 1, 5.0, 1.0)
+    assert np.max(np.abs(mass - want)) < 1e-12 * rho * h ** 3
