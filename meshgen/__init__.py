@@ -252,6 +252,54 @@ def cube_grid_batch(sides, jitter: float = 0.01, seed: int = 0) -> MeshBatch:
                      vert_off=np.asarray(voff), tet_off=np.asarray(toff))
 
 
+
+@dataclasses.dataclass
+class HubMesh:
+    """Tets (0, r_i, r_{i+1}, a_j) around a hub vertex (see ``hub_fan``).
+
+    X    : (N_v, 3) float64 rest positions: hub at 0, ring vertices 1..K+1,
+           apex vertices after them
+    tets : (K * J, 4) int32 keys
+    """
+    X: np.ndarray
+    tets: np.ndarray
+
+    @property
+    def n_verts(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def n_tets(self) -> int:
+        return int(self.tets.shape[0])
+
+
+def hub_fan(segments: int, apexes: int, seed: int) -> HubMesh:
+    """A mesh of high vertex valence (non-conforming: tets overlap).
+
+    The hub vertex sits at the origin and an open ring of ``segments + 1``
+    vertices lies in the plane z = 0 at unit radius, at increasing angles (a
+    span of at most 5.5 rad); ``apexes`` vertices lie above the plane (z in
+    [0.5, 1.5], x and y in [-1, 1]).  Every pair (ring segment, apex) is one
+    tet (hub, r_i, r_{i+1}, apex): the triangle (hub, r_i, r_{i+1}) turns
+    counter-clockwise seen from above and the apex lies above it, so every
+    tet is positively oriented by construction.  The hub is a corner of all
+    segments * apexes tets, ring vertices of up to 2 * apexes, apexes of
+    ``segments``.  With segments = 1 it is a fan of tets around one shared
+    triangle."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7000))
+    span = min(0.5 * segments, 5.5)
+    ang = np.linspace(0.0, span, segments + 1)
+    ring = np.stack([np.cos(ang), np.sin(ang), np.zeros_like(ang)], axis=1)
+    ap = np.stack([rng.uniform(-1, 1, apexes), rng.uniform(-1, 1, apexes), rng.uniform(0.5, 1.5, apexes)], axis=1)
+    X = np.concatenate([np.zeros((1, 3)), ring, ap])
+    i = np.repeat(np.arange(segments), apexes)
+    j = np.tile(np.arange(apexes), segments)
+    tets = np.stack([np.zeros_like(i), 1 + i, 2 + i, segments + 2 + j], axis=1)
+    # tets listed apex-major in a seeded random order, so that tiles mix
+    # segments and apexes
+    tets = tets[rng.permutation(tets.shape[0])]
+    return HubMesh(X=np.ascontiguousarray(X), tets=np.ascontiguousarray(tets.astype(np.int32)))
+
 # Workload recipes.  They stand in for the paper's FEM workloads (Section 7.2,
 # Vega: StVK, implicit backward Euler, Jacobi PCG on tet meshes; Section 7.3,
 # FreeFem++: neo-Hookean, implicit CG), whose meshes are not available: cube

@@ -119,9 +119,9 @@ def test_assembled_fp64_step_matches_oracle():
     abi = _abi()
     m = meshgen.cube_grid(6, jitter=0.01, seed=64)
     mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
-    uo, vo, io = _oracle(m, mu, lam, "stvk", 2, 400, 1e-12)
-    ug, vg, rg = _steps(m, mu, lam, "stvk", 2, "f64", abi.EBB_STEP_ASSEMBLED)
-    assert rel_err(vg, vo) < 1e-10 and rel_err(ug, uo) < 1e-10
+    uo, vo, io = _oracle(m, mu, lam, "stvk", 2, 400, 1e-14)
+    ug, vg, rg = _steps(m, mu, lam, "stvk", 2, "f64", abi.EBB_STEP_ASSEMBLED, rtol=1e-14)
+    assert rel_err(vg, vo) < 1e-12 and rel_err(ug, uo) < 1e-12
     assert all(abs(a.iters - b["iters"]) <= 2 for a, b in zip(rg, io))
 
 

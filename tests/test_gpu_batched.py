@@ -57,14 +57,14 @@ def test_batched_fp64_equals_single_mesh_steps(model):
     mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
     v0 = 0.05 * meshgen.random_field(b.X.shape[0], seed=5)
     v0[b.pinned] = 0.0
-    ub, vb, reps = _batched(b, mu, lam, model, abi.EBB_PREC_F64, 400, 1e-12, v0, steps=2)
+    ub, vb, reps = _batched(b, mu, lam, model, abi.EBB_PREC_F64, 400, 1e-14, v0, steps=2)
     iters = set()
     for m in range(len(b.sides)):
         X, tets, pinned = b.mesh(m)
         a, e = b.vert_off[m], b.vert_off[m + 1]
-        us, vs, rs = _single(X, tets, pinned, mu, lam, model, abi.EBB_PREC_F64, 400, 1e-12, v0[a:e], steps=2)
-        assert rel_err(vb[a:e], vs) < 1e-10, m
-        assert rel_err(ub[a:e], us) < 1e-10, m
+        us, vs, rs = _single(X, tets, pinned, mu, lam, model, abi.EBB_PREC_F64, 400, 1e-14, v0[a:e], steps=2)
+        assert rel_err(vb[a:e], vs) < 1e-12, m
+        assert rel_err(ub[a:e], us) < 1e-12, m
         for k in range(2):
             assert abs(reps[k][m].iters - rs[k].iters) <= 1
             assert reps[k][m].status == abi.EBB_OK

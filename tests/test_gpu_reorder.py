@@ -61,14 +61,14 @@ def test_reordered_step_matches_oracle():
     uo, vo, u_ = np.zeros_like(m.X), v0.copy(), None
     for _ in range(2):
         uo, vo, _ = implicit.implicit_step(m.X, uo, vo, m.tets, B, V, mass, mu, lam, fem.STVK, 1e-3,
-                                           np.array([0, 0, -9.81]), m.pinned, 400, 1e-12)
-    for prec, tol in ((abi.EBB_PREC_F64, 1e-10), (abi.EBB_PREC_F32, 1e-5)):
+                                           np.array([0, 0, -9.81]), m.pinned, 400, 1e-14)
+    for prec, tol in ((abi.EBB_PREC_F64, 1e-12), (abi.EBB_PREC_F32, 1e-5)):
         with DeviceTetMesh(m.X, m.tets, reorder_verts=True) as dm:
             uu = dm.vertex_field("u", torch.float64)
             vv = dm.vertex_field("v", torch.float64, value=v0)
             dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.int32)).to(dm.device))
             prm = abi.step_params(abi.EBB_STVK, 1e-3, 1000.0, mu, lam, precision=prec, max_iters=400,
-                                  rtol=1e-12 if prec == abi.EBB_PREC_F64 else 1e-8)
+                                  rtol=1e-14 if prec == abi.EBB_PREC_F64 else 1e-8)
             for _ in range(2):
                 abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm)
             assert rel_err(vv.cpu().numpy().T, vo) < tol

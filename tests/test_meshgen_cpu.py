@@ -47,3 +47,18 @@ def test_generators_repeat_for_a_seed():
     # E = mu (3 lam + 2 mu) / (lam + mu) stays inside [1e4, 1e6]
     E = mu1 * (3 * lam1 + 2 * mu1) / (lam1 + mu1)
     assert E.min() >= 1e4 * (1 - 1e-12) and E.max() <= 1e6 * (1 + 1e-12)
+
+
+def test_hub_fan_counts_valence_and_orientation():
+    for segments, apexes in ((1, 700), (16, 24)):
+        m = meshgen.hub_fan(segments, apexes, seed=3)
+        assert m.n_tets == segments * apexes and m.n_verts == segments + 2 + apexes
+        cnt = np.bincount(m.tets.ravel(), minlength=m.n_verts)
+        assert cnt[0] == segments * apexes                 # the hub is in every tet
+        assert cnt[segments + 2:].tolist() == [segments] * apexes
+        e = m.X[m.tets[:, 1:]] - m.X[m.tets[:, :1]]
+        assert np.all(np.linalg.det(e.transpose(0, 2, 1)) > 0)
+        assert len({tuple(t) for t in np.sort(m.tets, axis=1).tolist()}) == m.n_tets
+    a = meshgen.hub_fan(16, 24, seed=3)
+    b = meshgen.hub_fan(16, 24, seed=3)
+    assert np.array_equal(a.X, b.X) and np.array_equal(a.tets, b.tets)
