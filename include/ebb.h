@@ -275,7 +275,9 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * works more slowly.  The host buffers are borrowed for the call only; the
  * device fields keep the copied and computed values afterwards.  Errors: as
  * ebb_map_tet_force_Kv (checked before anything is copied); EBB_ERR_ARG for
- * a null host buffer (with N_v > 0); EBB_ERR_CUDA if a copy fails. */
+ * a null host buffer (with N_v > 0); EBB_ERR_PHASE if the device fields u
+ * and w overlap, unless they are the same field and u_host == w_host (one
+ * copy then fills it); EBB_ERR_CUDA if a copy fails. */
 ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                        const char* w, const char* f_out,
                                        const char* Kw_out, const void* u_host,
@@ -382,6 +384,25 @@ ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t mode
                                      int32_t precision, int32_t reduce, int32_t tile_tets,
                                      int32_t interleaved);
 
+/* Layout of a finalized tets relation as the maps see it (read only, host
+ * side): how many tiles the tiled variants walk and how many tets each holds
+ * at most, how many colours the coloured variant launches, whether FP32 tiled
+ * maps stage their operands vertex-interleaved, whether vertices are
+ * renumbered internally, and the variant EBB_REDUCE_AUTO resolves to per
+ * [model][precision] (-1: not tuned, AUTO means TILED).  Errors:
+ * EBB_ERR_ARG (null argument), EBB_ERR_STATE (not finalized). */
+typedef struct {
+  int64_t n_tets, n_verts;
+  int32_t ntiles;          /* tiles of the tiled variants */
+  int32_t tile_tets;       /* tets per tile at most */
+  int32_t ncolours;        /* colours (0 without EBB_FINALIZE_COLOR) */
+  int32_t interleaved;     /* FP32 tiled maps stage operands vertex-interleaved */
+  int32_t reordered;       /* finalized with EBB_FINALIZE_REORDER_VERTS */
+  int32_t tuned[2][2];     /* autotuned reduce per [model][precision], -1 none */
+} ebb_relation_info_t;
+
+ebb_status_t ebb_relation_info(ebb_ctx_t ctx, ebb_rel_t tets, ebb_relation_info_t* info);
+
 /* ---- implicit step (Section 7.2, Section 7.3) --------------------------- */
 
 /* One linearised backward-Euler step, in place on the F64 vertex fields
@@ -394,7 +415,8 @@ ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t mode
  * except one status read per batch of iterations.  Synchronous; fills
  * *report (may be NULL).  Errors: EBB_ERR_CG_BREAKDOWN,
  * EBB_ERR_NOT_CONVERGED (if requested), EBB_ERR_INVERTED, plus argument
- * errors. */
+ * errors.  After a solve that ran, u and v are advanced with the last CG
+ * iterate even when the call returns one of these three errors. */
 ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                   const char* v, const char* pinned,
                                   const ebb_step_params_t* params,
@@ -462,13 +484,19 @@ ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const c
  * process exits), so sizes are capped: n_verts <=
  * EBB_NOALLOC_MAX_VERTS and n_tets <= EBB_NOALLOC_MAX_TETS, else EBB_ERR_ARG
  * before any work is enqueued.  The call neither allocates nor frees device
- * memory.  The first call on a device looks up the array's device address
- * (make it before any stream capture).  Every call reuses the same array, so
- * two calls whose work overlaps on the GPU (other streams, other host threads)
- * race and corrupt each other; the call clears what must start at zero.
+ * memory.  Every call looks up the array's device address on the current
+ * device; the first call on a device also loads the library's device code
+ * there, so make it before any stream capture.  Every call reuses the same
+ * array, so two calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and corrupt each other; the call clears what must start
+ * at zero.
  * Errors: EBB_ERR_ARG, EBB_ERR_KEY, EBB_ERR_INVERTED, EBB_ERR_CG_BREAKDOWN,
  * EBB_ERR_NOT_CONVERGED (if requested), EBB_ERR_CUDA.  There is no context,
- * so no message: only the status code. */
+ * so no message: only the status code.  A bad key or an inverted rest tet is
+ * found before anything is written, and u, v are then left untouched; after
+ * a solve that ran (EBB_ERR_INVERTED from an element of the deformed state,
+ * EBB_ERR_CG_BREAKDOWN, EBB_ERR_NOT_CONVERGED) u and v have been advanced with
+ * the last CG iterate, as ebb_cg_implicit_step does. */
 #define EBB_NOALLOC_MAX_VERTS 4096
 #define EBB_NOALLOC_MAX_TETS 24576
 ebb_status_t ebb_cg_implicit_step_noalloc(void* cuda_stream, int32_t n_verts, int32_t n_tets,

@@ -82,6 +82,12 @@ class ebb_cg_report_t(C.Structure):
     _fields_ = [("iters", C.c_int32), ("rel_residual", C.c_double), ("status", C.c_int32)]
 
 
+class ebb_relation_info_t(C.Structure):
+    _fields_ = [("n_tets", C.c_int64), ("n_verts", C.c_int64), ("ntiles", C.c_int32), ("tile_tets", C.c_int32),
+                ("ncolours", C.c_int32), ("interleaved", C.c_int32), ("reordered", C.c_int32),
+                ("tuned", (C.c_int32 * 2) * 2)]
+
+
 _P = C.c_char_p
 _SIGS = {
     "ebb_ctx_create": ([C.POINTER(ebb_ctx_t), C.c_int, C.c_void_p], ebb_status_t),
@@ -107,6 +113,7 @@ _SIGS = {
                                C.POINTER(ebb_autotune_report_t)], ebb_status_t),
     "ebb_relation_set_tuning": ([ebb_ctx_t, ebb_rel_t, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
                                 ebb_status_t),
+    "ebb_relation_info": ([ebb_ctx_t, ebb_rel_t, C.POINTER(ebb_relation_info_t)], ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_vjp": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ebb_step_params_t),
@@ -280,6 +287,13 @@ def ebb_relation_autotune(ctx, tets, u, w, opts):
 def ebb_relation_set_tuning(ctx, tets, model, precision, reduce, tile_tets, interleaved):
     return _check(ctx, _lib.ebb_relation_set_tuning(ctx, tets, int(model), int(precision), int(reduce),
                                                     int(tile_tets), int(bool(interleaved))))
+
+
+def ebb_relation_info(ctx, tets):
+    """Layout of a finalized tets relation (tiles, colours, staging, tuning)."""
+    info = ebb_relation_info_t()
+    _check(ctx, _lib.ebb_relation_info(ctx, tets, C.byref(info)))
+    return info
 
 
 def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,

@@ -714,10 +714,17 @@ ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char
     return set_error(ctx, EBB_ERR_PHASE, "two reduce targets of one map overlap");
   if (bytes > 0 && (!u_host || !w_host || !f_host || !Kw_host))
     return set_error(ctx, EBB_ERR_ARG, "null host buffer");
+  // Both input copies land in the bound fields: if u and w overlap on the
+  // device, the second copy would overwrite the first, unless they are one
+  // field filled from one host buffer.
+  const bool same_input = dev[0] == dev[1] && u_host == w_host;
+  if (ranges_overlap(dev[0], bytes, dev[1], bytes) && !same_input)
+    return set_error(ctx, EBB_ERR_PHASE, "fields u and w overlap on the device but come from different host buffers");
   cudaError_t e = cudaSuccess;
   if (bytes > 0) {
     e = cudaMemcpyAsync(dev[0], u_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dev[1], w_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && !same_input)
+      e = cudaMemcpyAsync(dev[1], w_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "copying u, w to the device");
   }
   s = ebb_map_tet_force_Kv(ctx, tets, u, w, f_out, Kw_out, opts);
@@ -958,6 +965,25 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
   report->tile_tets = tets->tile_cap;
   report->interleaved = (!f64 && (x4 || tets->stage_interleaved)) ? 1 : 0;
   report->ncand = nc;
+  return EBB_OK;
+}
+
+ebb_status_t ebb_relation_info(ebb_ctx_t ctx, ebb_rel_t tets, ebb_relation_info_t* info) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!tets || !info) return set_error(ctx, EBB_ERR_ARG, "null argument");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  memset(info, 0, sizeof *info);
+  info->n_tets = tets->size;
+  info->n_verts = tets->verts->size;
+  info->ntiles = tets->tiles.ntiles;
+  info->tile_tets = tets->tile_cap;
+  info->ncolours = tets->has_colour ? tets->colour.ncolours : 0;
+  info->interleaved = tets->stage_interleaved ? 1 : 0;
+  info->reordered = tets->vperm != nullptr ? 1 : 0;
+  for (int m = 0; m < 2; ++m)
+    for (int p = 0; p < 2; ++p) info->tuned[m][p] = tets->tuned[m][p];
   return EBB_OK;
 }
 

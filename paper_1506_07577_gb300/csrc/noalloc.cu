@@ -10,7 +10,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "ebb_internal.h"
 #include "tet_math.cuh"
@@ -89,23 +88,16 @@ Regions carve(unsigned char* base) {
   return g;
 }
 
-// Device address of the scratch array, looked up once per device.
-std::mutex g_mu;
-unsigned char* g_addr[64] = {};
-
+// Device address of the scratch array on the current device.  In host code
+// g_noalloc_scratch names a host-side stand-in, so the address the kernels
+// use is looked up on every call: the lookup allocates nothing, and a cached
+// address would go stale if the module were reloaded (after a
+// cudaDeviceReset, for instance).
 cudaError_t scratch_address(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 

@@ -58,7 +58,7 @@ def test_struct_layouts_match_c_compiler(abi, tmp_path):
     and struct size with the ctypes mirror."""
     structs = {"ebb_map_opts_t": abi.ebb_map_opts_t, "ebb_step_params_t": abi.ebb_step_params_t,
                "ebb_cg_report_t": abi.ebb_cg_report_t, "ebb_autotune_cand_t": abi.ebb_autotune_cand_t,
-               "ebb_autotune_report_t": abi.ebb_autotune_report_t}
+               "ebb_autotune_report_t": abi.ebb_autotune_report_t, "ebb_relation_info_t": abi.ebb_relation_info_t}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ebb.h"', "int main(void){"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')

@@ -86,5 +86,32 @@ def test_host_map_refusals_leave_fields_untouched():
         with pytest.raises(abi.EbbError) as ei:              # an FP32 field in an FP64 map
             abi.ebb_map_tet_force_Kv_host(du.ctx, du.tets, "u", "w", "f", "k32", uh, wh, fh, kh, o)
         assert ei.value.status == abi.EBB_ERR_ARG
+        # u and w name one device field but come from two host buffers: the
+        # second copy would overwrite the first
+        with pytest.raises(abi.EbbError) as ei:
+            abi.ebb_map_tet_force_Kv_host(du.ctx, du.tets, "u", "u", "f", "k", uh, wh, fh, kh, o)
+        assert ei.value.status == abi.EBB_ERR_PHASE
+        # the same for two names bound to one tensor
+        du.bind("u_alias", tu)
+        with pytest.raises(abi.EbbError) as ei:
+            abi.ebb_map_tet_force_Kv_host(du.ctx, du.tets, "u", "u_alias", "f", "k", uh, wh, fh, kh, o)
+        assert ei.value.status == abi.EBB_ERR_PHASE
         torch.cuda.synchronize()
         assert torch.equal(tu, before)                       # nothing was copied in
+
+
+def test_host_map_one_field_for_u_and_w():
+    """u and w may be one field filled from one host buffer: K(u) u."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, _ = problem(4, "stvk", seed=49)
+    f, Ku, _ = oracle_maps(m, mu, lam, u, u, "stvk")
+    with DeviceTetMesh(m.X, m.tets, mu, lam) as dm:
+        for name in ("u", "f", "k"):
+            dm.vertex_field(name, torch.float64)
+        uh = _host(u, "f64")
+        fh, kh = torch.zeros_like(uh).pin_memory(), torch.zeros_like(uh).pin_memory()
+        o = abi.map_opts(abi.EBB_STVK, precision=abi.EBB_PREC_F64, flags=abi.EBB_MAP_ZERO_OUT)
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "u", "f", "k", uh, uh, fh, kh, o)
+    assert rel_err(_vec(fh, "f64"), f) < 1e-12
+    assert rel_err(_vec(kh, "f64"), Ku) < 1e-12

@@ -82,3 +82,56 @@ def test_noalloc_rejects_sizes_beyond_its_array():
         abi.ebb_cg_implicit_step_noalloc(None, 4, 0, None, X[:, :4].contiguous(), X[:, :4].contiguous(),
                                          X[:, :4].contiguous(), None, prm32)
     assert ei.value.status == abi.EBB_ERR_ARG
+
+
+def _noalloc_problem(n=3, seed=5):
+    m = meshgen.cube_grid(n, jitter=0.01, seed=seed)
+    dev = torch.device("cuda", 0)
+    keys = torch.from_numpy(np.ascontiguousarray(m.tets.T)).to(dev)
+    X = torch.from_numpy(np.ascontiguousarray(m.X.T)).to(dev)
+    u = 0.001 * torch.from_numpy(np.ascontiguousarray(meshgen.random_field(m.n_verts, seed=seed).T)).to(dev)
+    v = 0.05 * torch.from_numpy(np.ascontiguousarray(meshgen.random_field(m.n_verts, seed=seed + 1).T)).to(dev)
+    return m, keys, X, u, v
+
+
+def test_noalloc_bad_keys_and_inverted_rest_leave_state_untouched():
+    """A key equal to n_verts, a key repeated inside one tet and an inverted
+    rest tet are found before anything is written: the call fails and u, v
+    keep their bits."""
+    from paper_1506_07577_gb300 import abi
+
+    m, keys, X, u, v = _noalloc_problem()
+    prm = abi.step_params(abi.EBB_STVK, 1e-3, 1000.0, 1e4, 1e4, G, abi.EBB_PREC_F64, max_iters=50, rtol=1e-12)
+    u0, v0 = u.clone(), v.clone()
+    cases = []
+    k = keys.clone()
+    k[2, 7] = m.n_verts                        # out of range
+    cases.append((k, abi.EBB_ERR_KEY))
+    k = keys.clone()
+    k[3, 4] = k[0, 4]                          # a vertex twice in one tet
+    cases.append((k, abi.EBB_ERR_KEY))
+    k = keys.clone()
+    k[[2, 3], 5] = k[[3, 2], 5]                # two corners swapped: det(Dm) < 0
+    cases.append((k, abi.EBB_ERR_INVERTED))
+    for kk, want in cases:
+        kk = kk.contiguous()
+        torch.cuda.synchronize()
+        with pytest.raises(abi.EbbError) as ei:
+            abi.ebb_cg_implicit_step_noalloc(None, m.n_verts, m.n_tets, kk, X, u, v, None, prm)
+        assert ei.value.status == want
+        assert torch.equal(u, u0) and torch.equal(v, v0)
+
+
+def test_noalloc_zero_iterations_moves_with_the_old_velocity():
+    """max_iters = 0: no CG iteration, dv = 0, so v stays and u += dt v."""
+    from paper_1506_07577_gb300 import abi
+
+    m, keys, X, u, v = _noalloc_problem()
+    dt = 1e-3
+    prm = abi.step_params(abi.EBB_STVK, dt, 1000.0, 1e4, 1e4, G, abi.EBB_PREC_F64, max_iters=0, rtol=1e-12)
+    u0, v0 = u.clone(), v.clone()
+    torch.cuda.synchronize()
+    rep = abi.ebb_cg_implicit_step_noalloc(None, m.n_verts, m.n_tets, keys, X, u, v, None, prm)
+    assert rep.iters == 0 and rep.status == abi.EBB_OK
+    assert torch.equal(v, v0)
+    assert torch.allclose(u, u0 + dt * v0, rtol=0, atol=1e-18)
