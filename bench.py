@@ -1,23 +1,33 @@
 #!/usr/bin/env python
-"""Benchmark: tet elements/s of the fused force + K*w map and the implicit
-step, on the 64^3 mixed-precision neo-Hookean cube-grid workload.
+"""Benchmark: tet elements/s of the fused force + K*w map (fraction of the HBM
+roofline) and implicit-step ms against the plain FP64 form.
 
-Workload (stands in for the paper's FEM meshes, which are not available):
-64 x 64 x 64 cubes, 5 tets per cube (274,625 vertices, 1,310,720 tets),
-rest positions jittered by 1% of the edge, E log-uniform in [1e4, 1e6] per tet,
-nu = 0.4, FP32 element math.  A timed step is one fused force + K*w map over
-every tet (the metric's kernel) with inputs resident in HBM; L2 (129 MB) is
-flushed by a 256 MB write before every timed step.  The implicit step (FP32
-element maps + FP64 CG, 10 steps, rtol 1e-8) is timed in the same run next to
-the plain FP64 form.
+Headline workload (stands in for the paper's large Vega meshes, Section 7.2,
+which are not available): 128 x 128 x 128 cubes, 5 tets per cube (2,146,689
+vertices, 10,485,760 tets), rest positions jittered by 1% of the edge, vertex
+and tet ids randomly permuted by seed (poor locality: the library reorders
+tets internally), St. Venant-Kirchhoff with E = 1e5, nu = 0.45, FP32 element
+math.  A timed step zeroes f and K*w and runs one fused force + K*w map over
+every tet with inputs resident in HBM; L2 (129 MB) is flushed by a 256 MB
+write before every timed step (the map's inputs, about 1 GB, exceed L2 too).
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the baseline for this path: there is no reference code to run).
+Sub-records: the same map per reduction variant and field layout, warm; the
+64^3 mixed-precision neo-Hookean workload (E log-uniform in [1e4, 1e6] per
+tet, nu = 0.4): fused map, the assembled K, the spring-mass example, the FP64
+K*w map, 10 implicit steps (mixed, assembled, ordered, FP64 form), the
+batched step over 256 meshes and the 32^3 StVK adjoint rollout.
+
+The CPU leg (`cpu_baseline`) times the FP64 oracle on the host and checks
+every timed GPU result against it at sampled vertices (or whole meshes where
+the oracle finishes in seconds).  --impl reference times the same oracle on
+a bounded sample of the headline workload (the baseline for this path: there
+is no reference code to run).  --profile runs one map or step a few times
+for a profiler, and nothing else.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
-torch.distributed.run, each rank runs an independent replica of the
-workload (the single-mesh path is not sharded), value = all ranks' tets / max
-rank time.
+torch.distributed.run each rank runs an independent replica of the workload
+(the single-mesh path is not sharded), value = all ranks' tets / max rank
+time.
 """
 from __future__ import annotations
 
@@ -43,20 +53,17 @@ import meshgen  # noqa: E402
 
 METRIC = "tet elements/s for force+K·v (% of HBM roofline); implicit-step ms vs FP64 form"
 UNIT = "tets/s"
-N_SIDE = 64
-SEED = 2
 L2_FLUSH_BYTES = 256 << 20
+G = (0.0, 0.0, -9.81)
 
-
-# DRAM bytes (read + write) per launch of the bench kernel (interleaved
-# fields) from one ncu capture on the 64^3 workload
-# (profiles/tet_tile_kernel_fused_nh64.md).  Valid
-# only while the kernel's sources are the ones captured; otherwise reported
-# as null.
-NCU_TRAFFIC = {"sources_sha256_16": "77a71dbb3d417ce1", "bytes_per_launch": 121.93e6}
+# DRAM bytes (read + write) per launch of the headline kernel from one ncu
+# capture of the headline workload (`--profile` with the same arguments as
+# the main line).  They describe the kernel sources whose hash is given and
+# are reported as null (with a note) once those sources change.
+NCU_TRAFFIC = {"sources_sha256_16": None, "bytes_per_launch": None}
 # FP64 arithmetic of the FP64 kernels, counted by ncu (2 x DFMA + DADD + DMUL
-# thread instructions per unit, sm__pipe_fp64_cycles_active) on the 64^3
-# workload, valid while the map and spring sources hash to the same value.
+# thread instructions per unit) on the 64^3 workload, valid while the map and
+# spring sources hash to the same value.
 NCU_FP64 = {"sources_sha256_16": "dc32b4c70d73aa62", "kv_map_nh_flops_per_tet": 454.8,
             "kv_map_nh_pipe_active": 0.882, "spring_flops_per_directed_spring": 32.15,
             "spring_pipe_active": 0.858}
@@ -66,6 +73,11 @@ FP64_PEAK_TFLOPS = 4 * 152 * 2070e6 / 1e12
 KERNEL_SOURCES = ["tet_maps.cu", "tile_map.cuh", "element.cuh", "tet_io.cuh", "tet_math.cuh", "tet_math_x2.cuh",
                   "async_copy.cuh", "ebb_internal.h", "layout.cu"]
 FP64_SOURCES = KERNEL_SOURCES + ["springs.cu"]
+# Algorithmic bytes per free vertex and CG iteration of the mixed step's
+# vector work (FP64 vectors, 24 B per vertex): p, A p's K p (FP32, 12 B),
+# mass (8 B), 1/diag, r and y read; y, r and p written, and p's FP32 copy
+# (12 B) for the next K p map.
+CG_BYTES_PER_VERTEX = 24 + 12 + 8 + 24 + 24 + 24 + 24 + 24 + 24 + 12
 
 
 def kernel_sources_hash(files=None):
@@ -85,21 +97,33 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def workload():
-    m = meshgen.cube_grid(N_SIDE, jitter=0.01, seed=SEED)
-    mu, lam = meshgen.material_loguniform_E(m.n_tets, 1e4, 1e6, 0.4, SEED)
-    u = meshgen.random_displacement(m.X, N_SIDE, amp=0.05, seed=SEED, smooth=0.01)
-    w = meshgen.random_field(m.n_verts, seed=SEED)
+# ---- workloads --------------------------------------------------------------
+
+def workload_permuted(n=128):
+    """n^3 cube grid, ids permuted (seed 5), StVK E = 1e5, nu = 0.45 (uniform)."""
+    m = meshgen.cube_grid(n, jitter=0.01, seed=5, permute=True)
+    mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+    u = meshgen.random_displacement(m.X, n, amp=0.05, seed=5, smooth=0.01)
+    w = meshgen.random_field(m.n_verts, seed=5)
     return m, mu, lam, u, w
 
 
-def algorithmic_bytes_per_tet(n_verts, n_tets):
-    """Bytes the fused FP32 map must move once per tet: keys (4 x int32),
-    Dm^-1 (9 x f32), V (f32), per-tet (mu, lambda) (2 x f32), plus per vertex
-    u and w read and f and K*w written (4 x 3 x f32) amortised over tets."""
-    per_tet = 16 + 36 + 4 + 8
-    per_vertex = 4 * 12
-    return per_tet + per_vertex * n_verts / n_tets
+def workload_nh64(n=64):
+    """n^3 cube grid (seed 2), NH, E log-uniform [1e4, 1e6] per tet, nu = 0.4."""
+    m = meshgen.cube_grid(n, jitter=0.01, seed=2)
+    mu, lam = meshgen.material_loguniform_E(m.n_tets, 1e4, 1e6, 0.4, 2)
+    u = meshgen.random_displacement(m.X, n, amp=0.05, seed=2, smooth=0.01)
+    w = meshgen.random_field(m.n_verts, seed=2)
+    return m, mu, lam, u, w
+
+
+def algorithmic_bytes_per_tet(n_verts, n_tets, per_tet_material, fields=4):
+    """Bytes an FP32 map must move once per tet: keys (4 x int32), Dm^-1
+    (9 x f32), V (f32), per-tet (mu, lambda) (2 x f32) where bound, plus
+    per vertex `fields` 3-vectors of f32 (u and w read, f and K*w written
+    for the fused map) amortised over tets."""
+    per_tet = 16 + 36 + 4 + (8 if per_tet_material else 0)
+    return per_tet + fields * 12 * n_verts / n_tets
 
 
 class ClockSampler:
@@ -147,45 +171,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds, m, mu, lam, u, w, f_gpu, kw_gpu):
-    """The CPU leg: the FP64 oracle's force + K*w on a contiguous sample of
-    the same mesh's tets, timed on this host's cores (single thread); the
-    same oracle then recomputes 32 sampled vertices exactly (from their
-    incident tets only) and reports the GPU results' max-norm error there."""
-    from oracle import fem
-    sample = min(m.n_tets, 131072)
-    tets = m.tets[:sample]
-    B, V = fem.rest_shape(m.X, tets)
-    mu_s, lam_s = mu[:sample], lam[:sample]
-    x = m.X + u
-    done = 0
-    t0 = time.perf_counter()
-    while True:
-        fem.tet_forces(x, tets, B, V, mu_s, lam_s, fem.NEOHOOKEAN)
-        fem.tet_Kv(x, w, tets, B, V, mu_s, lam_s, fem.NEOHOOKEAN)
-        done += sample
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    rng = np.random.default_rng(0)
-    vs = rng.choice(m.n_verts, size=32, replace=False)
-    sel = np.isin(m.tets, vs).any(axis=1)
-    sub = m.tets[sel]
-    Bs, Vs = fem.rest_shape(m.X, sub)
-    fo = fem.tet_forces(x, sub, Bs, Vs, mu[sel], lam[sel], fem.NEOHOOKEAN)[vs]
-    ko = fem.tet_Kv(x, w, sub, Bs, Vs, mu[sel], lam[sel], fem.NEOHOOKEAN)[vs]
-    err = max(float(np.max(np.abs(f_gpu[vs] - fo)) / np.max(np.abs(fo))),
-              float(np.max(np.abs(kw_gpu[vs] - ko)) / np.max(np.abs(ko))))
-    return {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle force+K*w over the first {sample} tets of the 64^3 mesh, "
-                      f"repeated for {el:.1f} s ({done} tet evaluations), numpy single thread",
-            "gpu_parity_max_rel_err_sampled": err}
-
-
-def kern_avg_us(kern_ms):
-    return 1e3 * sum(kern_ms) / len(kern_ms)
-
-
 def max_over_ranks(seconds, dist, device):
     """The timing contract across replicas: the slowest rank's time (an
     all-reduce MAX when `dist` is torch.distributed, the value itself when
@@ -204,82 +189,76 @@ def replica_throughput(units_per_rank, seconds_max, world):
     return units_per_rank * world / seconds_max
 
 
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    m, mu, lam, u, w = workload()
-    from oracle import fem
-    sample = 65536
-    tets = m.tets[:sample]
-    B, V = fem.rest_shape(m.X, tets)
-    x = m.X + u
-    for _ in range(args.warmup):
-        fem.tet_forces(x, tets, B, V, mu[:sample], lam[:sample], fem.NEOHOOKEAN)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        fem.tet_forces(x, tets, B, V, mu[:sample], lam[:sample], fem.NEOHOOKEAN)
-        fem.tet_Kv(x, w, tets, B, V, mu[:sample], lam[:sample], fem.NEOHOOKEAN)
-    el = time.perf_counter() - t0
-    value = sample * args.steps / el
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "64^3 cube grid, 5 tets/cube, NH, E log-uniform [1e4,1e6], nu 0.4",
-                       "n_tets": m.n_tets, "n_verts": m.n_verts, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: FP64 oracle force+K*w over the first {sample} tets"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather", 5: "tiled_ordered"}
 
 
-def run_ours(args, rank, world, local_rank):
-    import torch
+def tune_report(abi, rep):
+    return {"reduce": REDUCE_NAMES[rep.reduce], "tile_tets": rep.tile_tets, "interleaved": bool(rep.interleaved),
+            "candidates_kw_map_us": [{"reduce": REDUCE_NAMES[rep.cand[i].reduce], "tile_tets": rep.cand[i].tile_tets,
+                                      "interleaved": bool(rep.cand[i].interleaved), "us": rep.cand[i].us}
+                                     for i in range(rep.ncand)]}
 
-    from paper_1506_07577_gb300 import abi
+
+def map_launches(reduce_name, info, staged):
+    """Library kernels one map call launches: the map itself (one launch per
+    colour for the coloured variant, two passes for gather and ordered),
+    plus the copy-in and add-back of staged operands."""
+    n = {"tiled": 1, "atomic": 1, "gather": 2, "tiled_ordered": 2, "colour": max(int(info.ncolours), 1)}[reduce_name]
+    return n + (2 if staged else 0)
+
+
+def time_calls(torch, stream, call, zero, flush, n, warm=3, flush_l2=True):
+    """Median CUDA-event time (us) of `call` over n launches after `warm`
+    untimed ones; `zero` (may be None) runs untimed before each; L2 flushed
+    before each launch unless flush_l2 is false (warm-cache figure)."""
+    ts = []
+    with torch.cuda.stream(stream):
+        for k in range(warm + n):
+            if flush_l2:
+                flush.fill_(float(k))
+            if zero is not None:
+                zero()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            b.record(stream)
+            b.synchronize()
+            if k >= warm:
+                ts.append(a.elapsed_time(b) * 1e3)
+    return statistics.median(ts)
+
+
+# ---- the headline: 128^3 permuted StVK, fused force + K*w -------------------
+
+def run_headline(args, abi, torch, dev, local_rank, stream, flush, dist, world, barrier):
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    m, mu, lam, u, w = workload()
-    stream = torch.cuda.Stream(device=dev)
-    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream, colour=True, edges=True)
-    # Vector fields stored element by element (EBB_F32X4: x, y, z, padding), the
-    # per-field contiguous vec3 storage of Section 6.1 padded to 16 bytes; the
-    # same map on 3-plane fields is reported under "layouts".
-    u32 = dm.vertex_field("u32", value=u, x4=True)
-    w32 = dm.vertex_field("w32", value=w, x4=True)
+    m, mu, lam, u, w = workload_permuted(args.n)
+    nt, nv = m.n_tets, m.n_verts
+    t0 = time.perf_counter()
+    dm = DeviceTetMesh(m.X, m.tets, device=local_rank, stream=stream, colour=True)
+    setup_s = time.perf_counter() - t0
+    # Vector fields stored element by element (EBB_F32X4: x, y, z, padding),
+    # the per-field contiguous vec3 storage of Section 6.1 padded to 16 bytes;
+    # the same map on 3-plane fields is a sub-record.
+    dm.vertex_field("u", value=u, x4=True)
+    dm.vertex_field("w", value=w, x4=True)
     f = dm.vertex_field("f", x4=True)
-    Kw = dm.vertex_field("Kw", x4=True)
-    dm.vertex_field("u32p", torch.float32, value=u)
-    dm.vertex_field("w32p", torch.float32, value=w)
-    dm.vertex_field("fp", torch.float32)
-    dm.vertex_field("Kwp", torch.float32)
-    opts = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
+    k = dm.vertex_field("k", x4=True)
+    opts_t = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32)
     # The autotuner picks the tile size and reduction variant EBB_REDUCE_AUTO
     # resolves to (timing the K w map on these fields); untimed set-up.
-    tune = tune_report(abi, abi.ebb_relation_autotune(dm.ctx, dm.tets, "u32", "w32",
-                                                      abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32)))
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    nt = m.n_tets
+    tune = tune_report(abi, abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", opts_t))
+    info = abi.ebb_relation_info(dm.ctx, dm.tets)
+    opts = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
 
     def step(ev=None):
         if ev is not None:
             ev[0].record(stream)
         f.zero_()
-        Kw.zero_()
+        k.zero_()
         if ev is not None:
             ev[1].record(stream)
-        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", opts)
+        abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", opts)
         if ev is not None:
             ev[2].record(stream)
 
@@ -294,9 +273,9 @@ def run_ours(args, rank, world, local_rank):
         clocks = ClockSampler(local_rank)
         clocks.start()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            step(evs[k])
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            step(evs[s])
         torch.cuda.synchronize()
         barrier()
         clk = clocks.stop()
@@ -304,173 +283,179 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [e[0].elapsed_time(e[2]) for e in evs]
     kern_ms = [e[1].elapsed_time(e[2]) for e in evs]
     total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
-    value = replica_throughput(nt * args.steps, total_s, world)
+    out = {"value": replica_throughput(nt * args.steps, total_s, world), "total_s": total_s,
+           "kern_us": 1e3 * sum(kern_ms) / len(kern_ms), "clocks": clk, "tune": tune, "setup_s": setup_s,
+           "n_tets": nt, "n_verts": nv, "ntiles": int(info.ntiles), "ncolours": int(info.ncolours),
+           "launches_per_step": map_launches(tune["reduce"], info, False)}
+    out["gpu_f"] = f[:, :3].double().cpu().numpy()
+    out["gpu_k"] = k[:, :3].double().cpu().numpy()
 
-    # ---- end to end: one C-ABI call on pinned host buffers (copy u, w in,
-    # zero f, K w, map, copy f, K w out, wait) -------------------------------
-    uh = u32.cpu().pin_memory()
-    wh = w32.cpu().pin_memory()
+    # ---- end to end: one C-ABI call on page-locked host buffers (copy u, w
+    # in, zero f, K w, map, copy f, K w out, wait) ---------------------------
+    uh = dm._tensors["u"].cpu().pin_memory()
+    wh = dm._tensors["w"].cpu().pin_memory()
     fh = torch.empty_like(f, device="cpu").pin_memory()
-    kh = torch.empty_like(Kw, device="cpu").pin_memory()
-    opts_e2e = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO,
+    kh = torch.empty_like(k, device="cpu").pin_memory()
+    opts_e2e = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO,
                             flags=abi.EBB_MAP_ZERO_OUT)
+    e2e_ms = []
     with torch.cuda.stream(stream):
-        e2e_ms = []
-        for k in range(args.warmup + args.steps):
-            flush.fill_(float(k))
+        for s in range(args.warmup + args.steps):
+            flush.fill_(float(s))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", uh, wh, fh, kh, opts_e2e)
+            abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, opts_e2e)
             e1.record(stream)
             e1.synchronize()
-            if k >= args.warmup:
+            if s >= args.warmup:
                 e2e_ms.append(e0.elapsed_time(e1))
     e2e_total = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
-    h2d = (uh.numel() + wh.numel()) * 4
-    d2h = (fh.numel() + kh.numel()) * 4
+    out["e2e"] = {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
+                  "h2d_bytes_per_step": (uh.numel() + wh.numel()) * 4,
+                  "d2h_bytes_per_step": (fh.numel() + kh.numel()) * 4,
+                  "ms_per_call": 1e3 * e2e_total / args.steps,
+                  "call": "ebb_map_tet_force_Kv_host on page-locked host buffers (EBB_MAP_ZERO_OUT)"}
 
-    f_last = fh[:, :3].double().numpy().copy()
-    kw_last = kh[:, :3].double().numpy().copy()
-
-    # ---- reduction variants of the fused map (kernel time only) ----------
+    # ---- every reduction variant and field layout (kernel time), warm ------
+    peak = _peaks()[0]
+    bpt = algorithmic_bytes_per_tet(nv, nt, False)
     variants = {}
-    for name, red in (("atomic", abi.EBB_REDUCE_ATOMIC), ("colour", abi.EBB_REDUCE_COLOR),
-                      ("gather", abi.EBB_REDUCE_GATHER), ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED),
-                      ("tiled", abi.EBB_REDUCE_TILED)):
-        o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=red)
-        ts = []
-        with torch.cuda.stream(stream):
-            for k in range(args.warmup + 5):
-                flush.fill_(float(k))
-                f.zero_()
-                Kw.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", o)
-                b.record(stream)
-                b.synchronize()
-                if k >= args.warmup:
-                    ts.append(a.elapsed_time(b) * 1e3)
-        variants[name] = {"us": statistics.median(ts), "tets_per_s": nt / (statistics.median(ts) * 1e-6)}
 
-    # ---- field layouts: the same tiled map on 3-plane fields --------------
-    layouts = {"f32x4": {"us": kern_avg_us(kern_ms)}}
-    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
-    ts = []
-    with torch.cuda.stream(stream):
-        for k in range(args.warmup + 5):
-            flush.fill_(float(k))
-            dm._tensors["fp"].zero_()
-            dm._tensors["Kwp"].zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32p", "w32p", "fp", "Kwp", o)
-            b.record(stream)
-            b.synchronize()
-            if k >= args.warmup:
-                ts.append(a.elapsed_time(b) * 1e3)
-    layouts["planes"] = {"us": statistics.median(ts)}
-    for v in layouts.values():
-        v["tets_per_s"] = nt / (v["us"] * 1e-6)
+    def zero_xk():
+        f.zero_()
+        k.zero_()
 
-    # ---- assembled K on the edge relation vs the matrix-free K w map ------
-    asm = assembled_compare(dm, abi, torch, stream, args, flush)
-    spr = springs_leg(dm, m, abi, torch, stream)
-    f64map = fp64_map_leg(dm, u, w, abi, torch, stream, flush)
+    for name, red in (("tiled", abi.EBB_REDUCE_TILED), ("atomic", abi.EBB_REDUCE_ATOMIC),
+                      ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED), ("gather", abi.EBB_REDUCE_GATHER),
+                      ("colour", abi.EBB_REDUCE_COLOR)):
+        o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
+        us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o),
+                        zero_xk, flush, 5)
+        variants[name] = {"us": us, "tets_per_s": nt / (us * 1e-6),
+                          "algorithmic_GBps": bpt * nt / (us * 1e-6) / 1e9,
+                          "frac_of_peak": bpt * nt / (us * 1e-6) / 1e9 / peak}
+    o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
+    warm_us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o),
+                         zero_xk, flush, 5, flush_l2=False)
+    variants["autotuned_warm_l2"] = {"us": warm_us, "tets_per_s": nt / (warm_us * 1e-6),
+                                     "note": "no L2 flush between launches (the map's ~1 GB of inputs exceed L2)"}
+    dm.vertex_field("up", torch.float32, value=u)
+    dm.vertex_field("wp", torch.float32, value=w)
+    fp = dm.vertex_field("fp", torch.float32)
+    kp = dm.vertex_field("kp", torch.float32)
 
-    # ---- implicit step: mixed form vs plain FP64 form -------------------
-    imp = implicit_steps(dm, m, abi, torch, stream, args)
-    bat = batched_steps(abi, torch, local_rank, args) if args.batch_meshes > 0 else None
-    adj = adjoint_rollout(abi, torch, local_rank, args) if not args.no_adjoint else None
-    perm = permuted_sweep(abi, torch, local_rank, args, _peaks()[0]) if args.permuted_n > 0 else None
+    def zero_p():
+        fp.zero_()
+        kp.zero_()
 
-    # ---- roofline of the dominant kernel ----------------------------------
-    peak, peak_kind = _peaks()
-    bpt = algorithmic_bytes_per_tet(m.n_verts, nt)
-    kern_avg = sum(kern_ms) / len(kern_ms) / 1e3
-    achieved = bpt * nt / kern_avg / 1e9
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if kernel_sources_hash() == NCU_TRAFFIC["sources_sha256_16"] else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read+write)",
-            "kernel": {"tiled": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved>",
-                       "atomic": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, atomic, interleaved>",
-                       "colour": "tet_map_kernel<float, NEOHOOKEAN, FORCE|KV, coloured, interleaved>",
-                       "gather": "tet_corner_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved> + "
-                                 "vertex_sum_kernel<float, 2, interleaved>",
-                       "tiled_ordered": "tet_tile_kernel<float, NEOHOOKEAN, FORCE|KV, interleaved> + "
-                                        "partial_sum_kernel<float, 2, interleaved>"}[tune["reduce"]],
-            "algorithmic_bytes_per_tet": bpt, "kernel_us": kern_avg * 1e6, "peak_kind": peak_kind}
-
+    o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
+    us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "up", "wp", "fp", "kp", o),
+                    zero_p, flush, 5)
+    variants["tiled_planes"] = {"us": us, "tets_per_s": nt / (us * 1e-6)}
     dm.close()
-    if rank != 0:
-        return
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64^3 cube grid, 5 tets/cube (274,625 verts, 1,310,720 tets), NH, "
-                                   "E log-uniform [1e4,1e6], nu 0.4, FP32 fused force+K*w map, reduction variant "
-                                   "and tile size from the autotuner, vector fields stored as 4-float elements",
-                       "n_tets": nt, "n_verts": m.n_verts, "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof,
-            "autotune": tune,
-            "reduction_variants": variants,
-            "layouts": layouts,
-            "assembled_K": asm,
-            "spring_mass": spr,
-            "fp64_kv_map": f64map,
-            "e2e": {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h,
-                    "call": "ebb_map_tet_force_Kv_host on page-locked host buffers (EBB_MAP_ZERO_OUT)"},
-            # library kernels per timed step: the map's launches for the
-            # autotuned variant (the zeroing of f, K w is torch's fill)
-            "gpu_launches": args.steps * {"tiled": 1, "atomic": 1, "gather": 2, "tiled_ordered": 2}.get(
-                tune["reduce"], 1),
-            "clocks": clk,
-            "implicit_step": imp,
-            "batched_step": bat,
-            "adjoint_rollout": adj,
-            "permuted_128": perm}
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, m, mu, lam, u, w, f_last, kw_last)
-    print(json.dumps(line), flush=True)
+    # vertex renumbering: the same map on a relation with internal Morton
+    # vertex order (u, w permuted in and f, K w added back inside the call)
+    t0 = time.perf_counter()
+    dmr = DeviceTetMesh(m.X, m.tets, device=local_rank, stream=stream, reorder_verts=True)
+    out["setup_vertex_reorder_s"] = time.perf_counter() - t0
+    dmr.vertex_field("u", value=u, x4=True)
+    dmr.vertex_field("w", value=w, x4=True)
+    fr = dmr.vertex_field("f", x4=True)
+    kr = dmr.vertex_field("k", x4=True)
+
+    def zero_r():
+        fr.zero_()
+        kr.zero_()
+
+    o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
+    us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dmr.ctx, dmr.tets, "u", "w", "f", "k", o),
+                    zero_r, flush, 5)
+    variants["tiled_vertex_reordered"] = {"us": us, "tets_per_s": nt / (us * 1e-6),
+                                          "note": "includes permuting u, w in and adding f, K*w back"}
+    dmr.close()
+    out["variants"] = variants
+    out["workload"] = (m, mu, lam, u, w)
+    return out
 
 
-def assembled_compare(dm, abi, torch, stream, args, flush):
+# ---- 64^3 mixed neo-Hookean sub-records -------------------------------------
+
+def run_nh64(args, abi, torch, local_rank, stream, flush):
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = workload_nh64()
+    nt = m.n_tets
+    dm = DeviceTetMesh(m.X, m.tets, mu, lam, device=local_rank, stream=stream, colour=True, edges=True)
+    dm.vertex_field("u32", value=u, x4=True)
+    dm.vertex_field("w32", value=w, x4=True)
+    f = dm.vertex_field("f", x4=True)
+    Kw = dm.vertex_field("Kw", x4=True)
+    tune = tune_report(abi, abi.ebb_relation_autotune(dm.ctx, dm.tets, "u32", "w32",
+                                                      abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32)))
+    peak = _peaks()[0]
+    bpt = algorithmic_bytes_per_tet(m.n_verts, nt, True)
+
+    def zero():
+        f.zero_()
+        Kw.zero_()
+
+    variants = {}
+    for name, red in (("autotuned", abi.EBB_REDUCE_AUTO), ("tiled", abi.EBB_REDUCE_TILED),
+                      ("atomic", abi.EBB_REDUCE_ATOMIC), ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED),
+                      ("gather", abi.EBB_REDUCE_GATHER), ("colour", abi.EBB_REDUCE_COLOR)):
+        o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=red)
+        us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", o),
+                        zero, flush, 5)
+        variants[name] = {"us": us, "tets_per_s": nt / (us * 1e-6), "frac_of_peak": bpt * nt / (us * 1e-6) / 1e9 / peak}
+    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO)
+    us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", o),
+                    zero, flush, 5, flush_l2=False)
+    variants["autotuned_warm_l2"] = {"us": us, "tets_per_s": nt / (us * 1e-6),
+                                     "frac_of_peak": bpt * nt / (us * 1e-6) / 1e9 / peak,
+                                     "note": "no L2 flush: the map's 97 MB of algorithmic data fit in L2"}
+    # the GPU result the CPU leg checks at sampled vertices
+    abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw",
+                             abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO,
+                                          flags=abi.EBB_MAP_ZERO_OUT))
+    abi.ebb_ctx_sync(dm.ctx)
+    gpu_map = (f[:, :3].double().cpu().numpy(), Kw[:, :3].double().cpu().numpy())
+    dm.vertex_field("u32p", torch.float32, value=u)
+    dm.vertex_field("w32p", torch.float32, value=w)
+    fp = dm.vertex_field("fp", torch.float32)
+    kp = dm.vertex_field("Kwp", torch.float32)
+    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
+    us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32p", "w32p", "fp", "Kwp", o),
+                    lambda: (fp.zero_(), kp.zero_()), flush, 5)
+    variants["tiled_planes"] = {"us": us, "tets_per_s": nt / (us * 1e-6)}
+    out = {"workload": "64^3 cube grid (274,625 verts, 1,310,720 tets), NH, E log-uniform [1e4,1e6] per tet, "
+                       "nu 0.4, FP32 fused force+K*w map on 4-float vector elements, L2 flushed",
+           "algorithmic_bytes_per_tet": bpt, "autotune": tune, "fused_map": variants}
+    out["assembled_K"] = assembled_compare(dm, abi, torch, stream, flush)
+    out["spring_mass"] = springs_leg(dm, m, abi, torch, stream)
+    out["fp64_kv_map"] = fp64_map_leg(dm, u, w, abi, torch, stream, flush)
+    imp, states = implicit_steps(dm, m, abi, torch, stream, args)
+    out["implicit_step"] = imp
+    dm.close()
+    return out, {"mesh": (m, mu, lam, u, w), "map": gpu_map, "steps": states}
+
+
+def assembled_compare(dm, abi, torch, stream, flush):
     """K(u) assembled on the edge relation (FP32 blocks) and its block-sparse
-    product with w, against the matrix-free K w map (tiled), on the bench's
-    4-float fields; L2 flushed before every timed launch."""
+    product with w, against the matrix-free K w map (tiled), on 4-float
+    fields; L2 flushed before every timed launch."""
     o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32)
     o_kv = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
     Kw = dm._tensors["Kw"]
     calls = {"assemble": lambda: abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u32", o),
              "spmv": lambda: abi.ebb_spmv_tet_K(dm.ctx, dm.tets, "w32", "Kw", o),
              "kv_map_tiled": lambda: abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u32", "w32", "Kw", o_kv)}
-    res = {}
-    with torch.cuda.stream(stream):
-        for name, call in calls.items():
-            ts = []
-            for k in range(args.warmup + 5):
-                flush.fill_(float(k))
-                Kw.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                call()
-                b.record(stream)
-                b.synchronize()
-                if k >= args.warmup:
-                    ts.append(a.elapsed_time(b) * 1e3)
-            res[name + "_us"] = statistics.median(ts)
-    return res
+    return {name + "_us": time_calls(torch, stream, call, Kw.zero_, flush, 5) for name, call in calls.items()}
 
 
 def springs_leg(dm, m, abi, torch, stream, steps=200):
     """The paper's spring-mass example (Section 4.1, Figure 1) on the 64^3
     mesh's edges: `steps` explicit steps per timed call, K = 1, dt = 1e-4,
     equal masses of density 1000 over the unit cube, from a perturbed rest
-    state; FP32 (the figure's floats) and FP64.  Per-step time with CUDA
-    events after warm-up."""
+    state; FP32 (the figure's floats) and FP64."""
     rng = np.random.default_rng(7)
     q0 = m.X + 0.002 * rng.normal(size=m.X.shape)
     mass = np.full(m.n_verts, 1000.0 / m.n_verts)
@@ -491,52 +476,16 @@ def springs_leg(dm, m, abi, torch, stream, steps=200):
             b.synchronize()
             energy = abi.ebb_springs_run(dm.ctx, dm.tets, "sq_" + name, "sqd_" + name, "sm_" + name, 1.0, 1e-4, 0,
                                          energy=True)
-        us = a.elapsed_time(b) * 1e3 / steps
-        out[name + "_us_per_step"] = us
+        out[name + "_us_per_step"] = a.elapsed_time(b) * 1e3 / steps
         out[name + "_kinetic_energy_after"] = energy
     nsprings = int(springs_directed_count(m))
     out["directed_springs"] = nsprings
     out["f32_springs_per_s"] = nsprings / (out["f32_us_per_step"] * 1e-6)
     if kernel_sources_hash(FP64_SOURCES) == NCU_FP64["sources_sha256_16"]:
-        # FP64 steps are bound by the FP64 pipe: flops counted by ncu
         fl = NCU_FP64["spring_flops_per_directed_spring"] * nsprings
         out["f64_achieved_tflops"] = fl / (out["f64_us_per_step"] * 1e-6) / 1e12
         out["f64_frac_of_fp64_peak"] = out["f64_achieved_tflops"] / FP64_PEAK_TFLOPS
         out["f64_pipe_active_ncu"] = NCU_FP64["spring_pipe_active"]
-    return out
-
-
-def fp64_map_leg(dm, u, w, abi, torch, stream, flush):
-    """The FP64 K w map (neo-Hookean, tiled, 3-plane FP64 fields) that the
-    FP64 form of the implicit step runs once per CG iteration: CUDA-event
-    median of 5 launches after 3 untimed ones, L2 flushed before each,
-    against GB300's FP64 arithmetic peak (the kernel is bound by the FP64
-    pipe, not by HBM)."""
-    nt = dm.n_tets
-    dm.vertex_field("u64", torch.float64, value=u)
-    dm.vertex_field("w64", torch.float64, value=w)
-    kk = dm.vertex_field("k64", torch.float64)
-    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64, reduce=abi.EBB_REDUCE_TILED)
-    ts = []
-    with torch.cuda.stream(stream):
-        for it in range(3 + 5):
-            flush.fill_(float(it))
-            kk.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u64", "w64", "k64", o)
-            b.record(stream)
-            b.synchronize()
-            if it >= 3:
-                ts.append(a.elapsed_time(b) * 1e3)
-    us = statistics.median(ts)
-    out = {"kernel": "tet_tile_kernel<double, NEOHOOKEAN, KV>", "us": us, "tets_per_s": nt / (us * 1e-6),
-           "bound": "alu", "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2070 MHz"}
-    if kernel_sources_hash(FP64_SOURCES) == NCU_FP64["sources_sha256_16"]:
-        fl = NCU_FP64["kv_map_nh_flops_per_tet"]
-        out.update({"fp64_flops_per_tet": fl, "achieved_tflops": fl * nt / (us * 1e-6) / 1e12,
-                    "fp64_pipe_active_ncu": NCU_FP64["kv_map_nh_pipe_active"]})
-        out["frac"] = out["achieved_tflops"] / FP64_PEAK_TFLOPS
     return out
 
 
@@ -548,17 +497,39 @@ def springs_directed_count(m):
     return np.unique(np.concatenate(keys)).size
 
 
+def fp64_map_leg(dm, u, w, abi, torch, stream, flush):
+    """The FP64 K w map (neo-Hookean, tiled, 3-plane FP64 fields) that the
+    FP64 form of the implicit step runs once per CG iteration, against
+    GB300's FP64 arithmetic peak (the kernel is bound by the FP64 pipe)."""
+    nt = dm.n_tets
+    dm.vertex_field("u64", torch.float64, value=u)
+    dm.vertex_field("w64", torch.float64, value=w)
+    kk = dm.vertex_field("k64", torch.float64)
+    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64, reduce=abi.EBB_REDUCE_TILED)
+    us = time_calls(torch, stream, lambda: abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u64", "w64", "k64", o), kk.zero_,
+                    flush, 5)
+    out = {"kernel": "tet_tile_kernel<double, NEOHOOKEAN, KV>", "us": us, "tets_per_s": nt / (us * 1e-6),
+           "bound": "alu", "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2070 MHz"}
+    if kernel_sources_hash(FP64_SOURCES) == NCU_FP64["sources_sha256_16"]:
+        fl = NCU_FP64["kv_map_nh_flops_per_tet"]
+        out.update({"fp64_flops_per_tet": fl, "achieved_tflops": fl * nt / (us * 1e-6) / 1e12,
+                    "fp64_pipe_active_ncu": NCU_FP64["kv_map_nh_pipe_active"]})
+        out["frac"] = out["achieved_tflops"] / FP64_PEAK_TFLOPS
+    return out
+
+
 def implicit_steps(dm, m, abi, torch, stream, args):
     """10 implicit steps from rest under gravity: the mixed form, the same with
     K assembled once per step (block-sparse CG products), the same with the
     ordered tiled reduction (the whole step bitwise reproducible), and the
     FP64 form.  One untimed step first (graph capture), then the state is
-    reset."""
+    reset.  Each form keeps the state before its last step for the CPU
+    leg's check against the oracle's linear system."""
     uu = dm.vertex_field("u_state", torch.float64)
     vv = dm.vertex_field("v_state", torch.float64)
     dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(uu.device))
-    out = {}
-    res = {}
+    res, out, states = {}, {}, {}
+    nsteps = args.implicit_steps
     for name, prec, flags, red in (("mixed", abi.EBB_PREC_F32, 0, abi.EBB_REDUCE_AUTO),
                                    ("mixed_assembled", abi.EBB_PREC_F32, abi.EBB_STEP_ASSEMBLED, abi.EBB_REDUCE_AUTO),
                                    ("mixed_ordered", abi.EBB_PREC_F32, 0, abi.EBB_REDUCE_TILED_ORDERED),
@@ -573,39 +544,50 @@ def implicit_steps(dm, m, abi, torch, stream, args):
         vv.zero_()
         times, iters = [], []
         with torch.cuda.stream(stream):
-            for s in range(args.implicit_steps):
+            for s in range(nsteps):
+                if s == nsteps - 1:
+                    before = (uu.cpu().numpy().T.copy(), vv.cpu().numpy().T.copy())
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 rep = abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u_state", "v_state", "pinned", prm)
                 times.append(time.perf_counter() - t0)
                 iters.append(rep.iters)
         res[name] = (uu.clone(), vv.clone())
+        states[name] = before + (vv.cpu().numpy().T.copy(),)
         out[name] = {"ms_per_step": 1e3 * sum(times) / len(times), "cg_iters": iters}
     vmax = res["fp64"][1].abs().max().item()
-    du = (res["mixed"][1] - res["fp64"][1]).abs().max().item() / vmax
-    da = (res["mixed_assembled"][1] - res["fp64"][1]).abs().max().item() / vmax
-    return {"steps": args.implicit_steps, "dt": 1e-3, "rtol": 1e-8,
-            "mixed_ms_per_step": out["mixed"]["ms_per_step"], "fp64_ms_per_step": out["fp64"]["ms_per_step"],
-            "speedup_vs_fp64_form": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
-            "cg_iters_mixed": out["mixed"]["cg_iters"], "cg_iters_fp64": out["fp64"]["cg_iters"],
-            "v_rel_diff_mixed_vs_fp64_form": du,
-            "mixed_assembled_ms_per_step": out["mixed_assembled"]["ms_per_step"],
-            "cg_iters_mixed_assembled": out["mixed_assembled"]["cg_iters"],
-            "v_rel_diff_mixed_assembled_vs_fp64_form": da,
-            "mixed_ordered_ms_per_step": out["mixed_ordered"]["ms_per_step"],
-            "cg_iters_mixed_ordered": out["mixed_ordered"]["cg_iters"],
-            "v_rel_diff_mixed_ordered_vs_fp64_form":
-                (res["mixed_ordered"][1] - res["fp64"][1]).abs().max().item() / vmax}
-
-
-REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather", 5: "tiled_ordered"}
-
-
-def tune_report(abi, rep):
-    return {"reduce": REDUCE_NAMES[rep.reduce], "tile_tets": rep.tile_tets, "interleaved": bool(rep.interleaved),
-            "candidates_kw_map_us": [{"reduce": REDUCE_NAMES[rep.cand[i].reduce], "tile_tets": rep.cand[i].tile_tets,
-                                      "interleaved": bool(rep.cand[i].interleaved), "us": rep.cand[i].us}
-                                     for i in range(rep.ncand)]}
+    peak = _peaks()[0]
+    nt, nv = m.n_tets, m.n_verts
+    free = int((~m.pinned).sum())
+    # bytes moved per step by the mixed form: per CG iteration the K p map
+    # (64 B per tet of keys, Dm^-1, V, mu, lambda and 3 x 12 B per vertex of
+    # u, p read and K p written) and the CG vector work; once per step the
+    # fused force + K v + diag map (60 B per vertex) and the set-up vectors.
+    kp_map = 64 * nt + 36 * nv
+    cg_vec = CG_BYTES_PER_VERTEX * free
+    once = 64 * nt + 60 * nv + 8 * 24 * nv
+    step_bytes = [it * (kp_map + cg_vec) + once for it in out["mixed"]["cg_iters"]]
+    ms = out["mixed"]["ms_per_step"]
+    gbs = statistics.mean(step_bytes) / (ms * 1e-3) / 1e9
+    r = {"steps": nsteps, "dt": 1e-3, "rtol": 1e-8,
+         "mixed_ms_per_step": ms, "fp64_ms_per_step": out["fp64"]["ms_per_step"],
+         "speedup_vs_fp64_form": out["fp64"]["ms_per_step"] / ms,
+         "cg_iters_mixed": out["mixed"]["cg_iters"], "cg_iters_fp64": out["fp64"]["cg_iters"],
+         "mixed_us_per_cg_iteration": 1e3 * ms / statistics.mean(out["mixed"]["cg_iters"]),
+         "mixed_roofline": {"bound": "hbm", "bytes_per_step": statistics.mean(step_bytes), "achieved_GBps": gbs,
+                            "peak": peak, "frac": gbs / peak,
+                            "bytes_model": f"iterations x (K p map {kp_map} B + CG vectors "
+                                           f"{CG_BYTES_PER_VERTEX} B per free vertex) + {once} B once"},
+         "v_rel_diff_mixed_vs_fp64_form": (res["mixed"][1] - res["fp64"][1]).abs().max().item() / vmax,
+         "mixed_assembled_ms_per_step": out["mixed_assembled"]["ms_per_step"],
+         "cg_iters_mixed_assembled": out["mixed_assembled"]["cg_iters"],
+         "v_rel_diff_mixed_assembled_vs_fp64_form":
+             (res["mixed_assembled"][1] - res["fp64"][1]).abs().max().item() / vmax,
+         "mixed_ordered_ms_per_step": out["mixed_ordered"]["ms_per_step"],
+         "cg_iters_mixed_ordered": out["mixed_ordered"]["cg_iters"],
+         "v_rel_diff_mixed_ordered_vs_fp64_form":
+             (res["mixed_ordered"][1] - res["fp64"][1]).abs().max().item() / vmax}
+    return r, states
 
 
 def batched_steps(abi, torch, local_rank, args):
@@ -619,20 +601,19 @@ def batched_steps(abi, torch, local_rank, args):
     nt = int(b.tets.shape[0])
     out = {"meshes": int(len(sides)), "n_tets": nt, "n_verts": int(b.X.shape[0]),
            "sides_min": int(sides.min()), "sides_max": int(sides.max())}
+    vfinal = {}
     with DeviceTetMesh(b.X, b.tets, batch=b.batch, device=local_rank) as dm:
         uu = dm.vertex_field("u", torch.float64)
         vv = dm.vertex_field("v", torch.float64)
         dm.bind("pinned", torch.from_numpy(b.pinned.astype(np.uint8)).to(uu.device))
-        # tile size and reduction variant of the batch picked by the autotuner
         dm.vertex_field("tu", torch.float32)
         dm.vertex_field("tw", torch.float32, value=meshgen.random_field(b.X.shape[0], seed=5))
         out["autotune"] = tune_report(abi, abi.ebb_relation_autotune(
             dm.ctx, dm.tets, "tu", "tw", abi.map_opts(abi.EBB_NEOHOOKEAN, mu, lam, precision=abi.EBB_PREC_F32)))
-        vfinal = {}
         for name, prec in (("mixed", abi.EBB_PREC_F32), ("fp64", abi.EBB_PREC_F64)):
             prm = abi.step_params(abi.EBB_NEOHOOKEAN, 1e-3, 1000.0, mu, lam, precision=prec, rtol=1e-8)
             ts = []
-            for rep in range(3):
+            for _ in range(3):
                 uu.zero_()
                 vv.zero_()
                 torch.cuda.synchronize()
@@ -643,14 +624,13 @@ def batched_steps(abi, torch, local_rank, args):
             out[f"{name}_ms"] = 1e3 * min(ts[1:])
             its = [r.iters for r in reps]
             out[f"{name}_cg_iters_min_max"] = [min(its), max(its)]
-            vfinal[name] = vv.double().cpu().numpy()
+            vfinal[name] = (uu.double().cpu().numpy().T.copy(), vv.double().cpu().numpy().T.copy())
         out["speedup_vs_fp64_form"] = out["fp64_ms"] / out["mixed_ms"]
-        out["v_rel_diff_mixed_vs_fp64_form"] = float(np.max(np.abs(vfinal["mixed"] - vfinal["fp64"]))
-                                                     / np.max(np.abs(vfinal["fp64"])))
-    # one regular call per mesh (mixed), meshes resident, same workload
+        out["v_rel_diff_mixed_vs_fp64_form"] = float(np.max(np.abs(vfinal["mixed"][1] - vfinal["fp64"][1]))
+                                                     / np.max(np.abs(vfinal["fp64"][1])))
     meshes = []
-    for m in range(len(sides)):
-        X, tets, pinned = b.mesh(m)
+    for mi in range(len(sides)):
+        X, tets, pinned = b.mesh(mi)
         dm = DeviceTetMesh(X, tets, device=local_rank)
         dm.vertex_field("u", torch.float64)
         dm.vertex_field("v", torch.float64)
@@ -670,7 +650,10 @@ def batched_steps(abi, torch, local_rank, args):
     out["batched_speedup_vs_per_mesh_calls"] = out["per_mesh_calls_mixed_ms"] / out["mixed_ms"]
     for dm in meshes:
         dm.close()
-    return out
+    return out, {"batch": b, "mu": mu, "lam": lam, "final": vfinal}
+
+
+ADJ = dict(n=32, steps=20, every=5, dt=1e-3, small_n=4)
 
 
 def adjoint_rollout(abi, torch, local_rank, args):
@@ -678,21 +661,25 @@ def adjoint_rollout(abi, torch, local_rank, args):
     nu = 0.45), 20 implicit steps, loss = sum of squared final displacements,
     gradient w.r.t. (u0, v0, mu, lambda) with checkpoints every 5 steps;
     timed against the plain FP64 forward rollout, and checked against a
-    central difference (h = 1e-6) along one random direction."""
+    central difference (h = 1e-6) along one random direction.  The same
+    rollout gradient on a 4^3 mesh is handed to the CPU leg, which checks it
+    against the oracle's adjoint."""
     from paper_1506_07577_gb300.autograd import rollout
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
-    n, steps, every, dt = 32, 20, 5, 1e-3
-    m = meshgen.cube_grid(n, jitter=0.01, seed=3)
-    mu, lam = meshgen.material_perturbed_lame(m.n_tets, 1e5, 0.45, 0.2, seed=3)
+    steps, every, dt = ADJ["steps"], ADJ["every"], ADJ["dt"]
     dev = torch.device("cuda", local_rank)
     prm = abi.step_params(abi.EBB_STVK, dt, 1000.0, precision=abi.EBB_PREC_F64, max_iters=4000, rtol=1e-12)
-    pin = torch.from_numpy(m.pinned.astype(np.uint8)).to(dev)
-    v0 = 0.05 * meshgen.random_field(m.n_verts, seed=3)
-    v0[m.pinned] = 0.0
 
-    def make(mu_, lam_):
+    def problem(n):
+        m = meshgen.cube_grid(n, jitter=0.01, seed=3)
+        mu, lam = meshgen.material_perturbed_lame(m.n_tets, 1e5, 0.45, 0.2, seed=3)
+        v0 = 0.05 * meshgen.random_field(m.n_verts, seed=3)
+        v0[m.pinned] = 0.0
+        return m, mu, lam, v0
+
+    def make(m, mu_, lam_):
         dm = DeviceTetMesh(m.X, m.tets, mu_, lam_, device=local_rank)
-        dm.bind("pinned", pin)
+        dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(dev))
         return dm
 
     def forward_loss(dm, u0_, v0_):
@@ -702,26 +689,12 @@ def adjoint_rollout(abi, torch, local_rank, args):
             abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "fu", "fv", "pinned", prm)
         return float((uu ** 2).sum())
 
-    out = {"n_tets": m.n_tets, "n_verts": m.n_verts, "steps": steps, "checkpoint_every": every, "dt": dt}
-    with make(mu, lam) as dm:
-        u0 = np.zeros_like(m.X)
-        forward_loss(dm, u0, v0)   # warm-up (graph capture)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        base = forward_loss(dm, u0, v0)
-        torch.cuda.synchronize()
-        out["fp64_forward_ms"] = 1e3 * (time.perf_counter() - t0)
+    def grads(dm, m, mu, lam, v0, timed=None):
         def leaves():
             return (torch.zeros((3, m.n_verts), dtype=torch.float64, device=dev, requires_grad=True),
                     torch.from_numpy(np.ascontiguousarray(v0.T)).to(dev).requires_grad_(True),
                     torch.from_numpy(mu).to(dev).requires_grad_(True),
                     torch.from_numpy(lam).to(dev).requires_grad_(True))
-
-        # Warm-up rollout and backward (first use of the adjoint kernels and
-        # of the solves on the recomputation fields), untimed.
-        tu0, tv0, tmu, tlam = leaves()
-        uT, _ = rollout(dm, tu0, tv0, tmu, tlam, steps, prm, checkpoint_every=every)
-        (uT ** 2).sum().backward()
         tu0, tv0, tmu, tlam = leaves()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -732,13 +705,28 @@ def adjoint_rollout(abi, torch, local_rank, args):
         loss.backward()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        out["forward_with_checkpoints_ms"] = 1e3 * (t1 - t0)
-        out["backward_ms"] = 1e3 * (t2 - t1)
-        out["gradient_over_forward"] = (t2 - t0) / (out["fp64_forward_ms"] / 1e3)
-        out["loss"] = float(loss.detach())
-        out["loss_rel_diff_vs_plain_forward"] = abs(float(loss) - base) / base
-        gu, gv = tu0.grad.cpu().numpy().T, tv0.grad.cpu().numpy().T
-        gmu, glam = tmu.grad.cpu().numpy(), tlam.grad.cpu().numpy()
+        if timed is not None:
+            timed["forward_with_checkpoints_ms"] = 1e3 * (t1 - t0)
+            timed["backward_ms"] = 1e3 * (t2 - t1)
+        return (float(loss.detach()), tu0.grad.cpu().numpy().T, tv0.grad.cpu().numpy().T, tmu.grad.cpu().numpy(),
+                tlam.grad.cpu().numpy())
+
+    m, mu, lam, v0 = problem(ADJ["n"])
+    out = {"n_tets": m.n_tets, "n_verts": m.n_verts, "steps": steps, "checkpoint_every": every, "dt": dt}
+    with make(m, mu, lam) as dm:
+        u0 = np.zeros_like(m.X)
+        forward_loss(dm, u0, v0)   # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        base = forward_loss(dm, u0, v0)
+        torch.cuda.synchronize()
+        out["fp64_forward_ms"] = 1e3 * (time.perf_counter() - t0)
+        grads(dm, m, mu, lam, v0)  # warm-up of the adjoint kernels, untimed
+        loss, gu, gv, gmu, glam = grads(dm, m, mu, lam, v0, timed=out)
+        out["gradient_over_forward"] = (out["forward_with_checkpoints_ms"] + out["backward_ms"]) / out["fp64_forward_ms"]
+        out["backward_over_forward"] = out["backward_ms"] / out["forward_with_checkpoints_ms"]
+        out["loss"] = loss
+        out["loss_rel_diff_vs_plain_forward"] = abs(loss - base) / base
     rng = np.random.default_rng(0)
     dv = rng.normal(size=v0.shape) * 1e-2
     dv[m.pinned] = 0.0
@@ -747,92 +735,324 @@ def adjoint_rollout(abi, torch, local_rank, args):
     h = 1e-6
     vals = []
     for sgn in (1.0, -1.0):
-        with make(mu + sgn * h * dmu, lam + sgn * h * dlam) as dmp:
+        with make(m, mu + sgn * h * dmu, lam + sgn * h * dlam) as dmp:
             vals.append(forward_loss(dmp, np.zeros_like(m.X), v0 + sgn * h * dv))
     fd = (vals[0] - vals[1]) / (2 * h)
     an = float(np.sum(gv * dv) + np.sum(gmu * dmu) + np.sum(glam * dlam))
     out["fd_directional_rel_err"] = abs(fd - an) / abs(an)
+    # the same gradient on a small mesh for the CPU leg's oracle check
+    ms, mus, lams, v0s = problem(ADJ["small_n"])
+    with make(ms, mus, lams) as dm:
+        small = grads(dm, ms, mus, lams, v0s)
+    return out, {"mesh": (ms, mus, lams, v0s), "grads": small}
+
+
+# ---- the CPU leg: oracle timing and every result's error vs the oracle -----
+
+def cpu_baseline(seconds, head, nh64, bat, adj):
+    """Times the FP64 oracle's force + K*w (single thread, numpy) on a
+    contiguous sample of the headline mesh's tets, then checks the timed GPU
+    results against the oracle: the maps at sampled vertices (each recomputed
+    exactly from its incident tets), each implicit-step form's last step
+    through the oracle's linear system at sampled free vertices (b and A dv
+    from the tets around each vertex, dv the GPU's velocity change), the
+    batched step on its smallest, a middle and its largest mesh (whole
+    oracle steps), and the rollout gradient on the small mesh (the oracle's
+    adjoint)."""
+    from oracle import adjoint, fem, implicit
+    m, mu, lam, u, w = head["workload"]
+    sample = min(m.n_tets, 131072)
+    tets = m.tets[:sample]
+    B, V = fem.rest_shape(m.X, tets)
+    x = m.X + u
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        fem.tet_forces(x, tets, B, V, mu, lam, fem.STVK)
+        fem.tet_Kv(x, w, tets, B, V, mu, lam, fem.STVK)
+        done += sample
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    out = {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle force+K*w over the first {sample} (randomly numbered) tets of the permuted "
+                     f"128^3 StVK mesh, repeated for {el:.1f} s ({done} tet evaluations), numpy single thread"}
+    rng = np.random.default_rng(0)
+    errs = {}
+
+    def map_err(mesh, mu_, lam_, u_, w_, model, f_gpu, k_gpu, nsample=32):
+        vs = rng.choice(mesh.n_verts, size=nsample, replace=False)
+        sel = np.isin(mesh.tets, vs).any(axis=1)
+        sub = mesh.tets[sel]
+        Bs, Vs = fem.rest_shape(mesh.X, sub)
+        mu_s = mu_[sel] if np.ndim(mu_) else mu_
+        lam_s = lam_[sel] if np.ndim(lam_) else lam_
+        xs = mesh.X + u_
+        fo = fem.tet_forces(xs, sub, Bs, Vs, mu_s, lam_s, model, mesh.n_verts)[vs]
+        ko = fem.tet_Kv(xs, w_, sub, Bs, Vs, mu_s, lam_s, model, mesh.n_verts)[vs]
+        return max(float(np.max(np.abs(f_gpu[vs] - fo)) / np.max(np.abs(fo))),
+                   float(np.max(np.abs(k_gpu[vs] - ko)) / np.max(np.abs(ko))))
+
+    errs["headline_fused_map_sampled"] = map_err(m, mu, lam, u, w, fem.STVK, head["gpu_f"], head["gpu_k"])
+    if nh64 is not None:
+        mn, mun, lamn, un, wn = nh64["mesh"]
+        errs["nh64_fused_map_sampled"] = map_err(mn, mun, lamn, un, wn, fem.NEOHOOKEAN, *nh64["map"])
+        free = np.flatnonzero(~mn.pinned)
+        vs = rng.choice(free, size=64, replace=False)
+        sel = np.isin(mn.tets, vs).any(axis=1)
+        sub = mn.tets[sel]
+        Bs, Vs = fem.rest_shape(mn.X, sub)
+        mass = fem.lumped_mass(Vs, sub, 1000.0, mn.n_verts)[vs][:, None]
+        dt = 1e-3
+        for name, (u_n, v_n, v_np1) in nh64["steps"].items():
+            xs = mn.X + u_n
+            dvel = v_np1 - v_n
+            f = fem.tet_forces(xs, sub, Bs, Vs, mun[sel], lamn[sel], fem.NEOHOOKEAN, mn.n_verts)[vs]
+            kv = fem.tet_Kv(xs, v_n, sub, Bs, Vs, mun[sel], lamn[sel], fem.NEOHOOKEAN, mn.n_verts)[vs]
+            kdv = fem.tet_Kv(xs, dvel, sub, Bs, Vs, mun[sel], lamn[sel], fem.NEOHOOKEAN, mn.n_verts)[vs]
+            b = dt * (f + mass * np.array(G) - dt * kv)
+            adv = mass * dvel[vs] + dt * dt * kdv
+            errs[f"nh64_step_{name}_residual_sampled"] = float(np.max(np.abs(adv - b)) / np.max(np.abs(b)))
+    if bat is not None:
+        b = bat["batch"]
+        order = np.argsort(b.sides, kind="stable")
+        worst = 0.0
+        for mi in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+            X, tets, pinned = b.mesh(mi)
+            Bm, Vm = fem.rest_shape(X, tets)
+            mass = fem.lumped_mass(Vm, tets, 1000.0, X.shape[0])
+            uo, vo, _ = implicit.implicit_step(X, np.zeros_like(X), np.zeros_like(X), tets, Bm, Vm, mass, bat["mu"],
+                                               bat["lam"], fem.NEOHOOKEAN, 1e-3, np.array(G), pinned, 1000, 1e-8)
+            a, e = b.vert_off[mi], b.vert_off[mi + 1]
+            worst = max(worst, float(np.max(np.abs(bat["final"]["mixed"][1][a:e] - vo)) / np.max(np.abs(vo))))
+        errs["batched_mixed_v_rel_err_3_meshes"] = worst
+    if adj is not None:
+        ms, mus, lams, v0s = adj["mesh"]
+        Bm, Vm = fem.rest_shape(ms.X, ms.tets)
+        mass = fem.lumped_mass(Vm, ms.tets, 1000.0, ms.n_verts)
+        states = adjoint.rollout(ms.X, np.zeros_like(ms.X), v0s, ms.tets, Bm, Vm, mass, mus, lams, ADJ["dt"],
+                                 np.array(G), ms.pinned, ADJ["steps"])
+        uT = states[-1][0]
+        gu, gv, gmu, glam, _ = adjoint.rollout_grad(ms.X, np.zeros_like(ms.X), v0s, ms.tets, Bm, Vm, mass, mus, lams,
+                                                    ADJ["dt"], np.array(G), ms.pinned, ADJ["steps"], 2 * uT,
+                                                    np.zeros_like(uT))
+        _, tgu, tgv, tgmu, tglam = adj["grads"]
+        errs["adjoint_rollout_grad_4cubed"] = max(
+            float(np.max(np.abs(a - b_)) / np.max(np.abs(b_))) for a, b_ in ((tgu, gu), (tgv, gv), (tgmu, gmu),
+                                                                             (tglam, glam)))
+    out["gpu_errors_vs_oracle"] = errs
     return out
 
 
-def permuted_sweep(abi, torch, local_rank, args, peak):
-    """128^3 StVK (FP32 element math), vertex and tet ids randomly permuted
-    (the library reorders tets internally): fused force + K*w per reduction
-    variant, L2 flushed before each timed launch."""
+# ---- reference arm and profiling mode ---------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    m, mu, lam, u, w = workload_permuted(args.n)
+    from oracle import fem
+    sample = min(65536, m.n_tets)
+    tets = m.tets[:sample]
+    B, V = fem.rest_shape(m.X, tets)
+    x = m.X + u
+    for _ in range(args.warmup):
+        fem.tet_forces(x, tets, B, V, mu, lam, fem.STVK)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fem.tet_forces(x, tets, B, V, mu, lam, fem.STVK)
+        fem.tet_Kv(x, w, tets, B, V, mu, lam, fem.STVK)
+    el = time.perf_counter() - t0
+    value = sample * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.n}^3 cube grid, 5 tets/cube, vertex and tet ids permuted, StVK E 1e5 "
+                                   "nu 0.45, force+K*w", "n_tets": m.n_tets, "n_verts": m.n_verts,
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: FP64 oracle force+K*w over the first {sample} tets"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile(argv):
+    """Run one element map (or step, assembled product, spring-mass steps) a
+    few times on a cube-grid workload, for profilers; prints one line.
+
+        python bench.py --profile --n 80 --permute --model stvk --uniform --x4
+
+    Meshes: the n^3 cube grid (1% jitter, seed 2 or, with --permute, seed 5
+    and permuted ids); neo-Hookean/StVK with E log-uniform in [1e4, 1e6],
+    nu = 0.4 per tet, or with --uniform E = 1e5, nu = 0.45."""
+    import torch
+
+    from paper_1506_07577_gb300 import abi
     from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
-    n = args.permuted_n
-    m = meshgen.cube_grid(n, jitter=0.01, seed=5, permute=True)
-    mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
-    u = meshgen.random_displacement(m.X, n, amp=0.05, seed=5, smooth=0.01)
-    w = meshgen.random_field(m.n_verts, seed=5)
+
+    ap = argparse.ArgumentParser(prog="bench.py --profile")
+    ap.add_argument("--profile", action="store_true")
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--variant", choices=["auto", "atomic", "tiled", "colour", "gather", "ordered"], default="tiled")
+    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step", "spmv", "springs"], default="fused")
+    ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
+    ap.add_argument("--permute", action="store_true")
+    ap.add_argument("--uniform", action="store_true", help="uniform material (no per-tet Lame fields)")
+    ap.add_argument("--x4", action="store_true", help="FP32 vector fields as EBB_F32X4 elements")
+    ap.add_argument("--iters", type=int, default=3)
+    a = ap.parse_args(argv)
+
+    seed = 5 if a.permute else 2
+    m = meshgen.cube_grid(a.n, jitter=0.01, seed=seed, permute=a.permute)
+    if a.uniform:
+        mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+    else:
+        mu, lam = meshgen.material_loguniform_E(m.n_tets, 1e4, 1e6, 0.4, 2)
+    u = meshgen.random_displacement(m.X, a.n, amp=0.05, seed=seed, smooth=0.01)
+    w = meshgen.random_field(m.n_verts, seed=seed)
+    dt = torch.float32 if a.prec == "f32" else torch.float64
+    mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
+    red = {"auto": abi.EBB_REDUCE_AUTO, "atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED,
+           "colour": abi.EBB_REDUCE_COLOR, "gather": abi.EBB_REDUCE_GATHER,
+           "ordered": abi.EBB_REDUCE_TILED_ORDERED}[a.variant]
+    mu0, lam0 = (mu, lam) if a.uniform else (0.0, 0.0)
+    prec = abi.EBB_PREC_F32 if a.prec == "f32" else abi.EBB_PREC_F64
+    with DeviceTetMesh(m.X, m.tets, None if a.uniform else mu, None if a.uniform else lam,
+                       colour=(a.variant == "colour"), edges=a.ops in ("spmv", "springs")) as dm:
+        x4 = a.x4 and a.prec == "f32"
+        dm.vertex_field("u", dt, value=u, x4=x4)
+        dm.vertex_field("w", dt, value=w, x4=x4)
+        dm.vertex_field("f", dt, x4=x4)
+        dm.vertex_field("k", dt, x4=x4)
+        o = abi.map_opts(mdl, mu0, lam0, precision=prec, reduce=red, flags=abi.EBB_MAP_ZERO_OUT)
+        if a.variant == "auto":
+            abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(mdl, mu0, lam0, precision=prec))
+        if a.ops == "step":
+            # implicit steps (dt 1e-3, rho 1000, rtol 1e-8) from rest, pinned bottom face
+            dm.vertex_field("uu", torch.float64)
+            dm.vertex_field("vv", torch.float64)
+            dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(dm.device))
+            prm = abi.step_params(mdl, 1e-3, 1000.0, mu0, lam0, precision=prec, reduce=red, rtol=1e-8)
+            for _ in range(a.iters):
+                abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "uu", "vv", "pinned", prm)
+        elif a.ops == "spmv":
+            # K(u) assembled once, then the block-sparse product K w
+            abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u", o)
+            for _ in range(a.iters):
+                abi.ebb_spmv_tet_K(dm.ctx, dm.tets, "w", "k", o)
+        elif a.ops == "springs":
+            # spring-mass steps (K = 1, dt = 1e-4, equal masses) from a perturbed rest state
+            dm.vertex_field("pos", dt, value=m.X)
+            dm.vertex_field("q", dt, value=m.X + 0.002 * np.asarray(w))
+            dm.vertex_field("qd", dt)
+            dm.vertex_field("mass", dt, ncomp=1, value=np.full(m.n_verts, 1000.0 / m.n_verts))
+            abi.ebb_springs_init(dm.ctx, dm.tets, "pos")
+            abi.ebb_springs_run(dm.ctx, dm.tets, "q", "qd", "mass", 1.0, 1e-4, a.iters)
+        else:
+            for _ in range(a.iters):
+                if a.ops == "fused":
+                    abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
+                elif a.ops == "kv":
+                    abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u", "w", "k", o)
+                elif a.ops == "force":
+                    abi.ebb_map_tet_forces(dm.ctx, dm.tets, "u", "f", o)
+                else:
+                    abi.ebb_map_tet_diagK(dm.ctx, dm.tets, "u", "k", o)
+        abi.ebb_ctx_sync(dm.ctx)
+    print("ok", m.n_tets)
+
+
+# ---- main line ----------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1506_07577_gb300 import abi
+
+    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    t0 = time.perf_counter()
-    dm = DeviceTetMesh(m.X, m.tets, device=local_rank, colour=True)
-    setup_s = time.perf_counter() - t0
-    # 4-float vector elements (EBB_F32X4) as in the main line; "tiled_planes"
-    # repeats the tiled map on 3-plane fields
-    dm.vertex_field("u", value=u, x4=True)
-    dm.vertex_field("w", value=w, x4=True)
-    f = dm.vertex_field("f", x4=True)
-    k = dm.vertex_field("k", x4=True)
-    dm.vertex_field("up", torch.float32, value=u)
-    dm.vertex_field("wp", torch.float32, value=w)
-    fp = dm.vertex_field("fp", torch.float32)
-    kp = dm.vertex_field("kp", torch.float32)
-    bpt = 16 + 36 + 4 + 4 * 12 * m.n_verts / m.n_tets
-    out = {"n_tets": m.n_tets, "n_verts": m.n_verts, "finalize_with_colouring_s": setup_s,
-           "algorithmic_bytes_per_tet": bpt}
-    t0 = time.perf_counter()
-    dmr = DeviceTetMesh(m.X, m.tets, device=local_rank, reorder_verts=True)
-    out["finalize_with_vertex_reorder_s"] = time.perf_counter() - t0
-    dmr.vertex_field("u", value=u, x4=True)
-    dmr.vertex_field("w", value=w, x4=True)
-    fr = dmr.vertex_field("f", x4=True)
-    kr = dmr.vertex_field("k", x4=True)
-    names = ("u", "w", "f", "k")
-    for name, red, mesh, ff, kk, nm in (("tiled", abi.EBB_REDUCE_TILED, dm, f, k, names),
-                                        ("tiled_planes", abi.EBB_REDUCE_TILED, dm, fp, kp, ("up", "wp", "fp", "kp")),
-                                        ("tiled_vertex_reordered", abi.EBB_REDUCE_TILED, dmr, fr, kr, names),
-                                        ("atomic", abi.EBB_REDUCE_ATOMIC, dm, f, k, names),
-                                        ("gather", abi.EBB_REDUCE_GATHER, dm, f, k, names),
-                                        ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED, dm, f, k, names),
-                                        ("colour", abi.EBB_REDUCE_COLOR, dm, f, k, names)):
-        o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
-        ts = []
-        for it in range(3 + 5):
-            flush.fill_(float(it))
-            ff.zero_()
-            kk.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            abi.ebb_map_tet_force_Kv(mesh.ctx, mesh.tets, *nm, o)
-            b.record()
-            b.synchronize()
-            if it >= 3:
-                ts.append(a.elapsed_time(b) * 1e-3)
-        t = statistics.median(ts)
-        gbs = bpt * m.n_tets / t / 1e9
-        out[name] = {"us": t * 1e6, "tets_per_s": m.n_tets / t, "algorithmic_GBps": gbs, "frac_of_peak": gbs / peak}
-    out["tiled_vertex_reordered"]["note"] = ("includes permuting u, w into the internal vertex order and adding "
-                                             "f, K*w back")
-    dm.close()
-    dmr.close()
-    return out
+    head = run_headline(args, abi, torch, dev, local_rank, stream, flush, dist, world, barrier)
+    nt, nv = head["n_tets"], head["n_verts"]
+    sub = {}
+    nh64 = bat = adj = None
+    if not args.headline_only:
+        sub, nh64 = run_nh64(args, abi, torch, local_rank, stream, flush)
+        if args.batch_meshes > 0:
+            sub["batched_step"], bat = batched_steps(abi, torch, local_rank, args)
+        if not args.no_adjoint:
+            sub["adjoint_rollout"], adj = adjoint_rollout(abi, torch, local_rank, args)
+
+    peak, peak_kind = _peaks()
+    bpt = algorithmic_bytes_per_tet(nv, nt, False)
+    kern_s = head["kern_us"] * 1e-6
+    achieved = bpt * nt / kern_s / 1e9
+    fresh = NCU_TRAFFIC["sources_sha256_16"] == kernel_sources_hash()
+    tune = head["tune"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": NCU_TRAFFIC["bytes_per_launch"] if fresh else None,
+            "traffic_unit": "bytes per launch (ncu dram read+write)",
+            "kernel": {"tiled": "tet_tile_kernel<float, STVK, FORCE|KV, interleaved>",
+                       "atomic": "tet_map_kernel<float, STVK, FORCE|KV, atomic, interleaved>",
+                       "colour": "tet_map_kernel<float, STVK, FORCE|KV, coloured, interleaved>",
+                       "gather": "tet_corner_kernel + vertex_sum_kernel",
+                       "tiled_ordered": "tet_tile_kernel (partial rows) + partial_sum_kernel"}[tune["reduce"]],
+            "algorithmic_bytes_per_tet": bpt, "kernel_us": head["kern_us"], "peak_kind": peak_kind}
+    if not fresh:
+        roof["traffic_note"] = "no ncu capture of the current kernel sources"
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * head["total_s"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.n}^3 cube grid, 5 tets/cube ({nv:,} verts, {nt:,} tets), vertex and tet "
+                                   "ids randomly permuted (seed 5), StVK E 1e5 nu 0.45, FP32 fused force+K*w map, "
+                                   "reduction variant and tile size from the autotuner, vector fields stored as "
+                                   "4-float elements",
+                       "n_tets": nt, "n_verts": nv, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": head["e2e"],
+            "gpu_launches": args.steps * head["launches_per_step"],
+            "clocks": head["clocks"],
+            "autotune": tune,
+            "layout": {"tiles": head["ntiles"], "colours": head["ncolours"],
+                       "finalize_with_colouring_s": head["setup_s"],
+                       "finalize_with_vertex_reorder_s": head["setup_vertex_reorder_s"]},
+            "reduction_variants": head["variants"]}
+    line.update(sub)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, head, nh64, bat, adj)
+    print(json.dumps(line), flush=True)
 
 
 def main():
+    if "--profile" in sys.argv[1:]:
+        run_profile([a for a in sys.argv[1:]])
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=128, help="cube-grid side of the headline workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true", help="skip the 64^3, batched and adjoint sub-records")
     ap.add_argument("--implicit-steps", type=int, default=10)
     ap.add_argument("--batch-meshes", type=int, default=256)
     ap.add_argument("--no-adjoint", action="store_true")
-    ap.add_argument("--permuted-n", type=int, default=128)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -71,3 +71,18 @@ def test_reference_arm_prints_on_rank_zero_only():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_a_small_headline_mesh():
+    """Rank 0 of the reference arm prints the contract's line: the oracle's
+    tets/s on the headline workload's recipe (here a 16^3 mesh), with
+    cpu_baseline and e2e describing the same run."""
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--n", "16"], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "tets/s" and line["value"] > 0
+    assert line["config"]["n_tets"] == 5 * 16 ** 3
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
