@@ -133,6 +133,19 @@ typedef enum {
                                           implicit step does so once per call.  Not
                                           combinable with verts.batch; the batched step
                                           and the step VJP refuse such relations. */
+#define EBB_FINALIZE_RENUMBER_VERTS 8u  /* renumber the verts relation itself in Morton
+                                          order of the rest positions (Section 5.1:
+                                          keys are opaque and the runtime may reorder a
+                                          relation).  Every vertex field bound or read
+                                          after finalize is indexed by the new row: row
+                                          i holds the caller's vertex order[i] of
+                                          ebb_relation_vertex_order.  verts.X (read at
+                                          finalize) and tets.v keep the caller's
+                                          numbering.  Maps and steps then run with no
+                                          gather or scatter of vertex fields (move data
+                                          into the new order once, and out when
+                                          needed).  Excludes EBB_FINALIZE_REORDER_VERTS
+                                          and verts.batch. */
 #define EBB_FINALIZE_EDGES    4u  /* build the edge relation with self-loops and the
                                      per-tet key-field tets.e[4][4] into it (Section
                                      5.2's tetmesh domain), needed by
@@ -397,11 +410,20 @@ typedef struct {
   int32_t tile_tets;       /* tets per tile at most */
   int32_t ncolours;        /* colours (0 without EBB_FINALIZE_COLOR) */
   int32_t interleaved;     /* FP32 tiled maps stage operands vertex-interleaved */
-  int32_t reordered;       /* finalized with EBB_FINALIZE_REORDER_VERTS */
+  int32_t reordered;       /* 1: EBB_FINALIZE_REORDER_VERTS, 2: EBB_FINALIZE_RENUMBER_VERTS */
   int32_t tuned[2][2];     /* autotuned reduce per [model][precision], -1 none */
 } ebb_relation_info_t;
 
 ebb_status_t ebb_relation_info(ebb_ctx_t ctx, ebb_rel_t tets, ebb_relation_info_t* info);
+
+/* Row order of the verts relation after finalize: order[i] = the caller's
+ * vertex (its row before finalize, the numbering of verts.X and tets.v) now
+ * held in row i of every vertex field.  Identity unless the relation was
+ * finalized with EBB_FINALIZE_RENUMBER_VERTS (EBB_FINALIZE_REORDER_VERTS
+ * keeps fields in the caller's order).  `order` is a HOST array of n =
+ * N_v entries.  Synchronous.  Errors: EBB_ERR_ARG (n != N_v, null order),
+ * EBB_ERR_STATE (not finalized). */
+ebb_status_t ebb_relation_vertex_order(ebb_ctx_t ctx, ebb_rel_t tets, int32_t* order, int64_t n);
 
 /* ---- implicit step (Section 7.2, Section 7.3) --------------------------- */
 

@@ -43,6 +43,7 @@ EBB_REDUCE_TILED_ORDERED = 5
 EBB_FINALIZE_COLOR = 1
 EBB_FINALIZE_REORDER_VERTS = 2
 EBB_FINALIZE_EDGES = 4
+EBB_FINALIZE_RENUMBER_VERTS = 8
 EBB_STEP_ASSEMBLED = 1
 EBB_MAP_ZERO_OUT = 1
 EBB_MAP_TEST_DROP_TILE = 0x80000000
@@ -114,6 +115,7 @@ _SIGS = {
     "ebb_relation_set_tuning": ([ebb_ctx_t, ebb_rel_t, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
                                 ebb_status_t),
     "ebb_relation_info": ([ebb_ctx_t, ebb_rel_t, C.POINTER(ebb_relation_info_t)], ebb_status_t),
+    "ebb_relation_vertex_order": ([ebb_ctx_t, ebb_rel_t, C.c_void_p, C.c_int64], ebb_status_t),
     "ebb_cg_implicit_step": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, C.POINTER(ebb_step_params_t),
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_vjp": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ebb_step_params_t),
@@ -294,6 +296,15 @@ def ebb_relation_info(ctx, tets):
     info = ebb_relation_info_t()
     _check(ctx, _lib.ebb_relation_info(ctx, tets, C.byref(info)))
     return info
+
+
+def ebb_relation_vertex_order(ctx, tets, n_verts):
+    """Row order of the verts relation: numpy int32 array, entry i = the
+    caller's vertex held in row i of every vertex field."""
+    import numpy as np
+    order = np.empty(int(n_verts), dtype=np.int32)
+    _check(ctx, _lib.ebb_relation_vertex_order(ctx, tets, C.c_void_p(order.ctypes.data), int(n_verts)))
+    return order
 
 
 def step_params(model, dt, rho, mu=0.0, lam=0.0, gravity=(0.0, 0.0, -9.81), precision=EBB_PREC_F64,

@@ -106,6 +106,7 @@ void free_tet_data(ebb_rel_s* r) {
   r->keys = nullptr;
   cudaFree(r->vperm);
   r->vperm = nullptr;
+  r->vorder.clear();
   for (void*& p : r->vscratch) {
     cudaFree(p);
     p = nullptr;
@@ -555,11 +556,17 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     }
   }
   // Optional vertex renumbering: keys, rest positions and everything built
-  // from them switch to the internal (Morton) vertex order.
+  // from them switch to the internal (Morton) vertex order.  REORDER keeps
+  // the vertex fields in the caller's order (maps and steps stage them);
+  // RENUMBER makes the new order the relation's own, for every vertex field
+  // bound or read from now on.
   double* X_int = nullptr;
-  if (flags & EBB_FINALIZE_REORDER_VERTS) {
+  const bool renumber = (flags & EBB_FINALIZE_RENUMBER_VERTS) != 0;
+  if ((flags & EBB_FINALIZE_REORDER_VERTS) && renumber)
+    return set_error(ctx, EBB_ERR_ARG, "EBB_FINALIZE_REORDER_VERTS and EBB_FINALIZE_RENUMBER_VERTS exclude each other");
+  if ((flags & EBB_FINALIZE_REORDER_VERTS) || renumber) {
     if (!hbatch.empty())
-      return set_error(ctx, EBB_ERR_ARG, "EBB_FINALIZE_REORDER_VERTS cannot be combined with verts.batch");
+      return set_error(ctx, EBB_ERR_ARG, "renumbering vertices cannot be combined with verts.batch");
     std::vector<int> vp, vinv(nv);
     vertex_morton_order(hX, vp);
     for (int i = 0; i < nv; ++i) vinv[vp[i]] = i;
@@ -569,8 +576,13 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     for (int c = 0; c < 3; ++c)
       for (int i = 0; i < nv; ++i) hXi[(size_t)c * nv + i] = hX[(size_t)c * nv + vp[i]];
     hX.swap(hXi);
-    cudaError_t ve = cudaMalloc(&tets->vperm, sizeof(int) * nv);
-    if (ve == cudaSuccess) ve = cudaMemcpy(tets->vperm, vp.data(), sizeof(int) * nv, cudaMemcpyHostToDevice);
+    cudaError_t ve = cudaSuccess;
+    if (renumber) {
+      tets->vorder = vp;
+    } else {
+      ve = cudaMalloc(&tets->vperm, sizeof(int) * nv);
+      if (ve == cudaSuccess) ve = cudaMemcpy(tets->vperm, vp.data(), sizeof(int) * nv, cudaMemcpyHostToDevice);
+    }
     if (ve == cudaSuccess) ve = cudaMalloc(&X_int, sizeof(double) * hX.size());
     if (ve == cudaSuccess) ve = cudaMemcpy(X_int, hX.data(), sizeof(double) * hX.size(), cudaMemcpyHostToDevice);
     if (ve != cudaSuccess) {
@@ -981,9 +993,21 @@ ebb_status_t ebb_relation_info(ebb_ctx_t ctx, ebb_rel_t tets, ebb_relation_info_
   info->tile_tets = tets->tile_cap;
   info->ncolours = tets->has_colour ? tets->colour.ncolours : 0;
   info->interleaved = tets->stage_interleaved ? 1 : 0;
-  info->reordered = tets->vperm != nullptr ? 1 : 0;
+  info->reordered = tets->vperm != nullptr ? 1 : (tets->vorder.empty() ? 0 : 2);
   for (int m = 0; m < 2; ++m)
     for (int p = 0; p < 2; ++p) info->tuned[m][p] = tets->tuned[m][p];
+  return EBB_OK;
+}
+
+ebb_status_t ebb_relation_vertex_order(ebb_ctx_t ctx, ebb_rel_t tets, int32_t* order, int64_t n) {
+  if (!ctx) return EBB_ERR_ARG;
+  ctx->last_error.clear();
+  if (!tets) return set_error(ctx, EBB_ERR_ARG, "null relation");
+  if (tets->ctx != ctx) return set_error(ctx, EBB_ERR_ARG, "relation belongs to another context");
+  if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
+  const int64_t nv = tets->verts->size;
+  if (n != nv || (nv > 0 && !order)) return set_error(ctx, EBB_ERR_ARG, "order needs exactly one entry per vertex");
+  for (int64_t i = 0; i < nv; ++i) order[i] = tets->vorder.empty() ? (int32_t)i : tets->vorder[i];
   return EBB_OK;
 }
 

@@ -176,6 +176,7 @@ struct ebb_rel_s {
   int4* keys = nullptr;                 // internal keys, one int4 per tet (Morton order)
   int* tet_perm = nullptr;              // internal row -> caller's row
   int* vperm = nullptr;                 // internal vertex -> caller's vertex (null: same order)
+  std::vector<int> vorder;              // EBB_FINALIZE_RENUMBER_VERTS: row i was the caller's vertex vorder[i]
   void* vscratch[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // reordered map operands
   ebb::TetStreams<double> s64;
   ebb::TetStreams<float> s32;

@@ -19,7 +19,7 @@ class DeviceTetMesh:
     bound, finalized on construction."""
 
     def __init__(self, X, tets, mu=None, lam=None, device=0, stream=None, colour=False, batch=None,
-                 reorder_verts=False, edges=False):
+                 reorder_verts=False, edges=False, renumber_verts=False):
         self.device = torch.device("cuda", device)
         self.ctx = abi.ebb_ctx_create(device, stream)
         self.n_verts = int(X.shape[0])
@@ -41,8 +41,27 @@ class DeviceTetMesh:
         # uploads ran on torch's current stream; the library may use another
         torch.cuda.synchronize(self.device)
         flags = ((abi.EBB_FINALIZE_COLOR if colour else 0) | (abi.EBB_FINALIZE_REORDER_VERTS if reorder_verts else 0) |
-                 (abi.EBB_FINALIZE_EDGES if edges else 0))
+                 (abi.EBB_FINALIZE_EDGES if edges else 0) | (abi.EBB_FINALIZE_RENUMBER_VERTS if renumber_verts else 0))
         abi.ebb_relation_finalize(self.ctx, self.tets, flags)
+        # Row order of vertex fields: identity unless the relation renumbered
+        # its vertices (then row i holds the caller's vertex order[i]).
+        self.renumbered = bool(renumber_verts)
+        self.order = abi.ebb_relation_vertex_order(self.ctx, self.tets, self.n_verts)
+
+    def rows(self, arr):
+        """A per-vertex array (N_v, ...) in the caller's vertex order, put in
+        the relation's row order."""
+        return np.asarray(arr)[self.order] if self.renumbered else np.asarray(arr)
+
+    def caller(self, arr):
+        """A per-vertex array (N_v, ...) in the relation's row order, put
+        back in the caller's vertex order."""
+        arr = np.asarray(arr)
+        if not self.renumbered:
+            return arr
+        out = np.empty_like(arr)
+        out[self.order] = arr
+        return out
 
     def _put(self, name, arr, rel):
         t = torch.from_numpy(np.ascontiguousarray(arr)).to(self.device)
@@ -54,7 +73,11 @@ class DeviceTetMesh:
         """Allocate (or upload) a vertex field of shape (ncomp, N_v), bind it
         under ``name`` and return the tensor.  ``value`` may be an (N_v, ncomp)
         numpy array.  With ``x4`` the field is an EBB_F32X4 field: a float32
-        tensor of shape (N_v, 4) whose first three columns hold the vectors."""
+        tensor of shape (N_v, 4) whose first three columns hold the vectors.
+        ``value`` is given in the caller's vertex order; on a relation that
+        renumbered its vertices it is stored in the relation's row order."""
+        if value is not None:
+            value = self.rows(value)
         if x4:
             t = torch.zeros((self.n_verts, 4), dtype=torch.float32, device=self.device)
             if value is not None:
