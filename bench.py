@@ -189,13 +189,16 @@ def replica_throughput(units_per_rank, seconds_max, world):
     return units_per_rank * world / seconds_max
 
 
-REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather", 5: "tiled_ordered"}
+REDUCE_NAMES = {0: "atomic", 1: "colour", 3: "tiled", 4: "gather", 5: "tiled_ordered", 6: "coop"}
 
 
 def tune_report(abi, rep):
     return {"reduce": REDUCE_NAMES[rep.reduce], "tile_tets": rep.tile_tets, "interleaved": bool(rep.interleaved),
+            "records": "planes" if rep.record_planes else "rows",
             "candidates_kw_map_us": [{"reduce": REDUCE_NAMES[rep.cand[i].reduce], "tile_tets": rep.cand[i].tile_tets,
-                                      "interleaved": bool(rep.cand[i].interleaved), "us": rep.cand[i].us}
+                                      "interleaved": bool(rep.cand[i].interleaved),
+                                      "records": "planes" if rep.cand[i].record_planes else "rows",
+                                      "us": rep.cand[i].us}
                                      for i in range(rep.ncand)]}
 
 
@@ -203,7 +206,8 @@ def map_launches(reduce_name, info, staged):
     """Library kernels one map call launches: the map itself (one launch per
     colour for the coloured variant, two passes for gather and ordered),
     plus the copy-in and add-back of staged operands."""
-    n = {"tiled": 1, "atomic": 1, "gather": 2, "tiled_ordered": 2, "colour": max(int(info.ncolours), 1)}[reduce_name]
+    n = {"tiled": 1, "atomic": 1, "coop": 1, "gather": 2, "tiled_ordered": 2,
+         "colour": max(int(info.ncolours), 1)}[reduce_name]
     return n + (2 if staged else 0)
 
 
@@ -332,7 +336,7 @@ def run_headline(args, abi, torch, dev, local_rank, stream, flush, dist, world, 
 
     for name, red in (("tiled", abi.EBB_REDUCE_TILED), ("atomic", abi.EBB_REDUCE_ATOMIC),
                       ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED), ("gather", abi.EBB_REDUCE_GATHER),
-                      ("colour", abi.EBB_REDUCE_COLOR)):
+                      ("coop", abi.EBB_REDUCE_COOP), ("colour", abi.EBB_REDUCE_COLOR)):
         o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=red)
         us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o),
                         zero_xk, flush, 5)
@@ -421,7 +425,8 @@ def run_nh64(args, abi, torch, local_rank, stream, flush):
     variants = {}
     for name, red in (("autotuned", abi.EBB_REDUCE_AUTO), ("tiled", abi.EBB_REDUCE_TILED),
                       ("atomic", abi.EBB_REDUCE_ATOMIC), ("tiled_ordered", abi.EBB_REDUCE_TILED_ORDERED),
-                      ("gather", abi.EBB_REDUCE_GATHER), ("colour", abi.EBB_REDUCE_COLOR)):
+                      ("gather", abi.EBB_REDUCE_GATHER), ("coop", abi.EBB_REDUCE_COOP),
+                      ("colour", abi.EBB_REDUCE_COLOR)):
         o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=red)
         us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32", "w32", "f", "Kw", o),
                         zero, flush, 5)
@@ -518,17 +523,27 @@ def springs_directed_count(m):
 
 
 def fp64_map_leg(dm, u, w, abi, torch, stream, flush):
-    """The FP64 K w map (neo-Hookean, tiled, 3-plane FP64 fields) that the
-    FP64 form of the implicit step runs once per CG iteration, against
-    GB300's FP64 arithmetic peak (the kernel is bound by the FP64 pipe)."""
+    """The FP64 K w map (neo-Hookean, 3-plane FP64 fields) that the FP64
+    form of the implicit step runs once per CG iteration, against GB300's
+    FP64 arithmetic peak (the kernel is bound by the FP64 pipe): the tiled
+    map with row records and with field-plane records, and the cooperative
+    map (three threads per tet); the fastest is the winner."""
     nt = dm.n_tets
     dm.vertex_field("u64", torch.float64, value=u)
     dm.vertex_field("w64", torch.float64, value=w)
     kk = dm.vertex_field("k64", torch.float64)
-    o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64, reduce=abi.EBB_REDUCE_TILED)
-    us = time_calls(torch, stream, lambda: abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u64", "w64", "k64", o), kk.zero_,
-                    flush, 5)
+    forms = {}
+    for name, red, flags in (("tiled_rows", abi.EBB_REDUCE_TILED, 0),
+                             ("tiled_planes", abi.EBB_REDUCE_TILED, abi.EBB_TUNE_RECORD_PLANES),
+                             ("coop", abi.EBB_REDUCE_COOP, 0)):
+        abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_NEOHOOKEAN, abi.EBB_PREC_F64, red, 128, flags)
+        o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64, reduce=abi.EBB_REDUCE_AUTO)
+        forms[name] = time_calls(torch, stream, lambda: abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u64", "w64", "k64", o),
+                                 kk.zero_, flush, 5)
+    abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_NEOHOOKEAN, abi.EBB_PREC_F64, abi.EBB_REDUCE_TILED, 128, 0)
+    us = forms["tiled_rows"]
     out = {"kernel": "tet_tile_kernel<double, NEOHOOKEAN, KV>", "us": us, "tets_per_s": nt / (us * 1e-6),
+           "forms_us": forms, "winner": min(forms, key=forms.get),
            "bound": "alu", "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2070 MHz"}
     if kernel_sources_hash(FP64_SOURCES) == NCU_FP64["sources_sha256_16"]:
         fl = NCU_FP64["kv_map_nh_flops_per_tet"]
@@ -913,7 +928,9 @@ def run_profile(argv):
     ap = argparse.ArgumentParser(prog="bench.py --profile")
     ap.add_argument("--profile", action="store_true")
     ap.add_argument("--n", type=int, default=64)
-    ap.add_argument("--variant", choices=["auto", "atomic", "tiled", "colour", "gather", "ordered"], default="tiled")
+    ap.add_argument("--variant", choices=["auto", "atomic", "tiled", "colour", "gather", "ordered", "coop"],
+                    default="tiled")
+    ap.add_argument("--planes", action="store_true", help="tile blobs with per-tet data as field planes")
     ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step", "spmv", "springs"], default="fused")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
@@ -936,7 +953,7 @@ def run_profile(argv):
     mdl = abi.EBB_NEOHOOKEAN if a.model == "nh" else abi.EBB_STVK
     red = {"auto": abi.EBB_REDUCE_AUTO, "atomic": abi.EBB_REDUCE_ATOMIC, "tiled": abi.EBB_REDUCE_TILED,
            "colour": abi.EBB_REDUCE_COLOR, "gather": abi.EBB_REDUCE_GATHER,
-           "ordered": abi.EBB_REDUCE_TILED_ORDERED}[a.variant]
+           "ordered": abi.EBB_REDUCE_TILED_ORDERED, "coop": abi.EBB_REDUCE_COOP}[a.variant]
     mu0, lam0 = (mu, lam) if a.uniform else (0.0, 0.0)
     prec = abi.EBB_PREC_F32 if a.prec == "f32" else abi.EBB_PREC_F64
     with DeviceTetMesh(m.X, m.tets, None if a.uniform else mu, None if a.uniform else lam,
@@ -950,6 +967,8 @@ def run_profile(argv):
         o = abi.map_opts(mdl, mu0, lam0, precision=prec, reduce=red, flags=abi.EBB_MAP_ZERO_OUT)
         if a.variant == "auto":
             abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(mdl, mu0, lam0, precision=prec))
+        elif a.planes:
+            abi.ebb_relation_set_tuning(dm.ctx, dm.tets, mdl, prec, red, 128, abi.EBB_TUNE_RECORD_PLANES)
         if a.ops == "step":
             # implicit steps (dt 1e-3, rho 1000, rtol 1e-8) from rest, pinned bottom face
             dm.vertex_field("uu", torch.float64)
@@ -1010,7 +1029,7 @@ def run_ours(args, rank, world, local_rank):
     sub = {}
     nh64 = bat = adj = None
     if not args.headline_only:
-        sub, nh64 = run_nh64(args, abi, torch, local_rank, stream, flush)
+        sub["nh64"], nh64 = run_nh64(args, abi, torch, local_rank, stream, flush)
         if args.batch_meshes > 0:
             sub["batched_step"], bat = batched_steps(abi, torch, local_rank, args)
         if not args.no_adjoint:

@@ -113,6 +113,11 @@ typedef enum { EBB_PREC_F64 = 0, EBB_PREC_F32 = 1 } ebb_precision_t;
  *           floating-point atomics: bitwise reproducible run to run, no
  *           colouring needed.  Not an autotuner candidate (it is the tiled
  *           pass plus a second pass).
+ *   COOP:   three threads per tet (Section 8's several threads per row):
+ *           thread r of a group computes row r of every per-tet matrix
+ *           product and component r of every corner output, exchanging
+ *           the rows it needs with its neighbours through warp shuffles;
+ *           hardware atomic adds into the vertex fields.
  *   AUTO:   the autotuned choice (ebb_relation_autotune), else TILED. */
 typedef enum {
   EBB_REDUCE_ATOMIC = 0,
@@ -120,7 +125,8 @@ typedef enum {
   EBB_REDUCE_AUTO = 2,
   EBB_REDUCE_TILED = 3,
   EBB_REDUCE_GATHER = 4,
-  EBB_REDUCE_TILED_ORDERED = 5
+  EBB_REDUCE_TILED_ORDERED = 5,
+  EBB_REDUCE_COOP = 6
 } ebb_reduce_t;
 
 /* ebb_relation_finalize flags */
@@ -355,8 +361,12 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * also at the best of those with the operands staged vertex-interleaved
  * (library-owned copies that let a vertex be fetched with one 16-byte copy
  * and reduced with one vector atomic, at the price of a copy in and an add
- * back per call), the atomic variant, the gather variant, and the coloured
- * variant if the relation was finalized with EBB_FINALIZE_COLOR.
+ * back per call), the atomic variant, the gather variant, the cooperative
+ * variant, and the coloured variant if the relation was finalized with
+ * EBB_FINALIZE_COLOR; then, at
+ * the best tiled configuration, the tile blobs' per-tet data as per-field
+ * planes (SoA) instead of one row record per tet (AoSoA: the fields an
+ * element uses together side by side, Section 8's row-oriented storage).
  * Each candidate: 2 untimed launches, then the median of 7 launches timed
  * with CUDA events on the context's stream.  Afterwards the relation's tiles
  * use the fastest tile size (the blobs are rebuilt if it changed) and
@@ -366,11 +376,12 @@ ebb_status_t ebb_map_tet_diagK(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * order of floating-point additions.  Synchronous; allocates and frees an
  * output scratch field.  Errors: EBB_ERR_ARG / EBB_ERR_STATE as for the maps;
  * device errors of the timed maps (EBB_ERR_INVERTED) are returned. */
-#define EBB_AUTOTUNE_MAX_CAND 8
+#define EBB_AUTOTUNE_MAX_CAND 12
 typedef struct {
-  int32_t reduce;       /* EBB_REDUCE_TILED, _ATOMIC, _GATHER or _COLOR */
+  int32_t reduce;       /* EBB_REDUCE_TILED, _ATOMIC, _GATHER, _COOP or _COLOR */
   int32_t tile_tets;    /* tets per tile for EBB_REDUCE_TILED, 0 otherwise */
   int32_t interleaved;  /* 1: FP32 operands staged vertex-interleaved */
+  int32_t record_planes;/* 1: tile blobs hold per-tet data as field planes */
   double us;            /* median duration of one K w map call, microseconds */
 } ebb_autotune_cand_t;
 
@@ -378,6 +389,7 @@ typedef struct {
   int32_t reduce;       /* variant EBB_REDUCE_AUTO now selects */
   int32_t tile_tets;    /* tets per tile of the relation's layout now */
   int32_t interleaved;  /* FP32 tiled maps now stage operands vertex-interleaved */
+  int32_t record_planes;/* tile blobs now hold per-tet data as field planes */
   int32_t ncand;
   ebb_autotune_cand_t cand[EBB_AUTOTUNE_MAX_CAND];
 } ebb_autotune_report_t;
@@ -387,15 +399,19 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                    ebb_autotune_report_t* report);
 
 /* Set by hand what ebb_relation_autotune would choose: EBB_REDUCE_AUTO
- * resolves to `reduce` (TILED, TILED_ORDERED, ATOMIC, GATHER or COLOR) for `model` and
+ * resolves to `reduce` (TILED, TILED_ORDERED, ATOMIC, GATHER, COOP or COLOR) for `model` and
  * `precision`;
  * the tiles are re-cut to at most `tile_tets` tets (1..128) if that differs;
- * `interleaved` (0/1) sets the FP32 vertex-interleaved staging of the tiled
- * maps.  Synchronous.  Errors: EBB_ERR_ARG (out-of-range value),
- * EBB_ERR_STATE (not finalized, or COLOR without EBB_FINALIZE_COLOR). */
+ * `flags` holds EBB_TUNE_INTERLEAVED (the FP32 vertex-interleaved staging of
+ * the tiled maps) and EBB_TUNE_RECORD_PLANES (tile blobs with per-tet data as
+ * field planes; without it, row records).  Synchronous.  Errors: EBB_ERR_ARG
+ * (out-of-range value), EBB_ERR_STATE (not finalized, or COLOR without
+ * EBB_FINALIZE_COLOR). */
+#define EBB_TUNE_INTERLEAVED    1u
+#define EBB_TUNE_RECORD_PLANES  2u
 ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t model,
                                      int32_t precision, int32_t reduce, int32_t tile_tets,
-                                     int32_t interleaved);
+                                     int32_t flags);
 
 /* Layout of a finalized tets relation as the maps see it (read only, host
  * side): how many tiles the tiled variants walk and how many tets each holds
@@ -411,6 +427,7 @@ typedef struct {
   int32_t ncolours;        /* colours (0 without EBB_FINALIZE_COLOR) */
   int32_t interleaved;     /* FP32 tiled maps stage operands vertex-interleaved */
   int32_t reordered;       /* 1: EBB_FINALIZE_REORDER_VERTS, 2: EBB_FINALIZE_RENUMBER_VERTS */
+  int32_t record_planes;   /* tile blobs hold per-tet data as field planes */
   int32_t tuned[2][2];     /* autotuned reduce per [model][precision], -1 none */
 } ebb_relation_info_t;
 

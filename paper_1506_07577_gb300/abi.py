@@ -40,6 +40,7 @@ EBB_STVK, EBB_NEOHOOKEAN = 0, 1
 EBB_PREC_F64, EBB_PREC_F32 = 0, 1
 EBB_REDUCE_ATOMIC, EBB_REDUCE_COLOR, EBB_REDUCE_AUTO, EBB_REDUCE_TILED, EBB_REDUCE_GATHER = 0, 1, 2, 3, 4
 EBB_REDUCE_TILED_ORDERED = 5
+EBB_REDUCE_COOP = 6
 EBB_FINALIZE_COLOR = 1
 EBB_FINALIZE_REORDER_VERTS = 2
 EBB_FINALIZE_EDGES = 4
@@ -67,15 +68,19 @@ class ebb_step_params_t(C.Structure):
                 ("rtol", C.c_double), ("fail_on_max_iters", C.c_int32), ("flags", C.c_uint32)]
 
 
-EBB_AUTOTUNE_MAX_CAND = 8
+EBB_AUTOTUNE_MAX_CAND = 12
+EBB_TUNE_INTERLEAVED = 1
+EBB_TUNE_RECORD_PLANES = 2
 
 
 class ebb_autotune_cand_t(C.Structure):
-    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("interleaved", C.c_int32), ("us", C.c_double)]
+    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("interleaved", C.c_int32),
+                ("record_planes", C.c_int32), ("us", C.c_double)]
 
 
 class ebb_autotune_report_t(C.Structure):
-    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("interleaved", C.c_int32), ("ncand", C.c_int32),
+    _fields_ = [("reduce", C.c_int32), ("tile_tets", C.c_int32), ("interleaved", C.c_int32),
+                ("record_planes", C.c_int32), ("ncand", C.c_int32),
                 ("cand", ebb_autotune_cand_t * EBB_AUTOTUNE_MAX_CAND)]
 
 
@@ -86,7 +91,7 @@ class ebb_cg_report_t(C.Structure):
 class ebb_relation_info_t(C.Structure):
     _fields_ = [("n_tets", C.c_int64), ("n_verts", C.c_int64), ("ntiles", C.c_int32), ("tile_tets", C.c_int32),
                 ("ncolours", C.c_int32), ("interleaved", C.c_int32), ("reordered", C.c_int32),
-                ("tuned", (C.c_int32 * 2) * 2)]
+                ("record_planes", C.c_int32), ("tuned", (C.c_int32 * 2) * 2)]
 
 
 _P = C.c_char_p
@@ -286,9 +291,11 @@ def ebb_relation_autotune(ctx, tets, u, w, opts):
     return rep
 
 
-def ebb_relation_set_tuning(ctx, tets, model, precision, reduce, tile_tets, interleaved):
+def ebb_relation_set_tuning(ctx, tets, model, precision, reduce, tile_tets, flags=0):
+    """`flags`: EBB_TUNE_INTERLEAVED | EBB_TUNE_RECORD_PLANES (a bool is
+    taken as EBB_TUNE_INTERLEAVED)."""
     return _check(ctx, _lib.ebb_relation_set_tuning(ctx, tets, int(model), int(precision), int(reduce),
-                                                    int(tile_tets), int(bool(interleaved))))
+                                                    int(tile_tets), int(flags)))
 
 
 def ebb_relation_info(ctx, tets):

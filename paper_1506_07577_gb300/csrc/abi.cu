@@ -170,7 +170,7 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 // A concrete reduction variant (AUTO resolved).
 bool valid_reduce(int r) {
   return r == EBB_REDUCE_ATOMIC || r == EBB_REDUCE_COLOR || r == EBB_REDUCE_TILED || r == EBB_REDUCE_GATHER ||
-         r == EBB_REDUCE_TILED_ORDERED;
+         r == EBB_REDUCE_TILED_ORDERED || r == EBB_REDUCE_COOP;
 }
 
 // EBB_REDUCE_AUTO: the autotuned variant for this model and precision, else
@@ -842,7 +842,7 @@ ebb_status_t ebb_spmv_tet_K(ebb_ctx_t ctx, ebb_rel_t tets, const char* w, const 
 }
 
 ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t model, int32_t precision,
-                                     int32_t reduce, int32_t tile_tets, int32_t interleaved) {
+                                     int32_t reduce, int32_t tile_tets, int32_t flags) {
   if (!ctx) return EBB_ERR_ARG;
   ctx->last_error.clear();
   if (!tets) return set_error(ctx, EBB_ERR_ARG, "null relation");
@@ -850,7 +850,7 @@ ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t mode
   if (!tets->finalized) return set_error(ctx, EBB_ERR_STATE, "relation not finalized");
   if ((model != EBB_STVK && model != EBB_NEOHOOKEAN) || (precision != EBB_PREC_F64 && precision != EBB_PREC_F32) ||
       !valid_reduce(reduce) || tile_tets < 1 ||
-      tile_tets > kTileTets || (interleaved != 0 && interleaved != 1))
+      tile_tets > kTileTets || (flags & ~(int32_t)(EBB_TUNE_INTERLEAVED | EBB_TUNE_RECORD_PLANES)) != 0)
     return set_error(ctx, EBB_ERR_ARG, "tuning value out of range");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
@@ -859,7 +859,12 @@ ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t mode
     if (s) return s;
   }
   tets->tuned[model][precision] = (signed char)reduce;
-  tets->stage_interleaved = interleaved != 0;
+  tets->stage_interleaved = (flags & EBB_TUNE_INTERLEAVED) != 0;
+  const bool planes = (flags & EBB_TUNE_RECORD_PLANES) != 0;
+  if (planes != tets->rec_planes) {
+    ebb_status_t s = repack_records(ctx, tets, planes);
+    if (s) return s;
+  }
   return EBB_OK;
 }
 
@@ -928,8 +933,9 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
   int best_cap = tets->tile_cap;
   ebb_reduce_t best = EBB_REDUCE_TILED;
   tets->stage_interleaved = false;
+  if (tets->rec_planes) s = repack_records(ctx, tets, false);   // tile sizes are timed with row records
   const int caps[3] = {128, 96, 64};
-  for (int ci = 0; ci < 3; ++ci) {
+  for (int ci = 0; ci < 3 && !s; ++ci) {
     if (tets->tile_cap != caps[ci]) {
       s = rebuild_tiles(ctx, tets, caps[ci]);
       if (s) break;
@@ -937,7 +943,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
     double us = 0.0;
     s = time_map(EBB_REDUCE_TILED, &us);
     if (s) break;
-    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], x4 ? 1 : 0, us};
+    report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, caps[ci], x4 ? 1 : 0, tets->rec_planes ? 1 : 0, us};
     if (us < best_tiled_us) {
       best_tiled_us = us;
       best_cap = caps[ci];
@@ -950,18 +956,33 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
     double us = 0.0;
     s = time_map(EBB_REDUCE_TILED, &us);
     if (!s) {
-      report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, best_cap, 1, us};
+      report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, best_cap, 1, tets->rec_planes ? 1 : 0, us};
       if (us < best_tiled_us) best_tiled_us = us;
       else tets->stage_interleaved = false;
     }
   }
-  const ebb_reduce_t others[3] = {EBB_REDUCE_ATOMIC, EBB_REDUCE_GATHER, EBB_REDUCE_COLOR};
-  for (int oi = 0; oi < 3 && !s; ++oi) {
+  if (!s) {
+    // the same configuration with the other record layout
+    const bool was = tets->rec_planes;
+    s = repack_records(ctx, tets, !was);
+    double us = 0.0;
+    if (!s) s = time_map(EBB_REDUCE_TILED, &us);
+    if (!s) {
+      report->cand[nc++] = ebb_autotune_cand_t{EBB_REDUCE_TILED, best_cap,
+                                               (!f64 && (x4 || tets->stage_interleaved)) ? 1 : 0, !was ? 1 : 0, us};
+      if (us < best_tiled_us)
+        best_tiled_us = us;
+      else
+        s = repack_records(ctx, tets, was);
+    }
+  }
+  const ebb_reduce_t others[4] = {EBB_REDUCE_ATOMIC, EBB_REDUCE_GATHER, EBB_REDUCE_COOP, EBB_REDUCE_COLOR};
+  for (int oi = 0; oi < 4 && !s; ++oi) {
     if (others[oi] == EBB_REDUCE_COLOR && !tets->has_colour) continue;
     double us = 0.0;
     s = time_map(others[oi], &us);
     if (s) break;
-    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, x4 ? 1 : 0, us};
+    report->cand[nc++] = ebb_autotune_cand_t{others[oi], 0, x4 ? 1 : 0, 0, us};
     if (us < best_us) {
       best_us = us;
       best = others[oi];
@@ -976,6 +997,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
   report->reduce = best;
   report->tile_tets = tets->tile_cap;
   report->interleaved = (!f64 && (x4 || tets->stage_interleaved)) ? 1 : 0;
+  report->record_planes = tets->rec_planes ? 1 : 0;
   report->ncand = nc;
   return EBB_OK;
 }
@@ -994,6 +1016,7 @@ ebb_status_t ebb_relation_info(ebb_ctx_t ctx, ebb_rel_t tets, ebb_relation_info_
   info->ncolours = tets->has_colour ? tets->colour.ncolours : 0;
   info->interleaved = tets->stage_interleaved ? 1 : 0;
   info->reordered = tets->vperm != nullptr ? 1 : (tets->vorder.empty() ? 0 : 2);
+  info->record_planes = tets->rec_planes ? 1 : 0;
   for (int m = 0; m < 2; ++m)
     for (int p = 0; p < 2; ++p) info->tuned[m][p] = tets->tuned[m][p];
   return EBB_OK;

@@ -63,14 +63,17 @@ struct Colouring {
 //                                    lane of that run (adds the sum into the
 //                                    field)
 //   vtx     int[kTileSlots]          vertex id of each slot
-//   rec     T[kTileTets][rec_len<T>] one row-oriented record per tet (the
-//                                    fields one element uses together):
-//                                    Dm^-1 entries (r,c) at 3r+c, rest
-//                                    volume at 9, Lame mu, lambda at 10, 11
-//                                    (zero without per-tet material), then
-//                                    padding; 48 B (FP32) or 112 B (FP64),
-//                                    strides at which a thread's 16-byte
-//                                    loads stay free of bank conflicts
+//   rec     the per-tet element data in one of two layouts (a tuning
+//           choice, BlobLayout::planes):
+//           rows    T[kTileTets][rec_len<T>] one row-oriented record per tet
+//                   (the fields one element uses together): Dm^-1 entries
+//                   (r,c) at 3r+c, rest volume at 9, Lame mu, lambda at 10,
+//                   11 (zero without per-tet material), then padding; 48 B
+//                   (FP32) or 112 B (FP64), strides at which a thread's
+//                   16-byte loads stay free of bank conflicts
+//           planes  T[12][kTileTets] one plane per field (Dm^-1 entries,
+//                   V, mu, lambda): consecutive tets' values adjacent; without
+//                   per-tet material the last two planes are not copied
 // Unused tail entries are zero.
 constexpr int kTileTets = 128;   // tets per tile (= threads per CTA)
 constexpr int kTileSlots = 128;  // distinct vertices per tile (u8 slots)
@@ -96,6 +99,7 @@ struct BlobLayout {
   int copy = 0;            // bytes a kernel copies per tile (multiple of 16, <= bytes)
   int rec = 0;             // byte offset of the per-tet records
   bool material = false;   // records carry per-tet Lame parameters
+  bool planes = false;     // per-tet data as field planes instead of row records
 };
 
 // Partial-sum index of the ordered tiled variant (EBB_REDUCE_TILED_ORDERED):
@@ -188,6 +192,7 @@ struct ebb_rel_s {
   signed char tuned[2][2] = {{-1, -1}, {-1, -1}};  // autotuned reduce per [model][precision], -1 none
   int test_drop_tile = -1;              // EBB_MAP_TEST_DROP_TILE: tile whose blob copy the next map skips
   bool stage_interleaved = false;       // FP32 tiled maps stage operands vertex-interleaved (autotuned)
+  bool rec_planes = false;              // tile blobs hold per-tet data as planes (autotuned)
   ebb::VertexIndex vindex;
   void* gather_corner[2] = {nullptr, nullptr};  // EBB_REDUCE_GATHER per-corner buffers, [0] FP32, [1] FP64
   ebb::EdgeIndex edges;                 // built with EBB_FINALIZE_EDGES
@@ -259,6 +264,9 @@ ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector
 void free_layout(ebb_rel_s* tets);
 // Re-cut the tiles with at most `cap` tets each and repack the blobs.
 ebb_status_t rebuild_tiles(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap);
+// Rewrite the per-tet part of every blob in the record layout `planes`
+// (the tiles stay as they are).
+ebb_status_t repack_records(ebb_ctx_s* ctx, ebb_rel_s* tets, bool planes);
 
 // Step VJP (cg.cu) and its adjoint element map (adjoint.cu).
 ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const void* pinned,

@@ -116,41 +116,57 @@ cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
   return cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, st);
 }
 
-BlobLayout make_layout(size_t elem, bool material) {
+// Blob layout for one precision.  The stride between blobs (and a ring
+// stage) holds the larger of the two record layouts, so that switching
+// between them needs no reallocation; a kernel copies only what the chosen
+// layout uses (planes without per-tet material stop after the V plane).
+BlobLayout make_layout(size_t elem, bool material, bool planes) {
   BlobLayout L;
   L.rec = kBlobPrefix;
   L.material = material;
+  L.planes = planes;
   const int rl = elem == 4 ? rec_len<float>() : rec_len<double>();
-  const int end = L.rec + (int)(kTileTets * rl * elem);
+  const int rows_end = L.rec + (int)(kTileTets * rl * elem);
+  const int planes_end = L.rec + (int)(kTileTets * (material ? 12 : 10) * elem);
+  const int end = planes ? planes_end : rows_end;
   L.copy = (end + 15) / 16 * 16;
-  L.bytes = (end + 127) / 128 * 128;
+  L.bytes = (std::max(rows_end, L.rec + (int)(kTileTets * 12 * elem)) + 127) / 128 * 128;
   return L;
 }
 
-// One CTA per tile: copy the integer prefix, then gather the tile's per-tet
-// element-precision values from the planar streams into the tets' records
-// (zero past the tile end).
+// One CTA per tile: copy the integer prefix (unless `prefix` is null: the
+// blob holds it already), then gather the tile's per-tet element-precision
+// values from the planar streams into the records (zero past the tile end).
 template <typename T>
 __global__ void pack_blob_kernel(int nt, const unsigned char* __restrict__ prefix, TetStreams<T> s, BlobLayout L,
                                  unsigned char* blob) {
   const int tile = blockIdx.x;
   unsigned char* b = blob + (size_t)tile * L.bytes;
-  const int4* src = reinterpret_cast<const int4*>(prefix + (size_t)tile * kBlobPrefix);
-  int4* dst = reinterpret_cast<int4*>(b);
-  for (int i = threadIdx.x; i < kBlobPrefix / 16; i += blockDim.x) dst[i] = src[i];
-  const int4 hdr = src[0];
+  if (prefix != nullptr) {
+    const int4* src = reinterpret_cast<const int4*>(prefix + (size_t)tile * kBlobPrefix);
+    int4* dst = reinterpret_cast<int4*>(b);
+    for (int i = threadIdx.x; i < kBlobPrefix / 16; i += blockDim.x) dst[i] = src[i];
+  }
+  const int4 hdr = prefix != nullptr ? reinterpret_cast<const int4*>(prefix + (size_t)tile * kBlobPrefix)[0]
+                                     : reinterpret_cast<const int4*>(b)[0];
   const int ntets = hdr.x, tb = hdr.z;
-  constexpr int RL = rec_len<T>();
   T* R = reinterpret_cast<T*>(b + L.rec);
   for (int i = threadIdx.x; i < kTileTets; i += blockDim.x) {
     const bool in = i < ntets;
     const int t = tb + i;
-    T* r = R + (size_t)RL * i;
-    for (int k = 0; k < 9; ++k) r[k] = in ? s.B[(size_t)k * nt + t] : T(0);
-    r[9] = in ? s.V[t] : T(0);
-    r[10] = (in && L.material) ? s.mu[t] : T(0);
-    r[11] = (in && L.material) ? s.lam[t] : T(0);
-    for (int k = 12; k < RL; ++k) r[k] = T(0);
+    T v[12];
+    for (int k = 0; k < 9; ++k) v[k] = in ? s.B[(size_t)k * nt + t] : T(0);
+    v[9] = in ? s.V[t] : T(0);
+    v[10] = (in && L.material) ? s.mu[t] : T(0);
+    v[11] = (in && L.material) ? s.lam[t] : T(0);
+    if (L.planes) {
+      for (int k = 0; k < 12; ++k) R[(size_t)k * kTileTets + i] = v[k];
+    } else {
+      constexpr int RL = rec_len<T>();
+      T* r = R + (size_t)RL * i;
+      for (int k = 0; k < 12; ++k) r[k] = v[k];
+      for (int k = 12; k < RL; ++k) r[k] = T(0);
+    }
   }
 }
 
@@ -466,6 +482,23 @@ ebb_status_t rebuild_tiles(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap) {
   return build_tile_blobs(ctx, tets, prefix);
 }
 
+ebb_status_t repack_records(ebb_ctx_s* ctx, ebb_rel_s* tets, bool planes) {
+  Tiles& tl = tets->tiles;
+  tets->rec_planes = planes;
+  if (tl.ntiles == 0) return EBB_OK;
+  const bool material = tets->s64.mu != nullptr;
+  tl.L32 = make_layout(sizeof(float), material, planes);
+  tl.L64 = make_layout(sizeof(double), material, planes);
+  const int nt = (int)tets->size;
+  pack_blob_kernel<float><<<tl.ntiles, 256, 0, ctx->stream>>>(nt, nullptr, tets->s32, tl.L32, tl.blob32);
+  pack_blob_kernel<double><<<tl.ntiles, 256, 0, ctx->stream>>>(nt, nullptr, tets->s64, tl.L64, tl.blob64);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "repacking tile records");
+  ++tets->layout_gen;
+  return EBB_OK;
+}
+
 ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<unsigned char>& prefix) {
   Tiles& tl = tets->tiles;
   const int ntiles = tl.ntiles;
@@ -505,8 +538,8 @@ ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector
     }
   }
   const bool material = tets->s64.mu != nullptr;
-  tl.L32 = make_layout(sizeof(float), material);
-  tl.L64 = make_layout(sizeof(double), material);
+  tl.L32 = make_layout(sizeof(float), material, tets->rec_planes);
+  tl.L64 = make_layout(sizeof(double), material, tets->rec_planes);
   unsigned char* dprefix = nullptr;
   cudaError_t e = upload(&dprefix, prefix, st);
   if (e == cudaSuccess) e = cudaMalloc(&tl.blob32, (size_t)ntiles * tl.L32.bytes);

@@ -23,6 +23,7 @@
 #include <cstdint>
 
 #include "async_copy.cuh"
+#include "coop.cuh"
 #include "ebb_internal.h"
 #include "element.cuh"
 #include "tet_io.cuh"
@@ -481,12 +482,31 @@ cudaError_t launch_gather(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, con
   return cudaGetLastError();
 }
 
+// The cooperative variant: three lanes per tet (coop.cuh), atomic scatter.
+template <typename T, int MODEL, int OPS>
+cudaError_t launch_coop(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, const int* active, cudaStream_t stream) {
+  const int nt = (int)rel->size, nv = (int)rel->verts->size;
+  const int grid = (nt + kCoopTetsPerBlock - 1) / kCoopTetsPerBlock;
+  if (io.aos) {
+    if constexpr (sizeof(T) == 4) {
+      tet_coop_kernel<T, MODEL, OPS, true><<<grid, kCoopThreads, 0, stream>>>(
+          nt, nv, rel->keys, rel->tet_perm, streams_of<T>(rel, false), mu0, lam0, io, active, rel->ctx->d_err);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
+  tet_coop_kernel<T, MODEL, OPS, false><<<grid, kCoopThreads, 0, stream>>>(
+      nt, nv, rel->keys, rel->tet_perm, streams_of<T>(rel, false), mu0, lam0, io, active, rel->ctx->d_err);
+  return cudaGetLastError();
+}
+
 template <typename T, int MODEL, int OPS>
 cudaError_t dispatch_reduce(ebb_rel_s* rel, ebb_reduce_t reduce, T mu0, T lam0, const MapIO<T>& io,
                             const int* active, cudaStream_t stream) {
   const int nt = (int)rel->size;
   const int nv = (int)rel->verts->size;
   int* err = rel->ctx->d_err;
+  if (reduce == EBB_REDUCE_COOP) return launch_coop<T, MODEL, OPS>(rel, mu0, lam0, io, active, stream);
   if (reduce == EBB_REDUCE_COLOR) {
     const Colouring& col = rel->colour;
     const TetStreams<T>& s = streams_of<T>(rel, true);

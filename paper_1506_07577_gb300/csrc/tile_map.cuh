@@ -323,10 +323,17 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
           }
         }
       }
-      // The tet's record: Dm^-1, V, mu, lambda in three (FP32) or six (FP64)
-      // 16-byte loads.
+      // The tet's Dm^-1, V, mu, lambda: from its row record in three (FP32)
+      // or six (FP64) 16-byte loads, or from the field planes.
       T rec[12];
-      if constexpr (sizeof(T) == 4) {
+      if (L.planes) {
+        // per-field planes: one coalesced load per field
+        const T* R = reinterpret_cast<const T*>(st + L.rec) + tid;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) rec[k] = R[k * TT];
+        rec[10] = L.material ? R[10 * TT] : T(0);
+        rec[11] = L.material ? R[11 * TT] : T(0);
+      } else if constexpr (sizeof(T) == 4) {
         const float4* R = reinterpret_cast<const float4*>(st + L.rec) + 3 * tid;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

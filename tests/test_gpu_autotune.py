@@ -30,16 +30,20 @@ def test_autotune_report_and_parity(prec):
         dm.vertex_field("w", dt, value=w)
         rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(abi.EBB_NEOHOOKEAN, precision=p))
         cands = [(rep.cand[i].reduce, rep.cand[i].tile_tets, rep.cand[i].us) for i in range(rep.ncand)]
-        # tiled at 3 tile sizes (FP32: staged interleaved, plus in place at the best size), atomic, gather,
-        # colour
-        assert rep.ncand == (7 if prec == "f32" else 6)
+        # tiled at 3 tile sizes with row records (FP32: then staged interleaved at the best size), the
+        # best tiled configuration with plane records, atomic, gather, cooperative, colour
+        assert rep.ncand == (9 if prec == "f32" else 8)
         assert {c[0] for c in cands} == {abi.EBB_REDUCE_TILED, abi.EBB_REDUCE_ATOMIC, abi.EBB_REDUCE_GATHER,
-                                         abi.EBB_REDUCE_COLOR}
-        staged = [rep.cand[i].us for i in range(rep.ncand) if rep.cand[i].interleaved]
+                                         abi.EBB_REDUCE_COOP, abi.EBB_REDUCE_COLOR}
+        tiled_c = [rep.cand[i] for i in range(rep.ncand) if rep.cand[i].reduce == abi.EBB_REDUCE_TILED]
+        staged = [c.us for c in tiled_c if c.interleaved and not c.record_planes]
         assert len(staged) == (1 if prec == "f32" else 0)
-        in_place = [rep.cand[i].us for i in range(rep.ncand)
-                    if rep.cand[i].reduce == abi.EBB_REDUCE_TILED and not rep.cand[i].interleaved]
+        in_place = [c.us for c in tiled_c if not c.interleaved and not c.record_planes]
+        assert len(in_place) == 3
         assert rep.interleaved == (1 if staged and staged[0] < min(in_place) else 0)
+        planes = [c.us for c in tiled_c if c.record_planes]
+        assert len(planes) == 1
+        assert rep.record_planes == (1 if planes[0] < min(in_place + staged) else 0)
         assert {c[1] for c in cands if c[0] == abi.EBB_REDUCE_TILED} == {128, 96, 64}
         assert all(c[2] > 0 for c in cands)
         best = min(cands, key=lambda c: c[2])
@@ -129,10 +133,57 @@ def test_set_tuning_rejects_bad_values():
         for args in ((abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED, 0, 0),
                      (abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED, 129, 0),
                      (abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_AUTO, 128, 0),
-                     (abi.EBB_STVK, 7, abi.EBB_REDUCE_TILED, 128, 0)):
+                     (abi.EBB_STVK, 7, abi.EBB_REDUCE_TILED, 128, 0),
+                     (abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED, 128, 4)):
             with pytest.raises(abi.EbbError) as ei:
                 abi.ebb_relation_set_tuning(dm.ctx, dm.tets, *args)
             assert ei.value.status == abi.EBB_ERR_ARG
         with pytest.raises(abi.EbbError) as ei:   # finalized without colouring
             abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_STVK, abi.EBB_PREC_F32, abi.EBB_REDUCE_COLOR, 128, 0)
         assert ei.value.status == abi.EBB_ERR_STATE
+
+
+@pytest.mark.parametrize("model", ["stvk", "nh"])
+@pytest.mark.parametrize("per_tet", [True, False])
+def test_record_planes_match_oracle(model, per_tet):
+    """Tile blobs with per-tet data as field planes (SoA) instead of row
+    records (AoSoA): every map in both precisions, with and without per-tet
+    material, on tiles of 128 and 37 tets."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(6, model, seed=37, per_tet=per_tet)
+    f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
+    mdl = abi.EBB_STVK if model == "stvk" else abi.EBB_NEOHOOKEAN
+    mu0, lam0 = (0.0, 0.0) if per_tet else (mu, lam)
+    with DeviceTetMesh(m.X, m.tets, mu if per_tet else None, lam if per_tet else None) as dm:
+        for tile in (128, 37):
+            for prec, dt, tol in ((abi.EBB_PREC_F64, torch.float64, 1e-12), (abi.EBB_PREC_F32, torch.float32, 1e-5)):
+                abi.ebb_relation_set_tuning(dm.ctx, dm.tets, mdl, prec, abi.EBB_REDUCE_TILED, tile,
+                                            abi.EBB_TUNE_RECORD_PLANES)
+                assert abi.ebb_relation_info(dm.ctx, dm.tets).record_planes == 1
+                dm.vertex_field("u", dt, value=u)
+                dm.vertex_field("w", dt, value=w)
+                out = {k: dm.vertex_field(k, dt) for k in ("f", "Kw", "d")}
+                o = abi.map_opts(mdl, mu0, lam0, prec, abi.EBB_REDUCE_AUTO, abi.EBB_MAP_ZERO_OUT)
+                abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "Kw", o)
+                abi.ebb_map_tet_diagK(dm.ctx, dm.tets, "u", "d", o)
+                abi.ebb_ctx_sync(dm.ctx)
+                got = {k: v.double().cpu().numpy().T for k, v in out.items()}
+                assert rel_err(got["f"], f) < tol and rel_err(got["Kw"], Kw) < tol and rel_err(got["d"], d) < tol
+        # back to row records
+        abi.ebb_relation_set_tuning(dm.ctx, dm.tets, mdl, abi.EBB_PREC_F32, abi.EBB_REDUCE_TILED, 128, 0)
+        assert abi.ebb_relation_info(dm.ctx, dm.tets).record_planes == 0
+
+
+def test_autotune_reports_both_record_layouts():
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(8, "nh", seed=39)
+    with DeviceTetMesh(m.X, m.tets, mu, lam) as dm:
+        dm.vertex_field("u", torch.float64, value=u)
+        dm.vertex_field("w", torch.float64, value=w)
+        rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w",
+                                        abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64))
+        tiled = [rep.cand[i] for i in range(rep.ncand) if rep.cand[i].reduce == abi.EBB_REDUCE_TILED]
+        assert {c.record_planes for c in tiled} == {0, 1}
+        assert rep.record_planes == abi.ebb_relation_info(dm.ctx, dm.tets).record_planes

@@ -72,13 +72,13 @@ def test_batched_fp64_equals_single_mesh_steps(model):
     assert len(iters) > 1          # meshes really converge at different iterations
 
 
-@pytest.mark.parametrize("reduce", ["auto", "gather", "ordered"])
+@pytest.mark.parametrize("reduce", ["auto", "gather", "ordered", "coop"])
 def test_batched_mixed_matches_oracle_per_mesh(reduce):
     abi = _abi()
     b = meshgen.cube_grid_batch([3, 6, 4], jitter=0.01, seed=21)
     mu, lam = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
     red = {"auto": abi.EBB_REDUCE_AUTO, "gather": abi.EBB_REDUCE_GATHER,
-           "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
+           "ordered": abi.EBB_REDUCE_TILED_ORDERED, "coop": abi.EBB_REDUCE_COOP}[reduce]
     ub, vb, reps = _batched(b, mu, lam, "nh", abi.EBB_PREC_F32, 1000, 1e-8, reduce=red)
     for m in range(len(b.sides)):
         X, tets, pinned = b.mesh(m)

@@ -46,14 +46,15 @@ def _run_maps(dm, u, w, model, prec, reduce, mu, lam):
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered", "coop"])
 @pytest.mark.parametrize("per_tet", [True, False])
 def test_maps_match_oracle(model, prec, reduce, per_tet):
     abi = _abi()
     m, mu, lam, u, w = problem(6 if per_tet else 7, model, seed=13, per_tet=per_tet)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
-           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED,
+           "coop": abi.EBB_REDUCE_COOP}[reduce]
     with _mesh(m, mu, lam) as dm:
         got = _run_maps(dm, u, w, model, prec, red, mu, lam)
     tol = TOL[prec]

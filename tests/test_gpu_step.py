@@ -56,7 +56,7 @@ def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, re
                               abi.EBB_PREC_F64 if precision == "f64" else abi.EBB_PREC_F32,
                               {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR,
                                "tiled": abi.EBB_REDUCE_TILED, "gather": abi.EBB_REDUCE_GATHER,
-                               "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce],
+                               "ordered": abi.EBB_REDUCE_TILED_ORDERED, "coop": abi.EBB_REDUCE_COOP}[reduce],
                               max_iters, rtol, fail_on_max)
         reps = []
         for _ in range(steps):
@@ -66,7 +66,7 @@ def _gpu_steps(m, mu, lam, model, steps, dt, rho, max_iters, rtol, precision, re
     return u, v, reps
 
 
-@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered"])
+@pytest.mark.parametrize("reduce", ["atomic", "colour", "tiled", "gather", "ordered", "coop"])
 def test_stvk_fp64_step_n8_matches_oracle(reduce):
     """8x8x8 StVK FP64 workload: one step, dt = 1e-3, 50 CG iterations
     (early stop at 1e-14 relative residual)."""
@@ -93,7 +93,8 @@ def test_fp64_multistep_matches_oracle(model):
 
 
 @pytest.mark.parametrize("pin_dtype,reduce", [(torch.uint8, "tiled"), (torch.int32, "tiled"),
-                                              (torch.uint8, "gather"), (torch.uint8, "ordered")])
+                                              (torch.uint8, "gather"), (torch.uint8, "ordered"),
+                                              (torch.uint8, "coop")])
 def test_mixed_nh_steps_match_oracle(pin_dtype, reduce):
     """Mixed precision (FP32 element maps, FP64 CG) neo-Hookean with E
     log-uniform in [1e4, 1e6]: error against the FP64 oracle after 4 steps

@@ -78,11 +78,12 @@ def _check(got, want, tol):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("model", ["stvk", "nh"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("reduce", ["tiled", "ordered", "gather", "atomic"])
+@pytest.mark.parametrize("reduce", ["tiled", "ordered", "gather", "atomic", "coop"])
 def test_high_valence_maps_match_oracle(case, model, prec, reduce):
     abi = _abi()
     red = {"tiled": abi.EBB_REDUCE_TILED, "ordered": abi.EBB_REDUCE_TILED_ORDERED,
-           "gather": abi.EBB_REDUCE_GATHER, "atomic": abi.EBB_REDUCE_ATOMIC}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "atomic": abi.EBB_REDUCE_ATOMIC,
+           "coop": abi.EBB_REDUCE_COOP}[reduce]
     m, mu, lam, u, w, want = _problem(case, model, per_tet=True)
     # the hub vertex really is shared by more tets than a tile holds
     assert np.bincount(m.tets.ravel()).max() > 128
@@ -90,12 +91,13 @@ def test_high_valence_maps_match_oracle(case, model, prec, reduce):
 
 
 @pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("reduce", ["tiled", "ordered", "gather", "atomic"])
+@pytest.mark.parametrize("reduce", ["tiled", "ordered", "gather", "atomic", "coop"])
 def test_high_valence_interleaved_fields_uniform_material(case, reduce):
     """The same on 4-float vector elements (one 16-byte copy and one vector
     atomic per vertex in the tiled kernels), uniform material."""
     abi = _abi()
     red = {"tiled": abi.EBB_REDUCE_TILED, "ordered": abi.EBB_REDUCE_TILED_ORDERED,
-           "gather": abi.EBB_REDUCE_GATHER, "atomic": abi.EBB_REDUCE_ATOMIC}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "atomic": abi.EBB_REDUCE_ATOMIC,
+           "coop": abi.EBB_REDUCE_COOP}[reduce]
     m, mu, lam, u, w, want = _problem(case, "stvk", per_tet=False)
     _check(_run(m, mu, lam, u, w, "stvk", "f32", red, x4=True), want, TOL["f32"])

@@ -21,7 +21,7 @@ def _got(t):
 
 
 @pytest.mark.parametrize("model", ["stvk", "nh"])
-@pytest.mark.parametrize("reduce", ["tiled", "atomic", "colour", "gather", "ordered"])
+@pytest.mark.parametrize("reduce", ["tiled", "atomic", "colour", "gather", "ordered", "coop"])
 @pytest.mark.parametrize("reorder", [False, True])
 def test_x4_maps_match_oracle(model, reduce, reorder):
     abi = _abi()
@@ -29,7 +29,8 @@ def test_x4_maps_match_oracle(model, reduce, reorder):
     m, mu, lam, u, w = problem(6, model, seed=41, permute=reorder)
     f, Kw, d = oracle_maps(m, mu, lam, u, w, model)
     red = {"atomic": abi.EBB_REDUCE_ATOMIC, "colour": abi.EBB_REDUCE_COLOR, "tiled": abi.EBB_REDUCE_TILED,
-           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
+           "gather": abi.EBB_REDUCE_GATHER, "ordered": abi.EBB_REDUCE_TILED_ORDERED,
+           "coop": abi.EBB_REDUCE_COOP}[reduce]
     mdl = abi.EBB_STVK if model == "stvk" else abi.EBB_NEOHOOKEAN
     with DeviceTetMesh(m.X, m.tets, mu, lam, colour=True, reorder_verts=reorder) as dm:
         dm.vertex_field("u", value=u, x4=True)
@@ -78,7 +79,8 @@ def test_x4_layout_rules_and_autotune():
         assert ei.value.status == abi.EBB_ERR_ARG
         rep = abi.ebb_relation_autotune(dm.ctx, dm.tets, "u", "w", abi.map_opts(abi.EBB_NEOHOOKEAN,
                                                                                precision=abi.EBB_PREC_F32))
-        assert rep.interleaved == 1 and rep.ncand == 5   # tiled x3 (fields already interleaved), atomic, gather
+        # tiled x3 (fields already interleaved), tiled with plane records, atomic, gather, cooperative
+        assert rep.interleaved == 1 and rep.ncand == 7
         abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u", "w", "f", "k", o)
         abi.ebb_ctx_sync(dm.ctx)
         assert rel_err(_got(tf), f) < 1e-5
