@@ -483,6 +483,20 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
                                       const ebb_step_params_t* params,
                                       ebb_cg_report_t* report);
 
+/* The same vector-Jacobian product for a caller that already holds the
+ * step's new velocity: `v_next` names an F64 vertex field with v' (for
+ * example from the forward replay of a checkpointed rollout).  The forward
+ * solve is skipped (dv = v' - v); the adjoint solve, the adjoint element map
+ * and the outputs are as in ebb_cg_implicit_step_vjp, which this equals to
+ * the forward solve's tolerance when v_next is that step's result.  Errors as
+ * ebb_cg_implicit_step_vjp; EBB_ERR_ARG for a null v_next, EBB_ERR_PHASE if
+ * v_next overlaps u, v, gu or gv. */
+ebb_status_t ebb_cg_implicit_step_vjp_at(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
+                                         const char* v, const char* v_next, const char* pinned,
+                                         const char* gu, const char* gv, const char* gmu,
+                                         const char* glam, const ebb_step_params_t* params,
+                                         ebb_cg_report_t* report);
+
 /* Batched form: one implicit step for each of many independent meshes
  * stored in one verts/tets relation pair (for example hundreds of small
  * meshes of uneven sizes; the per-mesh step is exactly the one above).

@@ -125,6 +125,8 @@ _SIGS = {
                               C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_vjp": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, C.POINTER(ebb_step_params_t),
                                   C.POINTER(ebb_cg_report_t)], ebb_status_t),
+    "ebb_cg_implicit_step_vjp_at": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, _P, _P, _P, _P,
+                                     C.POINTER(ebb_step_params_t), C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_batched": ([ebb_ctx_t, ebb_rel_t, _P, _P, _P, _P, C.c_int32,
                                       C.POINTER(ebb_step_params_t), C.POINTER(ebb_cg_report_t)], ebb_status_t),
     "ebb_cg_implicit_step_noalloc": ([C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -333,6 +335,15 @@ def ebb_cg_implicit_step_vjp(ctx, tets, u, v, pinned, gu, gv, gmu, glam, params)
     rep = ebb_cg_report_t()
     _check(ctx, _lib.ebb_cg_implicit_step_vjp(ctx, tets, _b(u), _b(v), _b(pinned), _b(gu), _b(gv), _b(gmu),
                                               _b(glam), C.byref(params), C.byref(rep)))
+    return rep
+
+
+def ebb_cg_implicit_step_vjp_at(ctx, tets, u, v, v_next, pinned, gu, gv, gmu, glam, params):
+    """The step VJP with the step's new velocity v_next given (no forward
+    solve)."""
+    rep = ebb_cg_report_t()
+    _check(ctx, _lib.ebb_cg_implicit_step_vjp_at(ctx, tets, _b(u), _b(v), _b(v_next), _b(pinned), _b(gu), _b(gv),
+                                                 _b(gmu), _b(glam), C.byref(params), C.byref(rep)))
     return rep
 
 

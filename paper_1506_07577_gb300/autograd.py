@@ -4,11 +4,14 @@
 backward-Euler steps through ``ebb_cg_implicit_step`` and returns the final
 displacement and velocity as tensors that autograd can differentiate with
 respect to the initial state (u0, v0) and the per-tet Lame parameters
-(mu, lam).  The backward pass calls the library's step VJP
-(``ebb_cg_implicit_step_vjp``) once per step, newest first.  Only every
-``checkpoint_every``-th state is kept in the forward pass; the states inside
-a segment are recomputed from its checkpoint during the backward pass, so
-memory grows with steps / checkpoint_every rather than with steps.
+(mu, lam).  The backward pass calls the library's step VJP once per step,
+newest first.  Only every ``checkpoint_every``-th state is kept in the
+forward pass; the states inside a segment are recomputed from its checkpoint
+during the backward pass, so memory grows with steps / checkpoint_every
+rather than with steps.  Each step's new velocity comes from that replay
+(or from the next checkpoint, or the final state), so the VJP is called in
+its form that takes it (``ebb_cg_implicit_step_vjp_at``) and solves only the
+adjoint system.
 
 The library computes with the per-tet ``mu``/``lambda`` fields that the mesh
 was finalized with; the ``mu``, ``lam`` tensors passed here must be those
@@ -33,6 +36,7 @@ class _ImplicitRollout(torch.autograd.Function):
             abi.ebb_cg_implicit_step(mesh.ctx, mesh.tets, "_ad_u", "_ad_v", pinned, params)
         fctx.mesh, fctx.params, fctx.steps, fctx.every, fctx.pinned = mesh, params, steps, every, pinned
         fctx.ckpts = ckpts
+        fctx.vT = v.clone()
         fctx.n_tets = mu.shape[0]
         return u.clone(), v.clone()
 
@@ -46,6 +50,7 @@ class _ImplicitRollout(torch.autograd.Function):
         glam = mesh.bind_tets("_ad_glam", torch.zeros(fctx.n_tets, dtype=torch.float64, device=ref.device))
         su = mesh.bind("_ad_su", torch.empty_like(ref))
         sv = mesh.bind("_ad_sv", torch.empty_like(ref))
+        vn = mesh.bind("_ad_vn", torch.empty_like(ref))
         for seg in range(len(fctx.ckpts) - 1, -1, -1):
             start = seg * every
             end = min(start + every, steps)
@@ -56,11 +61,14 @@ class _ImplicitRollout(torch.autograd.Function):
                 states.append((su.clone(), sv.clone()))
                 if k < end - 1:
                     abi.ebb_cg_implicit_step(mesh.ctx, mesh.tets, "_ad_su", "_ad_sv", pinned, params)
+            # velocity at the segment's end: the next checkpoint's, or the final one
+            v_end = fctx.ckpts[seg + 1][1] if seg + 1 < len(fctx.ckpts) else fctx.vT
             for k in range(end - 1, start - 1, -1):
                 su.copy_(states[k - start][0])
                 sv.copy_(states[k - start][1])
-                abi.ebb_cg_implicit_step_vjp(mesh.ctx, mesh.tets, "_ad_su", "_ad_sv", pinned, "_ad_gu", "_ad_gv",
-                                             "_ad_gmu", "_ad_glam", params)
+                vn.copy_(states[k + 1 - start][1] if k < end - 1 else v_end)
+                abi.ebb_cg_implicit_step_vjp_at(mesh.ctx, mesh.tets, "_ad_su", "_ad_sv", "_ad_vn", pinned, "_ad_gu",
+                                                "_ad_gv", "_ad_gmu", "_ad_glam", params)
         return None, None, None, None, None, gu.clone(), gv.clone(), gmu.clone(), glam.clone()
 
 

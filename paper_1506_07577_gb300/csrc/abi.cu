@@ -1082,9 +1082,10 @@ ebb_status_t ebb_cg_implicit_step(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
   return run_implicit_step(ctx, tets, (double*)pu, (double*)pv, pp, pdt, &p, report);
 }
 
-ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,
-                                      const char* pinned, const char* gu, const char* gv, const char* gmu,
-                                      const char* glam, const ebb_step_params_t* params, ebb_cg_report_t* report) {
+namespace {
+ebb_status_t step_vjp_entry(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v, const char* v_next,
+                            const char* pinned, const char* gu, const char* gv, const char* gmu, const char* glam,
+                            const ebb_step_params_t* params, ebb_cg_report_t* report) {
   if (!ctx) return EBB_ERR_ARG;
   ctx->last_error.clear();
   if (report) *report = ebb_cg_report_t{0, 0.0, EBB_ERR_ARG};
@@ -1102,18 +1103,20 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
     return set_error(ctx, EBB_ERR_ARG, "unknown reduction variant");
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
-  void *pu = nullptr, *pv = nullptr, *pgu = nullptr, *pgv = nullptr;
+  void *pu = nullptr, *pv = nullptr, *pgu = nullptr, *pgv = nullptr, *pvn = nullptr;
   ebb_status_t s = vertex_field(ctx, tets, u, EBB_F64, 3, &pu);
   if (!s) s = vertex_field(ctx, tets, v, EBB_F64, 3, &pv);
   if (!s) s = vertex_field(ctx, tets, gu, EBB_F64, 3, &pgu);
   if (!s) s = vertex_field(ctx, tets, gv, EBB_F64, 3, &pgv);
+  if (!s && v_next) s = vertex_field(ctx, tets, v_next, EBB_F64, 3, &pvn);
   if (s) return s;
   const size_t bytes = (size_t)tets->verts->size * 3 * 8;
-  const void* all[4] = {pu, pv, pgu, pgv};
-  for (int i = 0; i < 4; ++i)
-    for (int j = i + 1; j < 4; ++j)
+  const void* all[5] = {pu, pv, pgu, pgv, pvn};
+  const int nall = pvn ? 5 : 4;
+  for (int i = 0; i < nall; ++i)
+    for (int j = i + 1; j < nall; ++j)
       if (ranges_overlap(all[i], bytes, all[j], bytes))
-        return set_error(ctx, EBB_ERR_PHASE, "u, v, gu and gv must be four distinct fields");
+        return set_error(ctx, EBB_ERR_PHASE, "u, v, v_next, gu and gv must be distinct fields");
   double* per_tet[2] = {nullptr, nullptr};
   const char* names[2] = {gmu, glam};
   for (int i = 0; i < 2; ++i) {
@@ -1135,8 +1138,26 @@ ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char*
   }
   ebb_step_params_t p = *params;
   p.reduce = reduce;
-  return run_step_vjp(ctx, tets, (const double*)pu, (const double*)pv, pp, pdt, (double*)pgu, (double*)pgv,
-                      per_tet[0], per_tet[1], &p, report);
+  return run_step_vjp(ctx, tets, (const double*)pu, (const double*)pv, (const double*)pvn, pp, pdt, (double*)pgu,
+                      (double*)pgv, per_tet[0], per_tet[1], &p, report);
+}
+}  // namespace
+
+ebb_status_t ebb_cg_implicit_step_vjp(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,
+                                      const char* pinned, const char* gu, const char* gv, const char* gmu,
+                                      const char* glam, const ebb_step_params_t* params, ebb_cg_report_t* report) {
+  return step_vjp_entry(ctx, tets, u, v, nullptr, pinned, gu, gv, gmu, glam, params, report);
+}
+
+ebb_status_t ebb_cg_implicit_step_vjp_at(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,
+                                         const char* v_next, const char* pinned, const char* gu, const char* gv,
+                                         const char* gmu, const char* glam, const ebb_step_params_t* params,
+                                         ebb_cg_report_t* report) {
+  if (!v_next) {
+    if (ctx) return set_error(ctx, EBB_ERR_ARG, "null v_next");
+    return EBB_ERR_ARG;
+  }
+  return step_vjp_entry(ctx, tets, u, v, v_next, pinned, gu, gv, gmu, glam, params, report);
 }
 
 ebb_status_t ebb_cg_implicit_step_batched(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* v,

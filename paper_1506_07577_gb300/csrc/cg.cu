@@ -531,6 +531,11 @@ __global__ void vjp_finish_kernel(int n, double dt, const double* __restrict__ a
   }
 }
 
+// dv = v' - v (a step whose new velocity the caller already holds).
+__global__ void vel_diff_kernel(int n, const double* __restrict__ v_next, const double* __restrict__ v, double* dv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dv[i] = v_next[i] - v[i];
+}
+
 // v += dv; u += dt v.
 __global__ void step_finish_kernel(int n, double dt, const double* __restrict__ y, double* u, double* v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -609,6 +614,7 @@ struct VjpArgs {
   double* gv;     // in: dL/dv', out: dL/dv
   double* gmu;    // per-tet dL/dmu (+=), caller's tet order, may be null
   double* glam;   // per-tet dL/dlambda (+=), may be null
+  const double* v_next;  // the step's new velocity when the caller has it (no forward solve), else null
 };
 
 ebb_status_t ensure_scratch(ebb_ctx_s* ctx, ebb_rel_s* tets) {
@@ -798,7 +804,14 @@ ebb_status_t step_impl(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, double* v, co
       if (launched > prm->max_iters + 2 * kChunk) return cudaSuccess;  // defensive bound
     }
   };
-  e = run_chunks();
+  if (vjp != nullptr && vjp->v_next != nullptr) {
+    // The caller holds the step's new velocity (a forward replay): dv = v' - v
+    // replaces the forward solve.
+    vel_diff_kernel<<<vgrid, 256, 0, st>>>(n, vjp->v_next, v, s->y);
+    e = cudaGetLastError();
+  } else {
+    e = run_chunks();
+  }
   if (e != cudaSuccess) return cuda_check(ctx, e, "CG chunk");
 
   if (vjp != nullptr) {
@@ -903,9 +916,9 @@ ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, doubl
              : step_impl<float, unsigned char>(ctx, tets, u, v, (const unsigned char*)pinned, p, rep);
 }
 
-ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const void* pinned,
-                          ebb_dtype_t pinned_dtype, double* gu, double* gv, double* gmu, double* glam,
-                          const ebb_step_params_t* p, ebb_cg_report_t* rep) {
+ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const double* v_next,
+                          const void* pinned, ebb_dtype_t pinned_dtype, double* gu, double* gv, double* gmu,
+                          double* glam, const ebb_step_params_t* p, ebb_cg_report_t* rep) {
   if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
   if (tets->verts->size == 0) {
     if (rep) rep->status = EBB_OK;
@@ -928,7 +941,7 @@ ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, cons
       return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the step VJP failed");
     }
   }
-  VjpArgs a{gu, gv, gmu, glam};
+  VjpArgs a{gu, gv, gmu, glam, v_next};
   // The forward solve reads u and v only; the finish step is replaced by the
   // adjoint, so neither is written.
   if (pinned_dtype == EBB_I32)

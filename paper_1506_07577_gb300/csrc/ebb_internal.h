@@ -106,7 +106,9 @@ struct BlobLayout {
 // reduction unit i of tile t that adds a vertex's run total (the run's first
 // lane) owns partial row t * kTileTets + i; vertex v's rows are
 // vp_ent[vp_off[v] .. vp_off[v+1]), in increasing row (= tile, then unit)
-// order.
+// order.  (Rows numbered vertex by vertex instead, so that the second pass
+// reads them contiguously, measured slower: the tile pass then loads each
+// run's row index.)
 struct Tiles {
   int ntiles = 0;
   unsigned char* blob32 = nullptr;
@@ -218,7 +220,7 @@ struct MapIO {
   T* f = nullptr;          // force accumulator
   T* Kw = nullptr;         // K w accumulator
   T* d = nullptr;          // diag(K) accumulator
-  // Tiled reduction only: when set, each run total is stored to its partial
+  // Ordered tiled reduction only: each run total is stored to its partial
   // row (NF groups of 4 values: x, y, z, 0) instead of added to the fields.
   T* part = nullptr;
   // Vertex-interleaved operands (library-internal fields only): every field
@@ -269,9 +271,11 @@ ebb_status_t rebuild_tiles(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap);
 ebb_status_t repack_records(ebb_ctx_s* ctx, ebb_rel_s* tets, bool planes);
 
 // Step VJP (cg.cu) and its adjoint element map (adjoint.cu).
-ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const void* pinned,
-                          ebb_dtype_t pinned_dtype, double* gu, double* gv, double* gmu, double* glam,
-                          const ebb_step_params_t* p, ebb_cg_report_t* rep);
+// v_next (may be null): the step's new velocity, which replaces its forward
+// solve.
+ebb_status_t run_step_vjp(ebb_ctx_s* ctx, ebb_rel_s* tets, const double* u, const double* v, const double* v_next,
+                          const void* pinned, ebb_dtype_t pinned_dtype, double* gu, double* gv, double* gmu,
+                          double* glam, const ebb_step_params_t* p, ebb_cg_report_t* rep);
 cudaError_t launch_adjoint_map(ebb_rel_s* rel, double mu0, double lam0, const double* u, const double* lv,
                                const double* w, double* acc_kl, double* acc_xq, double* gmu, double* glam, double dt,
                                cudaStream_t st);

@@ -259,7 +259,7 @@ partial_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ 
 
 // ---- tiled (machinery in tile_map.cuh) ------------------------------------
 // The standalone map: one pass over fresh rings.
-template <typename T, int MODEL, int OPS, bool AOS>
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 2)
 tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, BlobLayout L,
                 const int* __restrict__ perm, T mu0, T lam0, MapIO<T> io, const int* active, int* err,
@@ -272,19 +272,19 @@ tet_tile_kernel(int ntiles, int nv, const unsigned char* __restrict__ blobs, Blo
   const TileView<T, OPS> V = tile_view<T, OPS>(smem, L);
   tile_init(V);
   __syncthreads();
-  tile_map_pass<T, MODEL, OPS, AOS>(V, n_my, 0, nv, blobs, L, perm, mu0, lam0, io, err, drop_tile, wait_cycles);
+  tile_map_pass<T, MODEL, OPS, AOS, ORD>(V, n_my, 0, nv, blobs, L, perm, mu0, lam0, io, err, drop_tile, wait_cycles);
 }
 
 
-template <typename T, int MODEL, int OPS, bool AOS>
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD>
 struct TileLaunchCfg {
   static size_t smem;
   static int grid_per_sm;
 };
-template <typename T, int MODEL, int OPS, bool AOS>
-size_t TileLaunchCfg<T, MODEL, OPS, AOS>::smem = 0;
-template <typename T, int MODEL, int OPS, bool AOS>
-int TileLaunchCfg<T, MODEL, OPS, AOS>::grid_per_sm = 0;
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD>
+size_t TileLaunchCfg<T, MODEL, OPS, AOS, ORD>::smem = 0;
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD>
+int TileLaunchCfg<T, MODEL, OPS, AOS, ORD>::grid_per_sm = 0;
 
 int sm_count() {
   static int n = 0;
@@ -297,13 +297,19 @@ int sm_count() {
   return n;
 }
 
-template <typename T, int MODEL, int OPS, bool AOS = false>
-cudaError_t configure_tiles() {
-  cudaError_t e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS, AOS>,
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD>
+cudaError_t configure_tiles_one() {
+  cudaError_t e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS, AOS, ORD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS, AOS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             100);
+    e = cudaFuncSetAttribute(tet_tile_kernel<T, MODEL, OPS, AOS, ORD>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
+}
+template <typename T, int MODEL, int OPS, bool AOS = false>
+cudaError_t configure_tiles() {
+  cudaError_t e = configure_tiles_one<T, MODEL, OPS, AOS, false>();
+  if (e == cudaSuccess) e = configure_tiles_one<T, MODEL, OPS, AOS, true>();
   return e;
 }
 
@@ -338,17 +344,17 @@ const BlobLayout& layout_of<float>(const Tiles& tl) { return tl.L32; }
 template <>
 const BlobLayout& layout_of<double>(const Tiles& tl) { return tl.L64; }
 
-template <typename T, int MODEL, int OPS, bool AOS>
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD = false>
 cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, const int* active,
                          cudaStream_t stream) {
   const Tiles& tl = rel->tiles;
   if (tl.ntiles == 0) return cudaSuccess;
   const BlobLayout& L = layout_of<T>(tl);
   const size_t smem = TileSmem<T, OPS>::bytes(L);
-  using Cfg = TileLaunchCfg<T, MODEL, OPS, AOS>;
+  using Cfg = TileLaunchCfg<T, MODEL, OPS, AOS, ORD>;
   if (Cfg::smem != smem) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tet_tile_kernel<T, MODEL, OPS, AOS>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tet_tile_kernel<T, MODEL, OPS, AOS, ORD>,
                                                                   kTileThreads, smem);
     if (e != cudaSuccess) return e;
     Cfg::grid_per_sm = per_sm > 0 ? per_sm : 1;
@@ -357,7 +363,7 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
   int grid = Cfg::grid_per_sm * sm_count();
   if (grid > tl.ntiles) grid = tl.ntiles;
   const int drop = rel->test_drop_tile;
-  tet_tile_kernel<T, MODEL, OPS, AOS><<<grid, kTileThreads, smem, stream>>>(
+  tet_tile_kernel<T, MODEL, OPS, AOS, ORD><<<grid, kTileThreads, smem, stream>>>(
       tl.ntiles, (int)rel->verts->size, blob_of<T>(tl), L, rel->tet_perm, mu0, lam0, io, active, rel->ctx->d_err,
       drop, drop >= 0 ? kTestWaitCycles : kWaitCycles);
   return cudaGetLastError();
@@ -397,7 +403,7 @@ cudaError_t launch_tiles_ordered(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& 
   MapIO<T> pio = io;
   cudaError_t e = partial_buffer<T>(rel, stream, &pio.part);
   if (e != cudaSuccess) return e;
-  e = launch_tiles<T, MODEL, OPS, AOS>(rel, mu0, lam0, pio, active, stream);
+  e = launch_tiles<T, MODEL, OPS, AOS, true>(rel, mu0, lam0, pio, active, stream);
   if (e != cudaSuccess) return e;
   T* outs[3] = {nullptr, nullptr, nullptr};
   int f = 0;

@@ -168,7 +168,9 @@ __device__ __forceinline__ void tile_init(const TileView<T, OPS>& V) {
 // abort flag (the timeout is raised in `err`; the producer has drained its
 // copies).  AOS: vertex-interleaved operands (MapIO::aos): the producer
 // copies each vertex's 16 bytes with one cp.async, the reduction adds each
-// vertex's three components with one vector atomic.
+// vertex's three components with one vector atomic.  ORD: the ordered
+// variant, each run total stored to its partial row (MapIO::part) instead
+// of added into the fields.
 // Partial row of reduction unit `unit` in this CTA's j-th tile (ordered
 // tiled variant).
 __device__ __forceinline__ size_t part_row(int j, int G, int unit) {
@@ -183,7 +185,7 @@ __device__ __forceinline__ void st_part4(double* p, double x, double y, double z
   reinterpret_cast<double2*>(p)[1] = make_double2(z, 0.0);
 }
 
-template <typename T, int MODEL, int OPS, bool AOS>
+template <typename T, int MODEL, int OPS, bool AOS, bool ORD>
 __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_my, int jbase, int nv,
                                               const unsigned char* __restrict__ blobs, const BlobLayout& L,
                                               const int* __restrict__ perm, T mu0, T lam0, const MapIO<T>& io,
@@ -420,7 +422,7 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
       }
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
-        if (io.part != nullptr) {
+        if constexpr (ORD) {
           float* row = reinterpret_cast<float*>(io.part) + part_row(j, G, tid) * 8;
           *reinterpret_cast<float4*>(row) = make_float4(acc[0].x, acc[1].x, acc[2].x, 0.f);
           *reinterpret_cast<float4*>(row + 4) = make_float4(acc[0].y, acc[1].y, acc[2].y, 0.f);
@@ -465,7 +467,7 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
       }
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
-        if (io.part != nullptr) {
+        if constexpr (ORD) {
           T* row = io.part + part_row(j, G, tid) * (4 * NF);
 #pragma unroll
           for (int f = 0; f < NF; ++f) st_part4(row + 4 * f, acc[f], acc[NF + f], acc[2 * NF + f]);

@@ -206,3 +206,43 @@ def test_vjp_rejects_unsupported_forms():
         with pytest.raises(abi.EbbError) as ei:
             abi.ebb_cg_implicit_step_vjp(dm.ctx, dm.tets, "u", "v", None, "gu", "gu", None, None, _params())
         assert ei.value.status == abi.EBB_ERR_PHASE
+
+
+def test_vjp_at_equals_vjp_with_its_own_solve():
+    """The VJP given the step's new velocity (from a forward step) equals the
+    VJP that re-solves the step, to the forward solve's tolerance; and it
+    refuses a v_next that is also an output."""
+    abi = _abi()
+    m, mu, lam = _setup(4, seed=5)
+    u = 0.3 * meshgen.random_displacement(m.X, 4, amp=0.05, seed=5)
+    u[m.pinned] = 0
+    v = 0.2 * meshgen.random_field(m.n_verts, seed=6)
+    v[m.pinned] = 0
+    rng = np.random.default_rng(3)
+    gu_out, gv_out = rng.normal(size=u.shape), rng.normal(size=v.shape)
+    res = []
+    with _mesh(m, mu, lam) as dm:
+        for given in (False, True):
+            dm.vertex_field("u", torch.float64, value=u)
+            dm.vertex_field("v", torch.float64, value=v)
+            tgu = dm.vertex_field("gu", torch.float64, value=gu_out)
+            tgv = dm.vertex_field("gv", torch.float64, value=gv_out)
+            tgmu = dm.bind_tets("gmu", torch.zeros(m.n_tets, dtype=torch.float64, device=dm.device))
+            tglam = dm.bind_tets("glam", torch.zeros(m.n_tets, dtype=torch.float64, device=dm.device))
+            if given:
+                # the step's result from a forward step on copies of the state
+                dm.vertex_field("u1", torch.float64, value=u)
+                vn = dm.vertex_field("vn", torch.float64, value=v)
+                abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u1", "vn", "pinned", _params())
+                abi.ebb_cg_implicit_step_vjp_at(dm.ctx, dm.tets, "u", "v", "vn", "pinned", "gu", "gv", "gmu",
+                                                "glam", _params())
+                with pytest.raises(abi.EbbError) as ei:
+                    abi.ebb_cg_implicit_step_vjp_at(dm.ctx, dm.tets, "u", "v", "gu", "pinned", "gu", "gv", None,
+                                                    None, _params())
+                assert ei.value.status == abi.EBB_ERR_PHASE
+            else:
+                abi.ebb_cg_implicit_step_vjp(dm.ctx, dm.tets, "u", "v", "pinned", "gu", "gv", "gmu", "glam",
+                                             _params())
+            res.append([t.cpu().numpy().copy() for t in (tgu, tgv, tgmu, tglam)])
+    for a, b in zip(res[1], res[0]):
+        assert rel_err(a, b) < 1e-12
