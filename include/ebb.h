@@ -291,7 +291,15 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * copies are complete.  Each host buffer holds exactly its field's bytes in
  * the field's layout (3 planes of N_v values, or N_v EBB_F32X4 elements);
  * page-locked host memory lets the copies run at full speed, pageable memory
- * works more slowly.  The host buffers are borrowed for the call only; the
+ * works more slowly.  With the tiled reduction on fields the map reads in
+ * place, and at least 16 tiles, the call runs in 8 consecutive tile chunks:
+ * the rows chunk c reads are copied in on one library stream, its tiles are
+ * mapped on the context's stream as soon as they have landed, and the rows
+ * no later chunk adds to are copied out on another library stream, so the
+ * copies overlap the map (fully so when consecutive tiles touch nearly
+ * consecutive rows, as after EBB_FINALIZE_RENUMBER_VERTS).  The chunk plan
+ * is built on the first such call after finalize or a re-tiling (a copy of
+ * the internal keys to the host).  The host buffers are borrowed for the call only; the
  * device fields keep the copied and computed values afterwards.  Errors: as
  * ebb_map_tet_force_Kv (checked before anything is copied); EBB_ERR_ARG for
  * a null host buffer (with N_v > 0); EBB_ERR_PHASE if the device fields u

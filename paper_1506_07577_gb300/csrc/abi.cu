@@ -101,12 +101,29 @@ __global__ void copy_material_kernel(int nt, const int* __restrict__ perm, const
   lam32[t] = (float)l;
 }
 
+void free_host_plan(ebb_rel_s* r) {
+  HostPlan* p = r->hplan;
+  if (!p) return;
+  for (int c = 0; c < HostPlan::kChunks; ++c) {
+    if (p->ev_in[c]) cudaEventDestroy(p->ev_in[c]);
+    if (p->ev_map[c]) cudaEventDestroy(p->ev_map[c]);
+  }
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_end) cudaEventDestroy(p->ev_end);
+  if (p->s_in) cudaStreamDestroy(p->s_in);
+  if (p->s_out) cudaStreamDestroy(p->s_out);
+  delete p;
+  r->hplan = nullptr;
+}
+
 void free_tet_data(ebb_rel_s* r) {
+  free_host_plan(r);
   cudaFree(r->keys);
   r->keys = nullptr;
   cudaFree(r->vperm);
   r->vperm = nullptr;
   r->vorder.clear();
+  r->vown = -1;
   for (void*& p : r->vscratch) {
     cudaFree(p);
     p = nullptr;
@@ -568,7 +585,16 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
     if (!hbatch.empty())
       return set_error(ctx, EBB_ERR_ARG, "renumbering vertices cannot be combined with verts.batch");
     std::vector<int> vp, vinv(nv);
-    vertex_morton_order(hX, vp);
+    if (renumber) {
+      // rows grouped by the chunks of the host-buffer map (Morton-ordered
+      // tets cut into tiles), so that its copies of one chunk's rows
+      // overlap the map of another
+      int own = nv;
+      chunked_vertex_order(packed, hX, tets->tile_cap, HostPlan::kChunks, vp, &own);
+      tets->vown = own;
+    } else {
+      vertex_morton_order(hX, vp);
+    }
     for (int i = 0; i < nv; ++i) vinv[vp[i]] = i;
     for (int t = 0; t < nt; ++t)
       packed[t] = make_int4(vinv[packed[t].x], vinv[packed[t].y], vinv[packed[t].z], vinv[packed[t].w]);
@@ -698,6 +724,160 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, 
   return run_map(ctx, tets, mc, OP_FORCE | OP_KV, opts);
 }
 
+extern "C++" {
+namespace {
+
+// The chunk plan of `tets` for its current tiles (built on first use and
+// after the tiles change).
+ebb_status_t host_plan(ebb_ctx_s* ctx, ebb_rel_s* tets, HostPlan** out) {
+  HostPlan* p = tets->hplan;
+  if (p && p->gen == tets->layout_gen) {
+    *out = p;
+    return EBB_OK;
+  }
+  if (!p) {
+    p = new HostPlan();
+    tets->hplan = p;
+    cudaError_t e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_end, cudaEventDisableTiming);
+    for (int c = 0; c < HostPlan::kChunks && e == cudaSuccess; ++c) {
+      e = cudaEventCreateWithFlags(&p->ev_in[c], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_map[c], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      free_host_plan(tets);
+      return cuda_check(ctx, e, "host-map streams");
+    }
+  }
+  const Tiles& tl = tets->tiles;
+  const int nt = (int)tets->size, nv = (int)tets->verts->size, ntiles = tl.ntiles;
+  std::vector<int4> hdr(ntiles), keys(nt);
+  cudaError_t e = cudaMemcpy2DAsync(hdr.data(), sizeof(int4), tl.blob32, tl.L32.bytes, sizeof(int4), ntiles,
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(keys.data(), tets->keys, sizeof(int4) * nt, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "host-map plan");
+  const int K = std::min(HostPlan::kChunks, ntiles);
+  p->K = K;
+  p->tile_off.assign(K + 1, 0);
+  p->need_hi.assign(K, 0);
+  p->done_lo.assign(K, nv);
+  // per chunk: the lowest and one past the highest row below `own` it touches
+  const int own0 = tets->vown >= 0 ? tets->vown : nv;
+  std::vector<int> lo_own(K, own0), hi_own(K, 0);
+  for (int c = 0; c < K; ++c) {
+    p->tile_off[c + 1] = (int)((long long)(c + 1) * ntiles / K);
+    const int r0 = hdr[p->tile_off[c]].z;
+    const int r1 = hdr[p->tile_off[c + 1] - 1].z + hdr[p->tile_off[c + 1] - 1].x;
+    for (int t = r0; t < r1; ++t) {
+      const int k4[4] = {keys[t].x, keys[t].y, keys[t].z, keys[t].w};
+      for (int a = 0; a < 4; ++a)
+        if (k4[a] < own0) {
+          lo_own[c] = std::min(lo_own[c], k4[a]);
+          hi_own[c] = std::max(hi_own[c], k4[a] + 1);
+        }
+    }
+  }
+  // Rows from `own` on (the vertices several chunks share, on a relation
+  // that renumbered its vertices by chunk) go in before the first chunk and
+  // out after the last; the ranges below cover the rows before them.
+  const int own = tets->vown >= 0 ? tets->vown : nv;
+  p->own = own;
+  for (int c = 0; c < K; ++c) {
+    p->need_hi[c] = std::max(c > 0 ? p->need_hi[c - 1] : 0, std::min(hi_own[c], own));
+    p->done_lo[c] = own;
+  }
+  for (int c = K - 2; c >= 0; --c) p->done_lo[c] = std::min(p->done_lo[c + 1], lo_own[c + 1]);
+  p->gen = tets->layout_gen;
+  *out = p;
+  return EBB_OK;
+}
+
+// Rows [r0, r1) of one vertex field between host and device buffers, as one
+// copy (EBB_F32X4) or one per plane.
+cudaError_t copy_rows(void* dst, const void* src, int r0, int r1, int nv, bool x4, size_t elem, cudaMemcpyKind kind,
+                      cudaStream_t st) {
+  if (r1 <= r0) return cudaSuccess;
+  if (x4) return cudaMemcpyAsync((char*)dst + 16 * (size_t)r0, (const char*)src + 16 * (size_t)r0,
+                                 16 * (size_t)(r1 - r0), kind, st);
+  for (int c = 0; c < 3; ++c) {
+    const size_t off = ((size_t)c * nv + r0) * elem;
+    cudaError_t e = cudaMemcpyAsync((char*)dst + off, (const char*)src + off, (size_t)(r1 - r0) * elem, kind, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The host-buffer map in tile chunks: chunk c's input rows are copied in on
+// one stream, its tiles mapped on the context's stream once they have
+// landed, and the output rows it completes copied out on a third stream,
+// so that the copies of one chunk overlap the map of another.
+template <typename T>
+ebb_status_t host_map_chunked(ebb_ctx_s* ctx, ebb_rel_s* tets, void* const* dev, bool x4, bool same_input,
+                              const void* u_host, const void* w_host, void* f_host, void* Kw_host,
+                              const ebb_map_opts_t* opts, ebb_reduce_t reduce) {
+  HostPlan* P = nullptr;
+  ebb_status_t s = host_plan(ctx, tets, &P);
+  if (s) return s;
+  const int nv = (int)tets->verts->size;
+  const size_t bytes = (size_t)nv * (x4 ? 16 : 3 * sizeof(T));
+  cudaStream_t st = ctx->stream;
+  cudaError_t e = cudaEventRecord(P->ev_start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_in, P->ev_start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_out, P->ev_start, 0);
+  if (e == cudaSuccess && (opts->flags & EBB_MAP_ZERO_OUT)) {
+    e = cudaMemsetAsync(dev[2], 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev[3], 0, bytes, st);
+  }
+  MapIO<T> io;
+  io.u = (const T*)dev[0];
+  io.w = (const T*)dev[1];
+  io.f = (T*)dev[2];
+  io.Kw = (T*)dev[3];
+  io.aos = x4;
+  // the shared rows first
+  if (e == cudaSuccess)
+    e = copy_rows(dev[0], u_host, P->own, nv, nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+  if (e == cudaSuccess && !same_input)
+    e = copy_rows(dev[1], w_host, P->own, nv, nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+  int in_done = 0, out_done = 0;
+  for (int c = 0; c < P->K && e == cudaSuccess; ++c) {
+    e = copy_rows(dev[0], u_host, in_done, P->need_hi[c], nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+    if (e == cudaSuccess && !same_input)
+      e = copy_rows(dev[1], w_host, in_done, P->need_hi[c], nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+    in_done = P->need_hi[c];
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_in[c], P->s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_in[c], 0);
+    io.tile_begin = P->tile_off[c];
+    io.tile_end = P->tile_off[c + 1];
+    if (e == cudaSuccess)
+      e = launch_tet_map<T>(tets, opts->model, OP_FORCE | OP_KV, reduce, (T)opts->mu, (T)opts->lambda, io, nullptr, st);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_map[c], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_out, P->ev_map[c], 0);
+    if (e == cudaSuccess)
+      e = copy_rows(f_host, dev[2], out_done, P->done_lo[c], nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+    if (e == cudaSuccess)
+      e = copy_rows(Kw_host, dev[3], out_done, P->done_lo[c], nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+    out_done = P->done_lo[c];
+  }
+  // the rows before `own` that no chunk touched, and the shared rows, last
+  if (e == cudaSuccess)
+    e = copy_rows(f_host, dev[2], out_done, nv, nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+  if (e == cudaSuccess)
+    e = copy_rows(Kw_host, dev[3], out_done, nv, nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+  if (e == cudaSuccess) e = cudaEventRecord(P->ev_end, P->s_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_end, 0);
+  if (e != cudaSuccess) return cuda_check(ctx, e, "chunked host-buffer map");
+  // Waits for the last copies and reports any device-detected error.
+  return read_device_error(ctx);
+}
+
+}  // namespace
+}  // extern "C++"
+
 ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* w,
                                        const char* f_out, const char* Kw_out, const void* u_host,
                                        const void* w_host, void* f_host, void* Kw_host,
@@ -732,6 +912,18 @@ ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char
   const bool same_input = dev[0] == dev[1] && u_host == w_host;
   if (ranges_overlap(dev[0], bytes, dev[1], bytes) && !same_input)
     return set_error(ctx, EBB_ERR_PHASE, "fields u and w overlap on the device but come from different host buffers");
+  if (opts->model != EBB_STVK && opts->model != EBB_NEOHOOKEAN)
+    return set_error(ctx, EBB_ERR_ARG, "unknown material model");
+  // The tiled map on fields it reads in place runs in chunks that overlap
+  // the copies; every other form copies everything in, maps, copies out.
+  const ebb_reduce_t reduce = resolve_reduce(tets, opts->reduce, opts->model, opts->precision);
+  const bool staged = !x4 && !f64 && tets->stage_interleaved;
+  if (bytes > 0 && reduce == EBB_REDUCE_TILED && !tets->vperm && !staged &&
+      !(opts->flags & EBB_MAP_TEST_DROP_TILE) && tets->tiles.ntiles >= 2 * HostPlan::kChunks) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
+    return f64 ? host_map_chunked<double>(ctx, tets, dev, x4, same_input, u_host, w_host, f_host, Kw_host, opts, reduce)
+               : host_map_chunked<float>(ctx, tets, dev, x4, same_input, u_host, w_host, f_host, Kw_host, opts, reduce);
+  }
   cudaError_t e = cudaSuccess;
   if (bytes > 0) {
     e = cudaMemcpyAsync(dev[0], u_host, bytes, cudaMemcpyHostToDevice, ctx->stream);

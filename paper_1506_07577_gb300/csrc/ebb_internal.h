@@ -155,6 +155,23 @@ struct EdgeIndex {
 };
 
 struct StepScratch;   // defined in cg.cu
+
+// Chunk plan of the host-buffer map (abi.cu): the tiles cut into K
+// consecutive ranges.  Before chunk c runs, the input rows [0, need_hi[c])
+// are on the device; after it, the output rows [0, done_lo[c]) are final (no
+// later chunk adds to them).  On a relation whose vertices are numbered in
+// Morton order consecutive tiles touch nearly consecutive rows, so the
+// copies of one chunk overlap the map of another.
+struct HostPlan {
+  static constexpr int kChunks = 8;
+  unsigned gen = ~0u;
+  int K = 0;
+  std::vector<int> tile_off, need_hi, done_lo;
+  int own = 0;      // rows [own, nv): shared by several chunks (copied in first, out last)
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  cudaEvent_t ev_in[kChunks] = {}, ev_map[kChunks] = {};
+};
 struct BatchScratch;  // defined in batched.cu
 
 struct ebb_rel_impl;
@@ -183,6 +200,7 @@ struct ebb_rel_s {
   int* tet_perm = nullptr;              // internal row -> caller's row
   int* vperm = nullptr;                 // internal vertex -> caller's vertex (null: same order)
   std::vector<int> vorder;              // EBB_FINALIZE_RENUMBER_VERTS: row i was the caller's vertex vorder[i]
+  int vown = -1;                        // rows before the vertices several host-map chunks share (-1: none)
   void* vscratch[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // reordered map operands
   ebb::TetStreams<double> s64;
   ebb::TetStreams<float> s32;
@@ -201,6 +219,7 @@ struct ebb_rel_s {
 
   // ---- implicit-step scratch ----
   ebb::StepScratch* step = nullptr;
+  ebb::HostPlan* hplan = nullptr;       // chunk plan of the host-buffer map (abi.cu)
   ebb::BatchScratch* batch = nullptr;
 };
 
@@ -223,6 +242,10 @@ struct MapIO {
   // Ordered tiled reduction only: each run total is stored to its partial
   // row (NF groups of 4 values: x, y, z, 0) instead of added to the fields.
   T* part = nullptr;
+  // Tiled (unordered) reduction: map only the tiles [tile_begin, tile_end)
+  // (tile_end < 0: to the last tile).
+  int tile_begin = 0;
+  int tile_end = -1;
   // Vertex-interleaved operands (library-internal fields only): every field
   // above is nv groups of 4 (x, y, z, padding) instead of 3 planes; FP32 and
   // the tiled reduction only.
@@ -259,6 +282,22 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
                           const std::vector<double>& X, const std::vector<int>* batch,
                           std::vector<int>& perm, std::vector<int4>& sorted_keys,
                           std::vector<unsigned char>& prefix);
+
+// Morton order of the tet centroids (grouped by the batch id of the first
+// corner when `batch` is given): perm[i] = the caller's row of internal tet i.
+void tet_morton_order(const std::vector<int4>& keys, const std::vector<double>& X, const std::vector<int>* batch,
+                      std::vector<int>& perm);
+// Tile boundaries of the internal tet order (tile t = internal tets
+// [off[t], off[t+1])).
+std::vector<int> tile_cut(const std::vector<int4>& sorted, int nv, int cap);
+// Vertex rows for EBB_FINALIZE_RENUMBER_VERTS: with the tiles cut into
+// `nchunks` consecutive ranges (as the host-buffer map cuts them), the
+// vertices only one chunk touches come first, chunk by chunk, then those
+// several chunks share, then unused ones, each group in order of first use
+// by the Morton-ordered tets; vp[i] = the caller's vertex of row i, *n_own =
+// the number of rows before the shared ones.
+void chunked_vertex_order(const std::vector<int4>& keys, const std::vector<double>& X, int cap, int nchunks,
+                          std::vector<int>& vp, int* n_own);
 
 // Pack the tile blobs (both precisions) from the host prefix and the
 // device-side per-tet streams (layout.cu).

@@ -170,14 +170,16 @@ __global__ void pack_blob_kernel(int nt, const unsigned char* __restrict__ prefi
   }
 }
 
-// Cut the internal tet order into tiles of at most `cap` tets and build each
-// tile's blob prefix; returns the tile count.
-int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<unsigned char>& prefix) {
+}  // namespace
+
+// Tiles: greedy cut of the internal (Morton) tet order.  A tile closes before
+// it would exceed `cap` tets, kTileSlots distinct vertices, kTileTets
+// reduction units (ceil(entries / kUnitEntries) summed over its vertices) or
+// kUnitMaxRun units for one vertex.  The cut depends on which corners share
+// a vertex, not on the vertex numbers.  Returns the tile boundaries
+// (ntiles + 1 entries).
+std::vector<int> tile_cut(const std::vector<int4>& sorted, int nv, int cap) {
   const int nt = (int)sorted.size();
-  // Tiles: greedy cut of the Morton order.  A tile closes before it would
-  // exceed `cap` tets, kTileSlots distinct vertices, kTileTets reduction
-  // units (ceil(entries / kUnitEntries) summed over its vertices) or
-  // kUnitMaxRun units for one vertex.
   std::vector<int> tet_off{0};
   {
     std::vector<int> stamp(nv, -1), count(nv, 0);
@@ -211,6 +213,15 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
     }
     if (tile_tets > 0) tet_off.push_back(nt);
   }
+  return tet_off;
+}
+
+namespace {
+
+// Cut the internal tet order into tiles of at most `cap` tets and build each
+// tile's blob prefix; returns the tile count.
+int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<unsigned char>& prefix) {
+  const std::vector<int> tet_off = tile_cut(sorted, nv, cap);
   const int ntiles = (int)tet_off.size() - 1;
 
   // Blob prefix per tile: slots (numbered by decreasing entry count), the
@@ -382,14 +393,10 @@ void free_layout(ebb_rel_s* tets) {
   tets->tet_perm = nullptr;
 }
 
-ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
-                          const std::vector<double>& X, const std::vector<int>* batch, std::vector<int>& perm,
-                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix) {
+void tet_morton_order(const std::vector<int4>& keys, const std::vector<double>& X, const std::vector<int>* batch,
+                      std::vector<int>& perm) {
   const int nt = (int)keys.size();
   const int nv = (int)(X.size() / 3);
-  cudaStream_t st = ctx->stream;
-
-  // 1. Morton order of centroids.
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
   for (int c = 0; c < 3; ++c) {
     if (nv > 0) {
@@ -416,11 +423,65 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
   }
   std::sort(code.begin(), code.end());
   perm.resize(nt);
-  sorted.resize(nt);
-  for (int i = 0; i < nt; ++i) {
-    perm[i] = std::get<2>(code[i]);
-    sorted[i] = keys[perm[i]];
+  for (int i = 0; i < nt; ++i) perm[i] = std::get<2>(code[i]);
+}
+
+void chunked_vertex_order(const std::vector<int4>& keys, const std::vector<double>& X, int cap, int nchunks,
+                          std::vector<int>& vp, int* n_own) {
+  const int nt = (int)keys.size();
+  const int nv = (int)(X.size() / 3);
+  std::vector<int> tperm;
+  tet_morton_order(keys, X, nullptr, tperm);
+  std::vector<int4> sorted(nt);
+  for (int i = 0; i < nt; ++i) sorted[i] = keys[tperm[i]];
+  const std::vector<int> tet_off = tile_cut(sorted, nv, cap);
+  const int ntiles = (int)tet_off.size() - 1;
+  const int K = std::max(1, std::min(nchunks, ntiles));
+  // first and last chunk of every vertex, and its first tet
+  std::vector<int> fc(nv, -1), lc(nv, -1), first(nv, nt);
+  for (int c = 0; c < K; ++c) {
+    const int t0 = tet_off[(size_t)((long long)c * ntiles / K)];
+    const int t1 = tet_off[(size_t)((long long)(c + 1) * ntiles / K)];
+    for (int t = t0; t < t1; ++t) {
+      const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
+      for (int a = 0; a < 4; ++a) {
+        if (fc[k[a]] < 0) {
+          fc[k[a]] = c;
+          first[k[a]] = t;
+        }
+        lc[k[a]] = c;
+      }
+    }
   }
+  // rows: the vertices of one chunk only, chunk by chunk, then the vertices
+  // several chunks share, then unreferenced ones; each group in the order of
+  // first use
+  std::vector<std::tuple<int, int, int>> key(nv);
+  for (int v = 0; v < nv; ++v) {
+    const int grp = fc[v] < 0 ? K + 1 : (fc[v] == lc[v] ? fc[v] : K);
+    key[v] = std::make_tuple(grp, first[v], v);
+  }
+  std::sort(key.begin(), key.end());
+  vp.resize(nv);
+  int own = 0;
+  for (int i = 0; i < nv; ++i) {
+    vp[i] = std::get<2>(key[i]);
+    if (std::get<0>(key[i]) < K) own = i + 1;
+  }
+  *n_own = own;
+}
+
+ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
+                          const std::vector<double>& X, const std::vector<int>* batch, std::vector<int>& perm,
+                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix) {
+  const int nt = (int)keys.size();
+  const int nv = (int)(X.size() / 3);
+  cudaStream_t st = ctx->stream;
+
+  // 1. Morton order of centroids.
+  tet_morton_order(keys, X, batch, perm);
+  sorted.resize(nt);
+  for (int i = 0; i < nt; ++i) sorted[i] = keys[perm[i]];
 
   // 2. Vertex -> (tet, corner) index in internal order.
   std::vector<int> voff(nv + 1, 0), vent((size_t)4 * nt);

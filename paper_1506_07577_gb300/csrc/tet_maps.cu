@@ -349,6 +349,14 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
                          cudaStream_t stream) {
   const Tiles& tl = rel->tiles;
   if (tl.ntiles == 0) return cudaSuccess;
+  // A tile range is the tiles of a shorter blob array: the kernel indexes
+  // tiles relative to the pointer it gets (the ordered variant's partial
+  // rows are numbered from tile 0, so it always maps every tile).
+  const int t0 = io.tile_begin;
+  const int t1 = io.tile_end < 0 ? tl.ntiles : io.tile_end;
+  if (t0 < 0 || t1 > tl.ntiles || t0 > t1 || (ORD && (t0 != 0 || t1 != tl.ntiles))) return cudaErrorInvalidValue;
+  const int count = t1 - t0;
+  if (count == 0) return cudaSuccess;
   const BlobLayout& L = layout_of<T>(tl);
   const size_t smem = TileSmem<T, OPS>::bytes(L);
   using Cfg = TileLaunchCfg<T, MODEL, OPS, AOS, ORD>;
@@ -361,11 +369,11 @@ cudaError_t launch_tiles(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& io, cons
     Cfg::smem = smem;
   }
   int grid = Cfg::grid_per_sm * sm_count();
-  if (grid > tl.ntiles) grid = tl.ntiles;
+  if (grid > count) grid = count;
   const int drop = rel->test_drop_tile;
   tet_tile_kernel<T, MODEL, OPS, AOS, ORD><<<grid, kTileThreads, smem, stream>>>(
-      tl.ntiles, (int)rel->verts->size, blob_of<T>(tl), L, rel->tet_perm, mu0, lam0, io, active, rel->ctx->d_err,
-      drop, drop >= 0 ? kTestWaitCycles : kWaitCycles);
+      count, (int)rel->verts->size, blob_of<T>(tl) + (size_t)t0 * L.bytes, L, rel->tet_perm, mu0, lam0, io, active,
+      rel->ctx->d_err, drop, drop >= 0 ? kTestWaitCycles : kWaitCycles);
   return cudaGetLastError();
 }
 
