@@ -56,15 +56,17 @@ UNIT = "tets/s"
 L2_FLUSH_BYTES = 256 << 20
 G = (0.0, 0.0, -9.81)
 
-# DRAM bytes (read + write) per launch of the headline kernel from one ncu
-# capture of the headline workload (`--profile` with the same arguments as
-# the main line).  They describe the kernel sources whose hash is given and
-# are reported as null (with a note) once those sources change.
-NCU_TRAFFIC = {"sources_sha256_16": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) per launch of the headline kernel (tiled, tiles
+# of 128 tets) from one ncu capture of the full 128^3 headline workload per
+# record layout (`--profile --n 128 --permute --renumber --model stvk
+# --uniform --x4 [--planes]`).  They describe the kernel sources whose hash
+# is given and are reported as null (with a note) once those sources change.
+NCU_TRAFFIC = {"sources_sha256_16": "393d109df27873ed", "n": 128,
+               "bytes_per_launch": {"rows": 988.79e6, "planes": 903.84e6}}
 # FP64 arithmetic of the FP64 kernels, counted by ncu (2 x DFMA + DADD + DMUL
 # thread instructions per unit) on the 64^3 workload, valid while the map and
 # spring sources hash to the same value.
-NCU_FP64 = {"sources_sha256_16": "dc32b4c70d73aa62", "kv_map_nh_flops_per_tet": 454.8,
+NCU_FP64 = {"sources_sha256_16": "6348968f747c117a", "kv_map_nh_flops_per_tet": 454.8,
             "kv_map_nh_pipe_active": 0.882, "spring_flops_per_directed_spring": 32.15,
             "spring_pipe_active": 0.858}
 # FP64 peak of the part, derived: 2 DFMA (4 flops) per clock per SM x 152 SMs
@@ -1039,19 +1041,26 @@ def run_ours(args, rank, world, local_rank):
     bpt = algorithmic_bytes_per_tet(nv, nt, False)
     kern_s = head["kern_us"] * 1e-6
     achieved = bpt * nt / kern_s / 1e9
-    fresh = NCU_TRAFFIC["sources_sha256_16"] == kernel_sources_hash()
     tune = head["tune"]
+    fresh = NCU_TRAFFIC["sources_sha256_16"] == kernel_sources_hash()
+    captured = fresh and args.n == NCU_TRAFFIC["n"] and tune["reduce"] == "tiled" and tune["tile_tets"] == 128
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": NCU_TRAFFIC["bytes_per_launch"] if fresh else None,
+            "traffic": NCU_TRAFFIC["bytes_per_launch"][tune["records"]] if captured else None,
             "traffic_unit": "bytes per launch (ncu dram read+write)",
             "kernel": {"tiled": "tet_tile_kernel<float, STVK, FORCE|KV, interleaved>",
                        "atomic": "tet_map_kernel<float, STVK, FORCE|KV, atomic, interleaved>",
                        "colour": "tet_map_kernel<float, STVK, FORCE|KV, coloured, interleaved>",
                        "gather": "tet_corner_kernel + vertex_sum_kernel",
-                       "tiled_ordered": "tet_tile_kernel (partial rows) + partial_sum_kernel"}[tune["reduce"]],
+                       "tiled_ordered": "tet_tile_kernel (partial rows) + partial_sum_kernel",
+                       "coop": "tet_coop_kernel<float, STVK, FORCE|KV, interleaved>"}[tune["reduce"]],
             "algorithmic_bytes_per_tet": bpt, "kernel_us": head["kern_us"], "peak_kind": peak_kind}
     if not fresh:
         roof["traffic_note"] = "no ncu capture of the current kernel sources"
+    elif not captured:
+        roof["traffic_note"] = "ncu traffic was captured for the tiled kernel with 128-tet tiles on the 128^3 mesh only"
+    else:
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of the same kernel "
+                                  "and record layout on the same mesh")
     if rank != 0:
         return
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1070,7 +1079,7 @@ def run_ours(args, rank, world, local_rank):
             "clocks": head["clocks"],
             "autotune": tune,
             "layout": {"tiles": head["ntiles"], "colours": head["ncolours"],
-                       "finalize_with_colouring_s": head["setup_s"],
+                       "finalize_renumbered_with_colouring_s": head["setup_s"],
                        "finalize_with_vertex_reorder_s": head["setup_vertex_reorder_s"]},
             "reduction_variants": head["variants"]}
     line.update(sub)

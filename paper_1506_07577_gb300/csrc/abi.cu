@@ -578,6 +578,7 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   // RENUMBER makes the new order the relation's own, for every vertex field
   // bound or read from now on.
   double* X_int = nullptr;
+  std::vector<int> tperm;
   const bool renumber = (flags & EBB_FINALIZE_RENUMBER_VERTS) != 0;
   if ((flags & EBB_FINALIZE_REORDER_VERTS) && renumber)
     return set_error(ctx, EBB_ERR_ARG, "EBB_FINALIZE_REORDER_VERTS and EBB_FINALIZE_RENUMBER_VERTS exclude each other");
@@ -586,11 +587,13 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
       return set_error(ctx, EBB_ERR_ARG, "renumbering vertices cannot be combined with verts.batch");
     std::vector<int> vp, vinv(nv);
     if (renumber) {
+      // The Morton order of the tets depends on their centroids only, which
+      // renumbering the vertices leaves as they are: build_layout reuses it.
       // rows grouped by the chunks of the host-buffer map (Morton-ordered
       // tets cut into tiles), so that its copies of one chunk's rows
       // overlap the map of another
       int own = nv;
-      chunked_vertex_order(packed, hX, tets->tile_cap, HostPlan::kChunks, vp, &own);
+      chunked_vertex_order(packed, hX, tets->tile_cap, HostPlan::kChunks, vp, &own, &tperm);
       tets->vown = own;
     } else {
       vertex_morton_order(hX, vp);
@@ -621,7 +624,8 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   std::vector<int> perm;
   std::vector<int4> sorted;
   std::vector<unsigned char> prefix;
-  s = build_layout(ctx, tets, packed, hX, hbatch.empty() ? nullptr : &hbatch, perm, sorted, prefix);
+  s = build_layout(ctx, tets, packed, hX, hbatch.empty() ? nullptr : &hbatch, perm, sorted, prefix,
+                   tperm.empty() ? nullptr : &tperm);
   if (s) {
     cudaFree(X_int);
     return s;

@@ -3,13 +3,47 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdint>
 #include <map>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "../../include/ebb.h"
 
 namespace ebb {
+
+// Host set-up work split over threads: fn(lo, hi) runs over contiguous
+// ranges covering [0, n), at least `min_chunk` items each, on up to 16 host
+// threads (the calling thread takes the first range; a thread that cannot
+// be started leaves its range to the caller).  fn must only write state of
+// its own range.
+template <class F>
+void parallel_ranges(int n, int min_chunk, F&& fn) {
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nth = std::max(1, std::min({hw > 0 ? hw : 1, 16, n / std::max(1, min_chunk)}));
+  auto lo_of = [&](int i) { return (int)((long long)n * i / nth); };
+  std::vector<std::thread> th;
+  std::vector<int> inline_ranges;
+  for (int i = 1; i < nth; ++i) {
+    try {
+      th.emplace_back([&fn, lo = lo_of(i), hi = lo_of(i + 1)] { fn(lo, hi); });
+    } catch (const std::system_error&) {
+      inline_ranges.push_back(i);
+    }
+  }
+  fn(0, lo_of(1));
+  for (int i : inline_ranges) fn(lo_of(i), lo_of(i + 1));
+  for (auto& t : th) t.join();
+}
+
+// Stable order of `key` (its low `bits` bits): order[i] = the index of the
+// i-th smallest key, equal keys in index order (LSD radix sort, 11-bit
+// digits).  With `order` non-empty on entry, that order is refined instead:
+// the result sorts by key and keeps the given order among equal keys.
+void radix_order(const std::vector<uint64_t>& key, int bits, std::vector<int>& order);
 
 // Device status word: [0] = first error code, [1] = row index it refers to.
 enum { ERRW_CODE = 0, ERRW_INDEX = 1, ERRW_WORDS = 4 };
@@ -274,14 +308,15 @@ ebb_status_t run_implicit_step(ebb_ctx_s* ctx, ebb_rel_s* tets, double* u, doubl
 
 // Morton order, tiles and vertex index from host keys (layout.cu).  `keys`
 // and `X` are the caller's order (X as 3 planes of nv); `batch` (may be null)
-// gives each vertex a group id that orders tets before the Morton code; on return
+// gives each vertex a group id that orders tets before the Morton code
+// (`known_perm`, when given, is that order already); on return
 // `perm[i]` is the caller's row of internal row i, the vertex index and
 // tet_perm of `tets` are on the device, and `prefix` holds the integer part
 // of every tile blob (kBlobPrefix bytes per tile).
 ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
                           const std::vector<double>& X, const std::vector<int>* batch,
                           std::vector<int>& perm, std::vector<int4>& sorted_keys,
-                          std::vector<unsigned char>& prefix);
+                          std::vector<unsigned char>& prefix, const std::vector<int>* known_perm = nullptr);
 
 // Morton order of the tet centroids (grouped by the batch id of the first
 // corner when `batch` is given): perm[i] = the caller's row of internal tet i.
@@ -295,9 +330,11 @@ std::vector<int> tile_cut(const std::vector<int4>& sorted, int nv, int cap);
 // vertices only one chunk touches come first, chunk by chunk, then those
 // several chunks share, then unused ones, each group in order of first use
 // by the Morton-ordered tets; vp[i] = the caller's vertex of row i, *n_own =
-// the number of rows before the shared ones.
+// the number of rows before the shared ones.  With `tperm_out`, also the
+// tets' Morton order (tet_morton_order without batch ids), which renumbering
+// the vertices leaves unchanged.
 void chunked_vertex_order(const std::vector<int4>& keys, const std::vector<double>& X, int cap, int nchunks,
-                          std::vector<int>& vp, int* n_own);
+                          std::vector<int>& vp, int* n_own, std::vector<int>* tperm_out = nullptr);
 
 // Pack the tile blobs (both precisions) from the host prefix and the
 // device-side per-tet streams (layout.cu).

@@ -220,6 +220,31 @@ namespace {
 
 // Cut the internal tet order into tiles of at most `cap` tets and build each
 // tile's blob prefix; returns the tile count.
+// Vertex -> per-tile value (open addressing; a tile holds at most
+// kTileSlots vertices), so that building one tile touches only its own few
+// kilobytes whatever the vertex numbering.
+struct TileVertexMap {
+  static constexpr int kBits = 9;
+  static constexpr int kSize = 1 << kBits;
+  static_assert(kSize >= 2 * kTileSlots, "load factor");
+  int key[kSize];
+  int val[kSize];
+  void clear() { std::fill(key, key + kSize, -1); }
+  // The value of vertex v (>= 0), inserted as -1 when absent.
+  int& operator[](int v) {
+    unsigned h = ((unsigned)v * 2654435761u) >> (32 - kBits);
+    while (key[h] != v) {
+      if (key[h] < 0) {
+        key[h] = v;
+        val[h] = -1;
+        break;
+      }
+      h = (h + 1) & (kSize - 1);
+    }
+    return val[h];
+  }
+};
+
 int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<unsigned char>& prefix) {
   const std::vector<int> tet_off = tile_cut(sorted, nv, cap);
   const int ntiles = (int)tet_off.size() - 1;
@@ -227,12 +252,14 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
   // Blob prefix per tile: slots (numbered by decreasing entry count), the
   // entries grouped by slot, the reduction units and the vertex ids.
   prefix.assign((size_t)ntiles * kBlobPrefix, 0);
-  {
-    std::vector<int> slot_of(nv, -1);
+  // Tiles are independent: host threads take contiguous ranges of them,
+  // each with scratch of its own.
+  parallel_ranges(ntiles, 512, [&](int lo, int hi) {
+    TileVertexMap slot_of;
     std::vector<int> vtx, rk, label, member_off, members;
     std::vector<long> grp_count;
     std::vector<int> cnt(kTileSlots + 1);
-    for (int ti = 0; ti < ntiles; ++ti) {
+    for (int ti = lo; ti < hi; ++ti) {
       unsigned char* b = prefix.data() + (size_t)ti * kBlobPrefix;
       uchar4* slots = reinterpret_cast<uchar4*>(b + kBlobSlots);
       unsigned short* ent = reinterpret_cast<unsigned short*>(b + kBlobEnt);
@@ -240,14 +267,16 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
       int* bvtx = reinterpret_cast<int*>(b + kBlobVtx);
       const int tb = tet_off[ti], te = tet_off[ti + 1];
       vtx.clear();
+      slot_of.clear();
       for (int t = tb; t < te; ++t) {
         const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
         for (int a = 0; a < 4; ++a) {
-          if (slot_of[k[a]] < 0) {
-            slot_of[k[a]] = 0;
+          int& c = slot_of[k[a]];
+          if (c < 0) {
+            c = 0;
             vtx.push_back(k[a]);
           }
-          slot_of[k[a]]++;
+          c++;
         }
       }
       std::stable_sort(vtx.begin(), vtx.end(), [&](int x, int y) { return slot_of[x] > slot_of[y]; });
@@ -352,17 +381,14 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
         while (last + 1 < nunits && uslot[last + 1] == uslot[i] && (last + 1) % 32 != 0) ++last;
         units[i] |= ((uint32_t)(last - i) << 22) | ((uint32_t)head << 26);
       }
-      for (int j = 0; j < nvu; ++j) {
-        bvtx[label[j]] = vtx[j];
-        slot_of[vtx[j]] = -1;
-      }
+      for (int j = 0; j < nvu; ++j) bvtx[label[j]] = vtx[j];
       int* hdr = reinterpret_cast<int*>(b);
       hdr[0] = te - tb;
       hdr[1] = nvu;
       hdr[2] = tb;
       hdr[3] = nunits;
     }
-  }
+  });
 
   return ntiles;
 }
@@ -393,6 +419,62 @@ void free_layout(ebb_rel_s* tets) {
   tets->tet_perm = nullptr;
 }
 
+void radix_order(const std::vector<uint64_t>& key, int bits, std::vector<int>& order) {
+  const int n = (int)key.size();
+  if (order.empty()) {
+    order.resize(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+  }
+  constexpr int kDigit = 11, kBuckets = 1 << kDigit;
+  // Each pass: per-block digit counts, their exclusive sums in (digit,
+  // block) order, then every block scatters its items in item order; the
+  // blocks are fixed ranges of the input, so the result does not depend on
+  // the thread count.
+  const int nblk = std::max(1, std::min(64, n / (1 << 15)));
+  auto blk_lo = [&](int b) { return (int)((long long)n * b / nblk); };
+  std::vector<uint64_t> k0(n), k1(n);
+  std::vector<int> i1(n);
+  for (int i = 0; i < n; ++i) k0[i] = key[order[i]];
+  std::vector<int> count((size_t)nblk * kBuckets);
+  for (int shift = 0; shift < bits; shift += kDigit) {
+    parallel_ranges(nblk, 1, [&](int b0, int b1) {
+      for (int b = b0; b < b1; ++b) {
+        int* c = count.data() + (size_t)b * kBuckets;
+        std::fill(c, c + kBuckets, 0);
+        for (int i = blk_lo(b); i < blk_lo(b + 1); ++i) c[(k0[i] >> shift) & (kBuckets - 1)]++;
+      }
+    });
+    bool moves = true;
+    {
+      const unsigned d0 = n ? (unsigned)((k0[0] >> shift) & (kBuckets - 1)) : 0u;
+      int same = 0;
+      for (int b = 0; b < nblk; ++b) same += count[(size_t)b * kBuckets + d0];
+      moves = same != n;  // one digit value: nothing moves
+    }
+    if (!moves) continue;
+    int run = 0;
+    for (int d = 0; d < kBuckets; ++d)
+      for (int b = 0; b < nblk; ++b) {
+        int& c = count[(size_t)b * kBuckets + d];
+        const int x = c;
+        c = run;
+        run += x;
+      }
+    parallel_ranges(nblk, 1, [&](int b0, int b1) {
+      for (int b = b0; b < b1; ++b) {
+        int* c = count.data() + (size_t)b * kBuckets;
+        for (int i = blk_lo(b); i < blk_lo(b + 1); ++i) {
+          const int d = c[(k0[i] >> shift) & (kBuckets - 1)]++;
+          k1[d] = k0[i];
+          i1[d] = order[i];
+        }
+      }
+    });
+    k0.swap(k1);
+    order.swap(i1);
+  }
+}
+
 void tet_morton_order(const std::vector<int4>& keys, const std::vector<double>& X, const std::vector<int>* batch,
                       std::vector<int>& perm) {
   const int nt = (int)keys.size();
@@ -406,28 +488,34 @@ void tet_morton_order(const std::vector<int4>& keys, const std::vector<double>& 
     }
     if (!(hi[c] > lo[c])) hi[c] = lo[c] + 1.0;
   }
-  // Sort key: (group id, Morton code of the centroid, row).
-  std::vector<std::tuple<int, uint64_t, int>> code(nt);
+  // Order: (group id, Morton code of the centroid, row).
+  std::vector<uint64_t> code(nt);
   const double q = (double)((1u << 21) - 1);
-  for (int t = 0; t < nt; ++t) {
-    const int k[4] = {keys[t].x, keys[t].y, keys[t].z, keys[t].w};
-    uint64_t m = 0;
-    for (int c = 0; c < 3; ++c) {
-      double s = 0.0;
-      for (int a = 0; a < 4; ++a) s += X[(size_t)c * nv + k[a]];
-      double r = (0.25 * s - lo[c]) / (hi[c] - lo[c]);
-      r = r < 0 ? 0 : (r > 1 ? 1 : r);
-      m |= spread3((uint64_t)(r * q)) << c;
+  parallel_ranges(nt, 1 << 16, [&](int t0, int t1) {
+    for (int t = t0; t < t1; ++t) {
+      const int k[4] = {keys[t].x, keys[t].y, keys[t].z, keys[t].w};
+      uint64_t m = 0;
+      for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        for (int a = 0; a < 4; ++a) s += X[(size_t)c * nv + k[a]];
+        double r = (0.25 * s - lo[c]) / (hi[c] - lo[c]);
+        r = r < 0 ? 0 : (r > 1 ? 1 : r);
+        m |= spread3((uint64_t)(r * q)) << c;
+      }
+      code[t] = m;
     }
-    code[t] = std::make_tuple(batch ? (*batch)[k[0]] : 0, m, t);
+  });
+  perm.clear();
+  radix_order(code, 63, perm);
+  if (batch) {
+    // group ids are non-negative (checked at finalize)
+    for (int t = 0; t < nt; ++t) code[t] = (uint32_t)(*batch)[keys[t].x];
+    radix_order(code, 32, perm);
   }
-  std::sort(code.begin(), code.end());
-  perm.resize(nt);
-  for (int i = 0; i < nt; ++i) perm[i] = std::get<2>(code[i]);
 }
 
 void chunked_vertex_order(const std::vector<int4>& keys, const std::vector<double>& X, int cap, int nchunks,
-                          std::vector<int>& vp, int* n_own) {
+                          std::vector<int>& vp, int* n_own, std::vector<int>* tperm_out) {
   const int nt = (int)keys.size();
   const int nv = (int)(X.size() / 3);
   std::vector<int> tperm;
@@ -455,31 +543,39 @@ void chunked_vertex_order(const std::vector<int4>& keys, const std::vector<doubl
   }
   // rows: the vertices of one chunk only, chunk by chunk, then the vertices
   // several chunks share, then unreferenced ones; each group in the order of
-  // first use
-  std::vector<std::tuple<int, int, int>> key(nv);
-  for (int v = 0; v < nv; ++v) {
-    const int grp = fc[v] < 0 ? K + 1 : (fc[v] == lc[v] ? fc[v] : K);
-    key[v] = std::make_tuple(grp, first[v], v);
+  // first use (ties within a tet by vertex number), unreferenced ones by
+  // number.  Built by one pass over the tets in order.
+  std::vector<std::vector<int>> group(K + 2);
+  for (int t = 0; t < nt; ++t) {
+    int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
+    std::sort(k, k + 4);
+    for (int a = 0; a < 4; ++a)
+      if (first[k[a]] == t) group[fc[k[a]] == lc[k[a]] ? fc[k[a]] : K].push_back(k[a]);
   }
-  std::sort(key.begin(), key.end());
-  vp.resize(nv);
-  int own = 0;
-  for (int i = 0; i < nv; ++i) {
-    vp[i] = std::get<2>(key[i]);
-    if (std::get<0>(key[i]) < K) own = i + 1;
+  for (int v = 0; v < nv; ++v)
+    if (fc[v] < 0) group[K + 1].push_back(v);
+  vp.clear();
+  vp.reserve(nv);
+  for (int g = 0; g < K + 2; ++g) {
+    vp.insert(vp.end(), group[g].begin(), group[g].end());
+    if (g == K - 1) *n_own = (int)vp.size();
   }
-  *n_own = own;
+  if (tperm_out) tperm_out->swap(tperm);
 }
 
 ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int4>& keys,
                           const std::vector<double>& X, const std::vector<int>* batch, std::vector<int>& perm,
-                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix) {
+                          std::vector<int4>& sorted, std::vector<unsigned char>& prefix,
+                          const std::vector<int>* known_perm) {
   const int nt = (int)keys.size();
   const int nv = (int)(X.size() / 3);
   cudaStream_t st = ctx->stream;
 
   // 1. Morton order of centroids.
-  tet_morton_order(keys, X, batch, perm);
+  if (known_perm && (int)known_perm->size() == nt)
+    perm = *known_perm;
+  else
+    tet_morton_order(keys, X, batch, perm);
   sorted.resize(nt);
   for (int i = 0; i < nt; ++i) sorted[i] = keys[perm[i]];
 
@@ -500,13 +596,23 @@ ebb_status_t build_layout(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector<int
     }
   }
 
-  std::vector<int> vorder(nv);
-  for (int v = 0; v < nv; ++v) vorder[v] = v;
-  std::stable_sort(vorder.begin(), vorder.end(), [&](int a, int b) {
-    const int ea = voff[a] < voff[a + 1] ? vent[voff[a]] : 0x7fffffff;
-    const int eb = voff[b] < voff[b + 1] ? vent[voff[b]] : 0x7fffffff;
-    return ea < eb;
-  });
+  // Vertices by first entry (= first use by the internal tets), unused ones
+  // last in number order.
+  std::vector<int> vorder;
+  vorder.reserve(nv);
+  {
+    std::vector<unsigned char> seen(nv, 0);
+    for (int i = 0; i < nt; ++i) {
+      const int k[4] = {sorted[i].x, sorted[i].y, sorted[i].z, sorted[i].w};
+      for (int a = 0; a < 4; ++a)
+        if (!seen[k[a]]) {
+          seen[k[a]] = 1;
+          vorder.push_back(k[a]);
+        }
+    }
+    for (int v = 0; v < nv; ++v)
+      if (!seen[v]) vorder.push_back(v);
+  }
 
   const int ntiles = tile_prefix(sorted, nv, tets->tile_cap, prefix);
 

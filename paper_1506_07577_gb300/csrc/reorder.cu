@@ -192,7 +192,7 @@ void vertex_morton_order(const std::vector<double>& X, std::vector<int>& perm) {
     if (!(hi[c] > lo[c])) hi[c] = lo[c] + 1.0;
   }
   const double q = (double)((1u << 21) - 1);
-  std::vector<std::pair<uint64_t, int>> code(nv);
+  std::vector<uint64_t> code(nv);
   for (int v = 0; v < nv; ++v) {
     uint64_t m = 0;
     for (int c = 0; c < 3; ++c) {
@@ -200,11 +200,10 @@ void vertex_morton_order(const std::vector<double>& X, std::vector<int>& perm) {
       r = r < 0 ? 0 : (r > 1 ? 1 : r);
       m |= spread3((uint64_t)(r * q)) << c;
     }
-    code[v] = {m, v};
+    code[v] = m;
   }
-  std::sort(code.begin(), code.end());
-  perm.resize(nv);
-  for (int i = 0; i < nv; ++i) perm[i] = code[i].second;
+  perm.clear();
+  radix_order(code, 63, perm);  // by code, ties by vertex number
 }
 
 }  // namespace ebb
