@@ -22,7 +22,8 @@ every timed GPU result against it at sampled vertices (or whole meshes where
 the oracle finishes in seconds).  --impl reference times the same oracle on
 a bounded sample of the headline workload (the baseline for this path: there
 is no reference code to run).  --profile runs one map or step a few times
-for a profiler, and nothing else.
+for a profiler, and nothing else; --host-link measures the page-locked copy
+bandwidth that bounds the end-to-end figure.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run each rank runs an independent replica of the workload
@@ -1088,9 +1089,66 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_host_link(argv):
+    """Page-locked host <-> device copy bandwidth for copies of the headline
+    end-to-end call's size (the 4-float u and w of the 128^3 mesh, 34.3 MB
+    each) and of 4x that: host to device alone, device to host alone, and
+    both directions at once on two streams.  CUDA events, median of 10 after
+    3 warm-up copies; prints one line.
+
+        python bench.py --host-link"""
+    import torch
+
+    out = {"metric": "page-locked host link bandwidth", "unit": "GB/s", "sizes": {}}
+    dev = torch.device("cuda", 0)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    for nbytes in (2146689 * 16, 4 * 2146689 * 16):
+        n = nbytes // 4
+        h_in = torch.empty(n, dtype=torch.float32).pin_memory()
+        h_out = torch.empty(n, dtype=torch.float32).pin_memory()
+        d_in = torch.empty(n, dtype=torch.float32, device=dev)
+        d_out = torch.zeros(n, dtype=torch.float32, device=dev)
+
+        def timed(fn):
+            ts = []
+            for it in range(13):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s1)
+                fn()
+                s1.wait_stream(s2)
+                b.record(s1)
+                b.synchronize()
+                if it >= 3:
+                    ts.append(a.elapsed_time(b) * 1e-3)
+            return statistics.median(ts)
+
+        def h2d():
+            with torch.cuda.stream(s1):
+                d_in.copy_(h_in, non_blocking=True)
+
+        def d2h():
+            with torch.cuda.stream(s1):
+                h_out.copy_(d_out, non_blocking=True)
+
+        def both():
+            s2.wait_stream(s1)
+            with torch.cuda.stream(s1):
+                d_in.copy_(h_in, non_blocking=True)
+            with torch.cuda.stream(s2):
+                h_out.copy_(d_out, non_blocking=True)
+
+        t_h2d, t_d2h, t_both = timed(h2d), timed(d2h), timed(both)
+        out["sizes"][str(nbytes)] = {"h2d_GBps": nbytes / t_h2d / 1e9, "d2h_GBps": nbytes / t_d2h / 1e9,
+                                     "both_directions_GBps_each": nbytes / t_both / 1e9}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     if "--profile" in sys.argv[1:]:
         run_profile([a for a in sys.argv[1:]])
+        return
+    if "--host-link" in sys.argv[1:]:
+        run_host_link(sys.argv[1:])
         return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
