@@ -363,7 +363,7 @@ def run_headline(args, abi, torch, dev, local_rank, stream, flush, dist, world, 
     o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
     us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "up", "wp", "fp", "kp", o),
                     zero_p, flush, 5)
-    variants["tiled_planes"] = {"us": us, "tets_per_s": nt / (us * 1e-6)}
+    variants["tiled_3plane_fields"] = {"us": us, "tets_per_s": nt / (us * 1e-6)}
     dm.close()
     # the vertex fields in the caller's scattered order (no renumbering): the
     # tiles gather and add each vertex where the caller's numbering puts it
@@ -453,7 +453,7 @@ def run_nh64(args, abi, torch, local_rank, stream, flush):
     o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_TILED)
     us = time_calls(torch, stream, lambda: abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "u32p", "w32p", "fp", "Kwp", o),
                     lambda: (fp.zero_(), kp.zero_()), flush, 5)
-    variants["tiled_planes"] = {"us": us, "tets_per_s": nt / (us * 1e-6)}
+    variants["tiled_3plane_fields"] = {"us": us, "tets_per_s": nt / (us * 1e-6)}
     out = {"workload": "64^3 cube grid (274,625 verts, 1,310,720 tets), NH, E log-uniform [1e4,1e6] per tet, "
                        "nu 0.4, FP32 fused force+K*w map on 4-float vector elements, L2 flushed",
            "algorithmic_bytes_per_tet": bpt, "autotune": tune, "fused_map": variants}
@@ -536,15 +536,15 @@ def fp64_map_leg(dm, u, w, abi, torch, stream, flush):
     dm.vertex_field("w64", torch.float64, value=w)
     kk = dm.vertex_field("k64", torch.float64)
     forms = {}
-    for name, red, flags in (("tiled_rows", abi.EBB_REDUCE_TILED, 0),
-                             ("tiled_planes", abi.EBB_REDUCE_TILED, abi.EBB_TUNE_RECORD_PLANES),
+    for name, red, flags in (("tiled_row_records", abi.EBB_REDUCE_TILED, 0),
+                             ("tiled_plane_records", abi.EBB_REDUCE_TILED, abi.EBB_TUNE_RECORD_PLANES),
                              ("coop", abi.EBB_REDUCE_COOP, 0)):
         abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_NEOHOOKEAN, abi.EBB_PREC_F64, red, 128, flags)
         o = abi.map_opts(abi.EBB_NEOHOOKEAN, precision=abi.EBB_PREC_F64, reduce=abi.EBB_REDUCE_AUTO)
         forms[name] = time_calls(torch, stream, lambda: abi.ebb_map_tet_Kv(dm.ctx, dm.tets, "u64", "w64", "k64", o),
                                  kk.zero_, flush, 5)
     abi.ebb_relation_set_tuning(dm.ctx, dm.tets, abi.EBB_NEOHOOKEAN, abi.EBB_PREC_F64, abi.EBB_REDUCE_TILED, 128, 0)
-    us = forms["tiled_rows"]
+    us = forms["tiled_row_records"]
     out = {"kernel": "tet_tile_kernel<double, NEOHOOKEAN, KV>", "us": us, "tets_per_s": nt / (us * 1e-6),
            "forms_us": forms, "winner": min(forms, key=forms.get),
            "bound": "alu", "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "derived: 2 DFMA/clock/SM x 152 SMs x 2070 MHz"}
