@@ -934,7 +934,8 @@ def run_profile(argv):
     ap.add_argument("--variant", choices=["auto", "atomic", "tiled", "colour", "gather", "ordered", "coop"],
                     default="tiled")
     ap.add_argument("--planes", action="store_true", help="tile blobs with per-tet data as field planes")
-    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step", "spmv", "springs"], default="fused")
+    ap.add_argument("--ops", choices=["fused", "kv", "force", "diag", "step", "spmv", "springs", "vjp"],
+                    default="fused")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--model", choices=["nh", "stvk"], default="nh")
     ap.add_argument("--permute", action="store_true")
@@ -980,6 +981,29 @@ def run_profile(argv):
             prm = abi.step_params(mdl, 1e-3, 1000.0, mu0, lam0, precision=prec, reduce=red, rtol=1e-8)
             for _ in range(a.iters):
                 abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "uu", "vv", "pinned", prm)
+        elif a.ops == "vjp":
+            # StVK FP64 (C3's solver settings): one implicit step from rest
+            # with a random initial velocity, then the step's VJP at the new
+            # velocity (adjoint solve + per-tet VJP map), a few times
+            prm = abi.step_params(abi.EBB_STVK, 1e-3, 1000.0, mu0, lam0, precision=abi.EBB_PREC_F64,
+                                  max_iters=4000, rtol=1e-12)
+            pin = dm.bind("pinned", torch.from_numpy(dm.rows(m.pinned).astype(np.uint8)).to(dm.device))
+            v0 = 0.05 * meshgen.random_field(m.n_verts, seed=seed)
+            v0[m.pinned] = 0.0
+            dm.vertex_field("uu", torch.float64)
+            dm.vertex_field("vv", torch.float64, value=v0)
+            dm.vertex_field("u0", torch.float64)
+            dm.vertex_field("v0", torch.float64, value=v0)
+            abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "uu", "vv", "pinned", prm)
+            gu = dm.vertex_field("gu", torch.float64)
+            gv = dm.vertex_field("gv", torch.float64)
+            gmu = dm.bind_tets("gmu", torch.zeros(m.n_tets, dtype=torch.float64, device=pin.device))
+            glam = dm.bind_tets("glam", torch.zeros(m.n_tets, dtype=torch.float64, device=pin.device))
+            for _ in range(a.iters):
+                gu.copy_(dm._tensors["uu"])
+                gv.zero_()
+                abi.ebb_cg_implicit_step_vjp_at(dm.ctx, dm.tets, "u0", "v0", "vv", "pinned", "gu", "gv", "gmu",
+                                                "glam", prm)
         elif a.ops == "spmv":
             # K(u) assembled once, then the block-sparse product K w
             abi.ebb_assemble_tet_K(dm.ctx, dm.tets, "u", o)
