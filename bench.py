@@ -62,12 +62,12 @@ G = (0.0, 0.0, -9.81)
 # record layout (`--profile --n 128 --permute --renumber --model stvk
 # --uniform --x4 [--planes]`).  They describe the kernel sources whose hash
 # is given and are reported as null (with a note) once those sources change.
-NCU_TRAFFIC = {"sources_sha256_16": "393d109df27873ed", "n": 128,
-               "bytes_per_launch": {"rows": 988.79e6, "planes": 903.84e6}}
+NCU_TRAFFIC = {"sources_sha256_16": "b9005aa1ea63b50f", "n": 128,
+               "bytes_per_launch": {"rows": 988.94e6, "planes": 904.24e6}}
 # FP64 arithmetic of the FP64 kernels, counted by ncu (2 x DFMA + DADD + DMUL
 # thread instructions per unit) on the 64^3 workload, valid while the map and
 # spring sources hash to the same value.
-NCU_FP64 = {"sources_sha256_16": "6348968f747c117a", "kv_map_nh_flops_per_tet": 454.8,
+NCU_FP64 = {"sources_sha256_16": "9587f3ea51b9ec74", "kv_map_nh_flops_per_tet": 454.8,
             "kv_map_nh_pipe_active": 0.882, "spring_flops_per_directed_spring": 32.15,
             "spring_pipe_active": 0.858}
 # FP64 peak of the part, derived: 2 DFMA (4 flops) per clock per SM x 152 SMs
@@ -303,30 +303,49 @@ def run_headline(args, abi, torch, dev, local_rank, stream, flush, dist, world, 
     out["gpu_k"] = dm.caller(k[:, :3].double().cpu().numpy())
 
     # ---- end to end: one C-ABI call on page-locked host buffers (copy u, w
-    # in, zero f, K w, map, copy f, K w out, wait) ---------------------------
-    uh = dm._tensors["u"].cpu().pin_memory()
-    wh = dm._tensors["w"].cpu().pin_memory()
-    fh = torch.empty_like(f, device="cpu").pin_memory()
-    kh = torch.empty_like(k, device="cpu").pin_memory()
-    opts_e2e = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO,
-                            flags=abi.EBB_MAP_ZERO_OUT)
-    e2e_ms = []
-    with torch.cuda.stream(stream):
-        for s in range(args.warmup + args.steps):
-            flush.fill_(float(s))
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, opts_e2e)
-            e1.record(stream)
-            e1.synchronize()
-            if s >= args.warmup:
-                e2e_ms.append(e0.elapsed_time(e1))
+    # in, zero f, K w, map, copy f, K w out, wait).  The host holds packed
+    # (x, y, z) FP32 rows (EBB_MAP_HOST_XYZ: widened to the 4-float fields on
+    # the device); the same call on 16-byte host elements is a sub-record.
+    def e2e_calls(uh, wh, fh, kh, flags):
+        o = abi.map_opts(abi.EBB_STVK, mu, lam, precision=abi.EBB_PREC_F32, reduce=abi.EBB_REDUCE_AUTO,
+                         flags=abi.EBB_MAP_ZERO_OUT | flags)
+        ms = []
+        with torch.cuda.stream(stream):
+            for s in range(args.warmup + args.steps):
+                flush.fill_(float(s))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
+                e1.record(stream)
+                e1.synchronize()
+                if s >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+        return ms
+
+    uh = dm._tensors["u"][:, :3].contiguous().cpu().pin_memory()
+    wh = dm._tensors["w"][:, :3].contiguous().cpu().pin_memory()
+    fh = torch.empty((nv, 3), dtype=torch.float32).pin_memory()
+    kh = torch.empty((nv, 3), dtype=torch.float32).pin_memory()
+    e2e_ms = e2e_calls(uh, wh, fh, kh, abi.EBB_MAP_HOST_XYZ)
+    # the host rows against the device-field map above (atomic order differs)
+    e2e_diff = max(float(np.abs(dm.caller(fh.double().numpy()) - out["gpu_f"]).max() / np.abs(out["gpu_f"]).max()),
+                   float(np.abs(dm.caller(kh.double().numpy()) - out["gpu_k"]).max() / np.abs(out["gpu_k"]).max()))
     e2e_total = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
     out["e2e"] = {"value": replica_throughput(nt * args.steps, e2e_total, world), "unit": UNIT,
                   "h2d_bytes_per_step": (uh.numel() + wh.numel()) * 4,
                   "d2h_bytes_per_step": (fh.numel() + kh.numel()) * 4,
                   "ms_per_call": 1e3 * e2e_total / args.steps,
-                  "call": "ebb_map_tet_force_Kv_host on page-locked host buffers (EBB_MAP_ZERO_OUT)"}
+                  "call": "ebb_map_tet_force_Kv_host on page-locked packed (x, y, z) FP32 host rows "
+                          "(EBB_MAP_HOST_XYZ | EBB_MAP_ZERO_OUT)",
+                  "rel_diff_vs_device_map": e2e_diff}
+    ux = dm._tensors["u"].cpu().pin_memory()
+    wx = dm._tensors["w"].cpu().pin_memory()
+    fx = torch.empty_like(f, device="cpu").pin_memory()
+    kx = torch.empty_like(k, device="cpu").pin_memory()
+    x4_ms = e2e_calls(ux, wx, fx, kx, 0)
+    out["e2e"]["host_4float_elements"] = {
+        "ms_per_call": statistics.mean(x4_ms), "tets_per_s": nt / (statistics.mean(x4_ms) * 1e-3),
+        "h2d_bytes_per_step": (ux.numel() + wx.numel()) * 4, "d2h_bytes_per_step": (fx.numel() + kx.numel()) * 4}
 
     # ---- every reduction variant and field layout (kernel time), warm ------
     peak = _peaks()[0]

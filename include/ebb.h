@@ -160,6 +160,14 @@ typedef enum {
 
 /* map flags */
 #define EBB_MAP_ZERO_OUT      1u  /* zero the output fields before reducing into them */
+/* ebb_map_tet_force_Kv_host only (other calls ignore it): the host buffers
+ * hold packed rows of three floats (x, y, z: 12 bytes per vertex) while the
+ * bound fields are FP32 EBB_F32X4 elements.  The rows pass through a
+ * library-owned device staging buffer (48 bytes per vertex, allocated on
+ * first use, freed with the relation's tet data) and are widened to, or
+ * narrowed from, the 4-float elements on the device, so a quarter fewer
+ * bytes cross the host link. */
+#define EBB_MAP_HOST_XYZ      2u
 /* Testing (failure detection): the tiled map skips the bulk copy of tile 0
  * and shortens its bounded waits to about 1 ms, so the CTA that owns tile 0
  * gives up waiting, reports EBB_ERR_TIMEOUT through the device status word
@@ -289,7 +297,8 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * accumulating, or into zeroed fields with EBB_MAP_ZERO_OUT -- copies the
  * fields f_out and Kw_out into f_host and Kw_host, and returns when the
  * copies are complete.  Each host buffer holds exactly its field's bytes in
- * the field's layout (3 planes of N_v values, or N_v EBB_F32X4 elements);
+ * the field's layout (3 planes of N_v values, or N_v EBB_F32X4 elements), or,
+ * with EBB_MAP_HOST_XYZ on EBB_F32X4 fields, N_v packed (x, y, z) FP32 rows;
  * page-locked host memory lets the copies run at full speed, pageable memory
  * works more slowly.  With the tiled reduction on fields the map reads in
  * place, and at least 16 tiles, the call runs in 8 consecutive tile chunks:
@@ -304,7 +313,9 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * ebb_map_tet_force_Kv (checked before anything is copied); EBB_ERR_ARG for
  * a null host buffer (with N_v > 0); EBB_ERR_PHASE if the device fields u
  * and w overlap, unless they are the same field and u_host == w_host (one
- * copy then fills it); EBB_ERR_CUDA if a copy fails. */
+ * copy then fills it); EBB_ERR_ARG for EBB_MAP_HOST_XYZ unless the fields
+ * are FP32 EBB_F32X4 elements; EBB_ERR_NOMEM if its staging buffer cannot be
+ * allocated; EBB_ERR_CUDA if a copy fails. */
 ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
                                        const char* w, const char* f_out,
                                        const char* Kw_out, const void* u_host,

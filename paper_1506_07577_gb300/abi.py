@@ -47,6 +47,7 @@ EBB_FINALIZE_EDGES = 4
 EBB_FINALIZE_RENUMBER_VERTS = 8
 EBB_STEP_ASSEMBLED = 1
 EBB_MAP_ZERO_OUT = 1
+EBB_MAP_HOST_XYZ = 2
 EBB_MAP_TEST_DROP_TILE = 0x80000000
 EBB_NOALLOC_MAX_VERTS = 4096
 EBB_NOALLOC_MAX_TETS = 24576

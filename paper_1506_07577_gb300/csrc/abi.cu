@@ -118,6 +118,8 @@ void free_host_plan(ebb_rel_s* r) {
 
 void free_tet_data(ebb_rel_s* r) {
   free_host_plan(r);
+  cudaFree(r->xyz_stage);
+  r->xyz_stage = nullptr;
   cudaFree(r->keys);
   r->keys = nullptr;
   cudaFree(r->vperm);
@@ -815,13 +817,37 @@ cudaError_t copy_rows(void* dst, const void* src, int r0, int r1, int nv, bool x
   return cudaSuccess;
 }
 
+// Rows [r0, r1) of an input field from the host, and of an output field to
+// the host: as copy_rows, or, with a staging buffer (EBB_MAP_HOST_XYZ), as
+// packed (x, y, z) host rows that pass through `stage` on the device and are
+// widened to (or narrowed from) the field's 4-float elements there.
+cudaError_t rows_in(void* dev, const void* host, float* stage, int r0, int r1, int nv, bool x4, size_t elem,
+                    cudaStream_t st) {
+  if (!stage) return copy_rows(dev, host, r0, r1, nv, x4, elem, cudaMemcpyHostToDevice, st);
+  if (r1 <= r0) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(stage + 3 * (size_t)r0, (const float*)host + 3 * (size_t)r0,
+                                  12 * (size_t)(r1 - r0), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = xyz_to_x4(stage, nullptr, (float*)dev, nullptr, r0, r1, st);
+  return e;
+}
+cudaError_t rows_out(void* host, const void* dev, float* stage, int r0, int r1, int nv, bool x4, size_t elem,
+                     cudaStream_t st) {
+  if (!stage) return copy_rows(host, dev, r0, r1, nv, x4, elem, cudaMemcpyDeviceToHost, st);
+  if (r1 <= r0) return cudaSuccess;
+  cudaError_t e = x4_to_xyz((const float*)dev, nullptr, stage, nullptr, r0, r1, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((float*)host + 3 * (size_t)r0, stage + 3 * (size_t)r0, 12 * (size_t)(r1 - r0),
+                        cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
 // The host-buffer map in tile chunks: chunk c's input rows are copied in on
 // one stream, its tiles mapped on the context's stream once they have
 // landed, and the output rows it completes copied out on a third stream,
 // so that the copies of one chunk overlap the map of another.
 template <typename T>
 ebb_status_t host_map_chunked(ebb_ctx_s* ctx, ebb_rel_s* tets, void* const* dev, bool x4, bool same_input,
-                              const void* u_host, const void* w_host, void* f_host, void* Kw_host,
+                              const void* u_host, const void* w_host, void* f_host, void* Kw_host, float* stage,
                               const ebb_map_opts_t* opts, ebb_reduce_t reduce) {
   HostPlan* P = nullptr;
   ebb_status_t s = host_plan(ctx, tets, &P);
@@ -842,36 +868,69 @@ ebb_status_t host_map_chunked(ebb_ctx_s* ctx, ebb_rel_s* tets, void* const* dev,
   io.f = (T*)dev[2];
   io.Kw = (T*)dev[3];
   io.aos = x4;
+  // Packed host rows (EBB_MAP_HOST_XYZ) pass through the staging buffer:
+  // the copy streams move 12-byte rows between the host and the staging,
+  // and the rows a chunk reads are widened into the fields just before its
+  // map, the rows it completes narrowed just after, on the map's stream
+  // (kernels beside the map would find its SMs full).  Without staging the
+  // copies move the fields' own rows.
+  const size_t sn = 3 * (size_t)nv;
+  float* const stg[4] = {stage, stage ? stage + sn : nullptr, stage ? stage + 2 * sn : nullptr,
+                         stage ? stage + 3 * sn : nullptr};
+  float* const w_dev = same_input ? nullptr : (float*)dev[1];
+  float* const w_stg = same_input ? nullptr : stg[1];
+  auto packed_copy = [&](void* dst, const void* src, int r0, int r1, cudaMemcpyKind kind, cudaStream_t cs) {
+    if (r1 <= r0) return cudaSuccess;
+    return cudaMemcpyAsync((float*)dst + 3 * (size_t)r0, (const float*)src + 3 * (size_t)r0, 12 * (size_t)(r1 - r0),
+                           kind, cs);
+  };
+  auto copy_in = [&](int r0, int r1) {
+    cudaError_t ce = stage ? packed_copy(stg[0], u_host, r0, r1, cudaMemcpyHostToDevice, P->s_in)
+                           : copy_rows(dev[0], u_host, r0, r1, nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+    if (ce == cudaSuccess && !same_input)
+      ce = stage ? packed_copy(stg[1], w_host, r0, r1, cudaMemcpyHostToDevice, P->s_in)
+                 : copy_rows(dev[1], w_host, r0, r1, nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+    return ce;
+  };
+  auto copy_out = [&](int r0, int r1) {
+    cudaError_t ce = stage ? packed_copy(f_host, stg[2], r0, r1, cudaMemcpyDeviceToHost, P->s_out)
+                 : copy_rows(f_host, dev[2], r0, r1, nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+    if (ce == cudaSuccess)
+      ce = stage ? packed_copy(Kw_host, stg[3], r0, r1, cudaMemcpyDeviceToHost, P->s_out)
+                 : copy_rows(Kw_host, dev[3], r0, r1, nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+    return ce;
+  };
   // the shared rows first
-  if (e == cudaSuccess)
-    e = copy_rows(dev[0], u_host, P->own, nv, nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
-  if (e == cudaSuccess && !same_input)
-    e = copy_rows(dev[1], w_host, P->own, nv, nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
+  if (e == cudaSuccess) e = copy_in(P->own, nv);
   int in_done = 0, out_done = 0;
   for (int c = 0; c < P->K && e == cudaSuccess; ++c) {
-    e = copy_rows(dev[0], u_host, in_done, P->need_hi[c], nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
-    if (e == cudaSuccess && !same_input)
-      e = copy_rows(dev[1], w_host, in_done, P->need_hi[c], nv, x4, sizeof(T), cudaMemcpyHostToDevice, P->s_in);
-    in_done = P->need_hi[c];
+    e = copy_in(in_done, P->need_hi[c]);
     if (e == cudaSuccess) e = cudaEventRecord(P->ev_in[c], P->s_in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_in[c], 0);
+    if (stage) {
+      if (e == cudaSuccess && c == 0) e = xyz_to_x4(stg[0], w_stg, (float*)dev[0], w_dev, P->own, nv, st);
+      if (e == cudaSuccess) e = xyz_to_x4(stg[0], w_stg, (float*)dev[0], w_dev, in_done, P->need_hi[c], st);
+    }
+    in_done = P->need_hi[c];
     io.tile_begin = P->tile_off[c];
     io.tile_end = P->tile_off[c + 1];
     if (e == cudaSuccess)
       e = launch_tet_map<T>(tets, opts->model, OP_FORCE | OP_KV, reduce, (T)opts->mu, (T)opts->lambda, io, nullptr, st);
+    if (e == cudaSuccess && stage)
+      e = x4_to_xyz((const float*)dev[2], (const float*)dev[3], stg[2], stg[3], out_done, P->done_lo[c], st);
     if (e == cudaSuccess) e = cudaEventRecord(P->ev_map[c], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_out, P->ev_map[c], 0);
-    if (e == cudaSuccess)
-      e = copy_rows(f_host, dev[2], out_done, P->done_lo[c], nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
-    if (e == cudaSuccess)
-      e = copy_rows(Kw_host, dev[3], out_done, P->done_lo[c], nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+    if (e == cudaSuccess) e = copy_out(out_done, P->done_lo[c]);
     out_done = P->done_lo[c];
   }
   // the rows before `own` that no chunk touched, and the shared rows, last
-  if (e == cudaSuccess)
-    e = copy_rows(f_host, dev[2], out_done, nv, nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
-  if (e == cudaSuccess)
-    e = copy_rows(Kw_host, dev[3], out_done, nv, nv, x4, sizeof(T), cudaMemcpyDeviceToHost, P->s_out);
+  // (narrowed after the last map; its event is recorded again)
+  if (e == cudaSuccess && stage) {
+    e = x4_to_xyz((const float*)dev[2], (const float*)dev[3], stg[2], stg[3], out_done, nv, st);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_map[P->K - 1], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->s_out, P->ev_map[P->K - 1], 0);
+  }
+  if (e == cudaSuccess) e = copy_out(out_done, nv);
   if (e == cudaSuccess) e = cudaEventRecord(P->ev_end, P->s_out);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P->ev_end, 0);
   if (e != cudaSuccess) return cuda_check(ctx, e, "chunked host-buffer map");
@@ -918,6 +977,21 @@ ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char
     return set_error(ctx, EBB_ERR_PHASE, "fields u and w overlap on the device but come from different host buffers");
   if (opts->model != EBB_STVK && opts->model != EBB_NEOHOOKEAN)
     return set_error(ctx, EBB_ERR_ARG, "unknown material model");
+  // Packed (x, y, z) host rows: staged on the device, widened into and
+  // narrowed from the 4-float fields there.
+  const bool xyz = (opts->flags & EBB_MAP_HOST_XYZ) != 0;
+  if (xyz && (!x4 || f64))
+    return set_error(ctx, EBB_ERR_ARG, "EBB_MAP_HOST_XYZ needs FP32 fields of EBB_F32X4 elements");
+  float* stage = nullptr;
+  if (xyz && bytes > 0) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
+    if (!tets->xyz_stage && cudaMalloc(&tets->xyz_stage, sizeof(float) * 12 * (size_t)tets->verts->size) != cudaSuccess) {
+      tets->xyz_stage = nullptr;
+      cudaGetLastError();
+      return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the packed-row staging failed");
+    }
+    stage = tets->xyz_stage;
+  }
   // The tiled map on fields it reads in place runs in chunks that overlap
   // the copies; every other form copies everything in, maps, copies out.
   const ebb_reduce_t reduce = resolve_reduce(tets, opts->reduce, opts->model, opts->precision);
@@ -925,21 +999,26 @@ ebb_status_t ebb_map_tet_force_Kv_host(ebb_ctx_t ctx, ebb_rel_t tets, const char
   if (bytes > 0 && reduce == EBB_REDUCE_TILED && !tets->vperm && !staged &&
       !(opts->flags & EBB_MAP_TEST_DROP_TILE) && tets->tiles.ntiles >= 2 * HostPlan::kChunks) {
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, EBB_ERR_CUDA, "cudaSetDevice failed");
-    return f64 ? host_map_chunked<double>(ctx, tets, dev, x4, same_input, u_host, w_host, f_host, Kw_host, opts, reduce)
-               : host_map_chunked<float>(ctx, tets, dev, x4, same_input, u_host, w_host, f_host, Kw_host, opts, reduce);
+    return f64 ? host_map_chunked<double>(ctx, tets, dev, x4, same_input, u_host, w_host, f_host, Kw_host, stage,
+                                          opts, reduce)
+               : host_map_chunked<float>(ctx, tets, dev, x4, same_input, u_host, w_host, f_host, Kw_host, stage,
+                                         opts, reduce);
   }
   cudaError_t e = cudaSuccess;
+  const int nv = (int)tets->verts->size;
+  const size_t elem = f64 ? 8 : 4, sn = 3 * (size_t)nv;
   if (bytes > 0) {
-    e = cudaMemcpyAsync(dev[0], u_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    e = rows_in(dev[0], u_host, stage, 0, nv, nv, x4, elem, ctx->stream);
     if (e == cudaSuccess && !same_input)
-      e = cudaMemcpyAsync(dev[1], w_host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+      e = rows_in(dev[1], w_host, stage ? stage + sn : nullptr, 0, nv, nv, x4, elem, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "copying u, w to the device");
   }
   s = ebb_map_tet_force_Kv(ctx, tets, u, w, f_out, Kw_out, opts);
   if (s) return s;
   if (bytes > 0) {
-    e = cudaMemcpyAsync(f_host, dev[2], bytes, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(Kw_host, dev[3], bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    e = rows_out(f_host, dev[2], stage ? stage + 2 * sn : nullptr, 0, nv, nv, x4, elem, ctx->stream);
+    if (e == cudaSuccess)
+      e = rows_out(Kw_host, dev[3], stage ? stage + 3 * sn : nullptr, 0, nv, nv, x4, elem, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "copying f, Kw to the host");
   }
   // Waits for the copies and reports any device-detected error of the map.

@@ -254,6 +254,8 @@ struct ebb_rel_s {
   // ---- implicit-step scratch ----
   ebb::StepScratch* step = nullptr;
   ebb::HostPlan* hplan = nullptr;       // chunk plan of the host-buffer map (abi.cu)
+  float* xyz_stage = nullptr;           // host-buffer map's packed-row staging: u, w, f, Kw, 3 x N_v floats
+                                        // each (EBB_MAP_HOST_XYZ; allocated on first use)
   ebb::BatchScratch* batch = nullptr;
 };
 
@@ -371,6 +373,10 @@ cudaError_t deinterleave_add_fields(int nv, const int* vperm, const float* const
 // Interleaved (4-float) elements in the internal vertex order: dst[i] =
 // src[vperm[i]], and dst[vperm[i]].xyz += src[i].xyz.
 cudaError_t permute_vec4(int nv, const int* vperm, const float* src, float* dst, cudaStream_t st);
+// Rows [r0, r1) of packed (x, y, z) FP32 triples into 4-float elements, and
+// back, for the field pair (a, b); b may be null (reorder.cu).
+cudaError_t xyz_to_x4(const float* sa, const float* sb, float* da, float* db, int r0, int r1, cudaStream_t st);
+cudaError_t x4_to_xyz(const float* sa, const float* sb, float* da, float* db, int r0, int r1, cudaStream_t st);
 cudaError_t permute_add_vec4(int nv, const int* vperm, const float* src, float* dst, cudaStream_t st);
 
 // Vertex reordering helpers (reorder.cu).  Gather: dst[c][i] = src[c][vperm[i]];

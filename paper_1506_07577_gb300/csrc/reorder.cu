@@ -111,7 +111,58 @@ uint64_t spread3(uint64_t x) {
   return x;
 }
 
+// Rows [r0, r1) of packed (x, y, z) triples to 4-float elements (x, y, z, 0)
+// and back, for one field or two: the host-buffer map's transfers in 12-byte
+// rows (blocks striding over the rows).
+constexpr int kXyzThreads = 256;
+constexpr int kXyzMaxBlocks = 4 * 152;
+
+__global__ void xyz_to_x4_kernel(int r0, int r1, const float* __restrict__ sa, const float* __restrict__ sb,
+                                 float4* __restrict__ da, float4* __restrict__ db) {
+  for (int r = r0 + blockIdx.x * kXyzThreads + threadIdx.x; r < r1; r += gridDim.x * kXyzThreads) {
+    const float* p = sa + 3 * (size_t)r;
+    da[r] = make_float4(p[0], p[1], p[2], 0.f);
+    if (sb) {
+      const float* q = sb + 3 * (size_t)r;
+      db[r] = make_float4(q[0], q[1], q[2], 0.f);
+    }
+  }
+}
+
+__global__ void x4_to_xyz_kernel(int r0, int r1, const float4* __restrict__ sa, const float4* __restrict__ sb,
+                                 float* __restrict__ da, float* __restrict__ db) {
+  for (int r = r0 + blockIdx.x * kXyzThreads + threadIdx.x; r < r1; r += gridDim.x * kXyzThreads) {
+    const float4 a = sa[r];
+    float* p = da + 3 * (size_t)r;
+    p[0] = a.x;
+    p[1] = a.y;
+    p[2] = a.z;
+    if (sb) {
+      const float4 b = sb[r];
+      float* q = db + 3 * (size_t)r;
+      q[0] = b.x;
+      q[1] = b.y;
+      q[2] = b.z;
+    }
+  }
+}
+
+int xyz_blocks(int rows) { return std::max(1, std::min((rows + kXyzThreads - 1) / kXyzThreads, kXyzMaxBlocks)); }
+
 }  // namespace
+
+cudaError_t xyz_to_x4(const float* sa, const float* sb, float* da, float* db, int r0, int r1, cudaStream_t st) {
+  if (r1 <= r0) return cudaSuccess;
+  xyz_to_x4_kernel<<<xyz_blocks(r1 - r0), kXyzThreads, 0, st>>>(r0, r1, sa, sb, (float4*)da, (float4*)db);
+  return cudaGetLastError();
+}
+
+cudaError_t x4_to_xyz(const float* sa, const float* sb, float* da, float* db, int r0, int r1, cudaStream_t st) {
+  if (r1 <= r0) return cudaSuccess;
+  x4_to_xyz_kernel<<<xyz_blocks(r1 - r0), kXyzThreads, 0, st>>>(r0, r1, (const float4*)sa, (const float4*)sb, da,
+                                                                  db);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t gather_vertex_field(int nv, const int* vperm, const T* src, T* dst, cudaStream_t st) {

@@ -148,3 +148,79 @@ def test_chunked_host_map_matches_oracle(layout, renumber):
         abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
         assert rel_err(dm.caller(_vec(fh, layout)), 2 * f) < tol
         assert rel_err(dm.caller(_vec(kh, layout)), 2 * Kw) < tol
+
+
+def _host_xyz(arr):
+    """Host copy of an (N_v, 3) array as packed FP32 (x, y, z) rows, page-locked."""
+    return torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float32)).pin_memory()
+
+
+@pytest.mark.parametrize("reduce", ["tiled", "ordered"])
+@pytest.mark.parametrize("renumber", [True, False])
+def test_packed_host_rows_match_the_x4_host_call(reduce, renumber):
+    """EBB_MAP_HOST_XYZ: 12-byte (x, y, z) host rows for 4-float fields, widened
+    and narrowed on the device, in the chunked form (tiled, many tiles) and
+    the whole-field form (ordered): the outputs equal, bit for bit, those of
+    the same call on 16-byte host elements, and match the oracle; the
+    accumulating call adds; one field for u and w works too."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(12, "stvk", seed=53, permute=True)
+    f, Kw, _ = oracle_maps(m, mu, lam, u, w, "stvk")
+    red = {"tiled": abi.EBB_REDUCE_TILED, "ordered": abi.EBB_REDUCE_TILED_ORDERED}[reduce]
+    with DeviceTetMesh(m.X, m.tets, mu, lam, renumber_verts=renumber) as dm:
+        assert abi.ebb_relation_info(dm.ctx, dm.tets).ntiles >= 16
+        for name in ("u", "w", "f", "k"):
+            dm.vertex_field(name, torch.float32, x4=True)
+        ur, wr = dm.rows(u), dm.rows(w)
+        uh, wh = _host_xyz(ur), _host_xyz(wr)
+        fh, kh = torch.full_like(uh, 7.0).pin_memory(), torch.full_like(uh, 7.0).pin_memory()
+        o = abi.map_opts(abi.EBB_STVK, precision=abi.EBB_PREC_F32, reduce=red,
+                         flags=abi.EBB_MAP_ZERO_OUT | abi.EBB_MAP_HOST_XYZ)
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
+        assert rel_err(dm.caller(fh.double().numpy()), f) < 1e-5
+        assert rel_err(dm.caller(kh.double().numpy()), Kw) < 1e-5
+        assert torch.equal(dm._tensors["f"][:, :3].cpu(), fh)       # the fields hold the same values
+        # the same call on 16-byte host elements
+        ux, wx = _host(ur, "x4"), _host(wr, "x4")
+        fx, kx = torch.zeros_like(ux).pin_memory(), torch.zeros_like(ux).pin_memory()
+        ox = abi.map_opts(abi.EBB_STVK, precision=abi.EBB_PREC_F32, reduce=red, flags=abi.EBB_MAP_ZERO_OUT)
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", ux, wx, fx, kx, ox)
+        if reduce == "ordered":
+            assert torch.equal(fx[:, :3], fh) and torch.equal(kx[:, :3], kh)
+        else:
+            assert rel_err(fx[:, :3].double().numpy(), fh.double().numpy()) < 1e-6
+        # accumulation
+        o.flags = abi.EBB_MAP_HOST_XYZ
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
+        assert rel_err(dm.caller(fh.double().numpy()), 2 * f) < 1e-5
+        assert rel_err(dm.caller(kh.double().numpy()), 2 * Kw) < 1e-5
+        # one field for u and w
+        o.flags = abi.EBB_MAP_ZERO_OUT | abi.EBB_MAP_HOST_XYZ
+        abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "u", "f", "k", uh, uh, fh, kh, o)
+        _, Ku, _ = oracle_maps(m, mu, lam, u, u, "stvk")
+        assert rel_err(dm.caller(kh.double().numpy()), Ku) < 1e-5
+
+
+def test_packed_host_rows_need_float4_fields():
+    """EBB_MAP_HOST_XYZ on 3-plane or FP64 fields is refused before anything
+    is copied: the host outputs and the device fields keep their values."""
+    abi = _abi()
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    m, mu, lam, u, w = problem(3, "stvk", seed=55)
+    for dt in (torch.float32, torch.float64):
+        with DeviceTetMesh(m.X, m.tets, mu, lam) as dm:
+            for name in ("u", "w", "f", "k"):
+                dm.vertex_field(name, dt)
+            tu = dm._tensors["u"]
+            tu.fill_(3.0)
+            uh, wh = _host_xyz(u), _host_xyz(w)
+            fh = torch.full_like(uh, 5.0).pin_memory()
+            kh = torch.full_like(uh, 5.0).pin_memory()
+            prec = abi.EBB_PREC_F64 if dt == torch.float64 else abi.EBB_PREC_F32
+            o = abi.map_opts(abi.EBB_STVK, precision=prec, flags=abi.EBB_MAP_ZERO_OUT | abi.EBB_MAP_HOST_XYZ)
+            with pytest.raises(abi.EbbError) as ei:
+                abi.ebb_map_tet_force_Kv_host(dm.ctx, dm.tets, "u", "w", "f", "k", uh, wh, fh, kh, o)
+            assert ei.value.status == abi.EBB_ERR_ARG
+            torch.cuda.synchronize()
+            assert (fh == 5.0).all() and (kh == 5.0).all() and (tu == 3.0).all()
