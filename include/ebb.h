@@ -262,8 +262,9 @@ ebb_status_t ebb_field_bind(ebb_rel_t rel, const char* name, ebb_dtype_t dtype,
  * tet B = Dm^-1 and V = det(Dm)/6 in FP64 from verts.X (EBB_ERR_INVERTED if
  * det(Dm) <= 0) plus FP32 copies, snapshots per-tet Lame fields, and with
  * EBB_FINALIZE_COLOR builds the vertex-conflict colouring.  Synchronous.
- * Rebinding verts.X, tets.v, tets.mu or tets.lambda requires finalizing
- * again. */
+ * EBB_ERR_NOMEM if device or host memory for the layout runs out (the
+ * relation is then left unfinalized).  Rebinding verts.X, tets.v, tets.mu or
+ * tets.lambda requires finalizing again. */
 ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags);
 
 /* ---- maps over tets (Section 4.1 kernels, Section 6.2 reductions) ------- */
@@ -301,7 +302,8 @@ ebb_status_t ebb_map_tet_force_Kv(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
  * with EBB_MAP_HOST_XYZ on EBB_F32X4 fields, N_v packed (x, y, z) FP32 rows;
  * page-locked host memory lets the copies run at full speed, pageable memory
  * works more slowly.  With the tiled reduction on fields the map reads in
- * place, and at least 16 tiles, the call runs in 8 consecutive tile chunks:
+ * place, and at least 12 tiles, the call runs in 6 consecutive tile chunks
+ * (1, 3, 4, 4, 3 and 1 sixteenths of the tiles):
  * the rows chunk c reads are copied in on one library stream, its tiles are
  * mapped on the context's stream as soon as they have landed, and the rows
  * no later chunk adds to are copied out on another library stream, so the

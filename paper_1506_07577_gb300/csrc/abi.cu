@@ -478,8 +478,7 @@ ebb_status_t ebb_field_bind(ebb_rel_t rel, const char* name, ebb_dtype_t dtype, 
   return EBB_OK;
 }
 
-ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
-  if (!tets) return EBB_ERR_ARG;
+static ebb_status_t relation_finalize(ebb_rel_t tets, uint32_t flags) {
   ebb_ctx_s* ctx = tets->ctx;
   ctx->last_error.clear();
   const Field* kv = find_field(tets, "v");
@@ -697,6 +696,18 @@ ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
   return EBB_OK;
 }
 
+// Host memory for the layout (keys, orders, tile tables) runs out as an
+// exception of the set-up code; it becomes a status here.
+ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
+  if (!tets) return EBB_ERR_ARG;
+  try {
+    return relation_finalize(tets, flags);
+  } catch (const std::bad_alloc&) {
+    free_tet_data(tets);
+    return set_error(tets->ctx, EBB_ERR_NOMEM, "host memory for the tet layout ran out");
+  }
+}
+
 ebb_status_t ebb_map_tet_forces(ebb_ctx_t ctx, ebb_rel_t tets, const char* u, const char* f_out,
                                 const ebb_map_opts_t* opts) {
   MapCall mc;
@@ -775,7 +786,7 @@ ebb_status_t host_plan(ebb_ctx_s* ctx, ebb_rel_s* tets, HostPlan** out) {
   const int own0 = tets->vown >= 0 ? tets->vown : nv;
   std::vector<int> lo_own(K, own0), hi_own(K, 0);
   for (int c = 0; c < K; ++c) {
-    p->tile_off[c + 1] = (int)((long long)(c + 1) * ntiles / K);
+    p->tile_off[c + 1] = chunk_first_tile(c + 1, ntiles, K);
     const int r0 = hdr[p->tile_off[c]].z;
     const int r1 = hdr[p->tile_off[c + 1] - 1].z + hdr[p->tile_off[c + 1] - 1].x;
     for (int t = r0; t < r1; ++t) {

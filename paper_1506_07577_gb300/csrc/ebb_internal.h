@@ -7,43 +7,12 @@
 #include <cstdint>
 #include <map>
 #include <string>
-#include <system_error>
-#include <thread>
 #include <vector>
 
 #include "../../include/ebb.h"
+#include "host_parallel.h"
 
 namespace ebb {
-
-// Host set-up work split over threads: fn(lo, hi) runs over contiguous
-// ranges covering [0, n), at least `min_chunk` items each, on up to 16 host
-// threads (the calling thread takes the first range; a thread that cannot
-// be started leaves its range to the caller).  fn must only write state of
-// its own range.
-template <class F>
-void parallel_ranges(int n, int min_chunk, F&& fn) {
-  const int hw = (int)std::thread::hardware_concurrency();
-  const int nth = std::max(1, std::min({hw > 0 ? hw : 1, 16, n / std::max(1, min_chunk)}));
-  auto lo_of = [&](int i) { return (int)((long long)n * i / nth); };
-  std::vector<std::thread> th;
-  std::vector<int> inline_ranges;
-  for (int i = 1; i < nth; ++i) {
-    try {
-      th.emplace_back([&fn, lo = lo_of(i), hi = lo_of(i + 1)] { fn(lo, hi); });
-    } catch (const std::system_error&) {
-      inline_ranges.push_back(i);
-    }
-  }
-  fn(0, lo_of(1));
-  for (int i : inline_ranges) fn(lo_of(i), lo_of(i + 1));
-  for (auto& t : th) t.join();
-}
-
-// Stable order of `key` (its low `bits` bits): order[i] = the index of the
-// i-th smallest key, equal keys in index order (LSD radix sort, 11-bit
-// digits).  With `order` non-empty on entry, that order is refined instead:
-// the result sorts by key and keeps the given order among equal keys.
-void radix_order(const std::vector<uint64_t>& key, int bits, std::vector<int>& order);
 
 // Device status word: [0] = first error code, [1] = row index it refers to.
 enum { ERRW_CODE = 0, ERRW_INDEX = 1, ERRW_WORDS = 4 };
@@ -197,7 +166,7 @@ struct StepScratch;   // defined in cg.cu
 // Morton order consecutive tiles touch nearly consecutive rows, so the
 // copies of one chunk overlap the map of another.
 struct HostPlan {
-  static constexpr int kChunks = 8;
+  static constexpr int kChunks = 6;
   unsigned gen = ~0u;
   int K = 0;
   std::vector<int> tile_off, need_hi, done_lo;
@@ -206,6 +175,19 @@ struct HostPlan {
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   cudaEvent_t ev_in[kChunks] = {}, ev_map[kChunks] = {};
 };
+// First tile of chunk c of K consecutive chunks over ntiles tiles (c = K:
+// ntiles).  With K = HostPlan::kChunks the chunks hold 1, 3, 4, 4, 3 and 1
+// sixteenths of the tiles: the first and last are small, so that the copy-in
+// before the first map and the copy-out after the last are short, and the
+// others large, so that few launches pay a map's ramp and tail.  Other
+// counts cut evenly.
+inline int chunk_first_tile(int c, int ntiles, int K) {
+  static const int kEnd[HostPlan::kChunks + 1] = {0, 1, 4, 8, 12, 15, 16};
+  static_assert(HostPlan::kChunks == 6, "chunk weights");
+  if (K != HostPlan::kChunks) return (int)((long long)c * ntiles / K);
+  return (int)((long long)kEnd[c] * ntiles / kEnd[HostPlan::kChunks]);
+}
+
 struct BatchScratch;  // defined in batched.cu
 
 struct ebb_rel_impl;

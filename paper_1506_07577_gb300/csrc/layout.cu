@@ -528,8 +528,8 @@ void chunked_vertex_order(const std::vector<int4>& keys, const std::vector<doubl
   // first and last chunk of every vertex, and its first tet
   std::vector<int> fc(nv, -1), lc(nv, -1), first(nv, nt);
   for (int c = 0; c < K; ++c) {
-    const int t0 = tet_off[(size_t)((long long)c * ntiles / K)];
-    const int t1 = tet_off[(size_t)((long long)(c + 1) * ntiles / K)];
+    const int t0 = tet_off[(size_t)chunk_first_tile(c, ntiles, K)];
+    const int t1 = tet_off[(size_t)chunk_first_tile(c + 1, ntiles, K)];
     for (int t = t0; t < t1; ++t) {
       const int k[4] = {sorted[t].x, sorted[t].y, sorted[t].z, sorted[t].w};
       for (int a = 0; a < 4; ++a) {
