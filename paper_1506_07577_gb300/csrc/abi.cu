@@ -696,6 +696,19 @@ static ebb_status_t relation_finalize(ebb_rel_t tets, uint32_t flags) {
   return EBB_OK;
 }
 
+// Re-tiling, with host memory that runs out (an exception of the set-up
+// code) as a status; the tiles may then be gone, so the relation has to be
+// finalized again.
+static ebb_status_t retile(ebb_ctx_s* ctx, ebb_rel_s* tets, int cap) {
+  try {
+    return rebuild_tiles(ctx, tets, cap);
+  } catch (const std::bad_alloc&) {
+    free_tet_data(tets);
+    tets->finalized = false;
+    return set_error(ctx, EBB_ERR_NOMEM, "host memory for the tile tables ran out; finalize the relation again");
+  }
+}
+
 // Host memory for the layout (keys, orders, tile tables) runs out as an
 // exception of the set-up code; it becomes a status here.
 ebb_status_t ebb_relation_finalize(ebb_rel_t tets, uint32_t flags) {
@@ -1141,7 +1154,7 @@ ebb_status_t ebb_relation_set_tuning(ebb_ctx_t ctx, ebb_rel_t tets, int32_t mode
   if (reduce == EBB_REDUCE_COLOR && !tets->has_colour)
     return set_error(ctx, EBB_ERR_STATE, "colour reduction requested but relation finalized without EBB_FINALIZE_COLOR");
   if (tets->tile_cap != tile_tets) {
-    ebb_status_t s = rebuild_tiles(ctx, tets, tile_tets);
+    ebb_status_t s = retile(ctx, tets, tile_tets);
     if (s) return s;
   }
   tets->tuned[model][precision] = (signed char)reduce;
@@ -1223,7 +1236,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
   const int caps[3] = {128, 96, 64};
   for (int ci = 0; ci < 3 && !s; ++ci) {
     if (tets->tile_cap != caps[ci]) {
-      s = rebuild_tiles(ctx, tets, caps[ci]);
+      s = retile(ctx, tets, caps[ci]);
       if (s) break;
     }
     double us = 0.0;
@@ -1235,7 +1248,7 @@ ebb_status_t ebb_relation_autotune(ebb_ctx_t ctx, ebb_rel_t tets, const char* u,
       best_cap = caps[ci];
     }
   }
-  if (!s && tets->tile_cap != best_cap) s = rebuild_tiles(ctx, tets, best_cap);
+  if (!s && tets->tile_cap != best_cap) s = retile(ctx, tets, best_cap);
   if (!s && !f64 && !x4) {
     // the same tile size with the operands staged vertex-interleaved
     tets->stage_interleaved = true;
