@@ -105,20 +105,23 @@ struct BlobLayout {
   bool planes = false;     // per-tet data as field planes instead of row records
 };
 
-// Partial-sum index of the ordered tiled variant (EBB_REDUCE_TILED_ORDERED):
-// reduction unit i of tile t that adds a vertex's run total (the run's first
-// lane) owns partial row t * kTileTets + i; vertex v's rows are
-// vp_ent[vp_off[v] .. vp_off[v+1]), in increasing row (= tile, then unit)
-// order.  (Rows numbered vertex by vertex instead, so that the second pass
-// reads them contiguously, measured slower: the tile pass then loads each
-// run's row index.)
+// Partial-row index of the ordered tiled variant (EBB_REDUCE_TILED_ORDERED).
+// The rows are numbered vertex by vertex: the vertices that own rows are
+// listed in order of first use by the tiles (ord_vtx, n_ord of them), and
+// vertex ord_vtx[i] owns rows ord_off[i] .. ord_off[i+1], one per tile whose
+// units add into it, in tile order.  unit_row[t * kTileTets + i] is the row
+// of reduction unit i of tile t when that unit heads a vertex's run (-1
+// otherwise); the tile pass reads it at the start of the tile, so that the
+// second pass reads every vertex's rows contiguously.
 struct Tiles {
   int ntiles = 0;
   unsigned char* blob32 = nullptr;
   unsigned char* blob64 = nullptr;
   BlobLayout L32, L64;
-  int* vp_off = nullptr;
-  int* vp_ent = nullptr;
+  int n_ord = 0;
+  int* ord_off = nullptr;
+  int* ord_vtx = nullptr;
+  int* unit_row = nullptr;
   // Partial rows (ntiles * kTileTets rows of 3 fields x 4 values), [0] FP32,
   // [1] FP64; allocated at first use.
   void* partial[2] = {nullptr, nullptr};
@@ -258,8 +261,10 @@ struct MapIO {
   T* Kw = nullptr;         // K w accumulator
   T* d = nullptr;          // diag(K) accumulator
   // Ordered tiled reduction only: each run total is stored to its partial
-  // row (NF groups of 4 values: x, y, z, 0) instead of added to the fields.
+  // row (NF groups of 4 values: x, y, z, 0; row index from unit_row) instead
+  // of added to the fields.
   T* part = nullptr;
+  const int* unit_row = nullptr;
   // Tiled (unordered) reduction: map only the tiles [tile_begin, tile_end)
   // (tile_end < 0: to the last tile).
   int tile_begin = 0;

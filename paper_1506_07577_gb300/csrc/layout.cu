@@ -399,8 +399,9 @@ int tile_prefix(const std::vector<int4>& sorted, int nv, int cap, std::vector<un
 void free_tiles(Tiles& tl) {
   cudaFree(tl.blob32);
   cudaFree(tl.blob64);
-  cudaFree(tl.vp_off);
-  cudaFree(tl.vp_ent);
+  cudaFree(tl.ord_off);
+  cudaFree(tl.ord_vtx);
+  cudaFree(tl.unit_row);
   cudaFree(tl.partial[0]);
   cudaFree(tl.partial[1]);
   const int n = tl.ntiles;
@@ -672,17 +673,31 @@ ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector
   if (ntiles == 0) return EBB_OK;
   cudaStream_t st = ctx->stream;
   {
-    // Partial index of the ordered tiled variant: each run-head unit owns
-    // the row tile * kTileTets + unit; a vertex lists its rows in row order.
+    // Partial-row index of the ordered tiled variant: vertices in order of
+    // first use by the run-head units (tile by tile), each vertex's rows
+    // consecutive and in tile order.
     const int nv = (int)tets->verts->size;
-    std::vector<int> vp_off((size_t)nv + 1, 0), vp_ent;
-    for (int pass = 0; pass < 2; ++pass) {
-      std::vector<int> fill;
-      if (pass == 1) {
-        for (int v = 0; v < nv; ++v) vp_off[v + 1] += vp_off[v];
-        vp_ent.resize(vp_off[nv]);
-        fill.assign(vp_off.begin(), vp_off.end() - 1);
+    std::vector<int> pos(nv, -1), ord_vtx, count;
+    for (int t = 0; t < ntiles; ++t) {
+      const unsigned char* b = prefix.data() + (size_t)t * kBlobPrefix;
+      const uint32_t* units = reinterpret_cast<const uint32_t*>(b + kBlobUnits);
+      const int* bvtx = reinterpret_cast<const int*>(b + kBlobVtx);
+      for (int i = 0; i < kTileTets; ++i) {
+        if (!((units[i] >> 26) & 1u)) continue;
+        const int v = bvtx[(units[i] >> 14) & 0xffu];
+        if (pos[v] < 0) {
+          pos[v] = (int)ord_vtx.size();
+          ord_vtx.push_back(v);
+          count.push_back(0);
+        }
+        ++count[pos[v]];
       }
+    }
+    std::vector<int> ord_off(ord_vtx.size() + 1, 0);
+    for (size_t k = 0; k < ord_vtx.size(); ++k) ord_off[k + 1] = ord_off[k] + count[k];
+    std::vector<int> unit_row((size_t)ntiles * kTileTets, -1);
+    {
+      std::vector<int> fill(ord_off.begin(), ord_off.end() - 1);
       for (int t = 0; t < ntiles; ++t) {
         const unsigned char* b = prefix.data() + (size_t)t * kBlobPrefix;
         const uint32_t* units = reinterpret_cast<const uint32_t*>(b + kBlobUnits);
@@ -690,15 +705,14 @@ ebb_status_t build_tile_blobs(ebb_ctx_s* ctx, ebb_rel_s* tets, const std::vector
         for (int i = 0; i < kTileTets; ++i) {
           if (!((units[i] >> 26) & 1u)) continue;
           const int v = bvtx[(units[i] >> 14) & 0xffu];
-          if (pass == 0)
-            ++vp_off[(size_t)v + 1];
-          else
-            vp_ent[fill[v]++] = t * kTileTets + i;
+          unit_row[(size_t)t * kTileTets + i] = fill[pos[v]]++;
         }
       }
     }
-    cudaError_t e = upload(&tl.vp_off, vp_off, st);
-    if (e == cudaSuccess) e = upload(&tl.vp_ent, vp_ent, st);
+    tl.n_ord = (int)ord_vtx.size();
+    cudaError_t e = upload(&tl.ord_off, ord_off, st);
+    if (e == cudaSuccess) e = upload(&tl.ord_vtx, ord_vtx, st);
+    if (e == cudaSuccess) e = upload(&tl.unit_row, unit_row, st);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return set_error(ctx, EBB_ERR_NOMEM, "device allocation for the tile partial index failed");

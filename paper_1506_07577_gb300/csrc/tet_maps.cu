@@ -206,24 +206,24 @@ vertex_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ e
   }
 }
 
-// Second pass of the ordered tiled variant: vertex order[i] adds its partial
-// rows (NF groups of x, y, z, 0) in row order, i.e. tile by tile, into the
-// fields.
+// Second pass of the ordered tiled variant: vertex vtx[i] adds its partial
+// rows off[i] .. off[i+1] (NF groups of x, y, z, 0; consecutive, in tile
+// order) into the fields.
 template <typename T, int NF, bool AOS>
 __global__ void __launch_bounds__(kSumThreads)
-partial_sum_kernel(int nv, const int* __restrict__ off, const int* __restrict__ ent, const int* __restrict__ order,
+partial_sum_kernel(int n, int nv, const int* __restrict__ off, const int* __restrict__ vtx,
                    const T* __restrict__ part, T* out0, T* out1, T* out2, const int* active) {
   if (active != nullptr && *active == 0) return;
   const int i = blockIdx.x * kSumThreads + threadIdx.x;
-  if (i >= nv) return;
-  const int v = order[i];
+  if (i >= n) return;
+  const int v = vtx[i];
   T acc[NF][3];
 #pragma unroll
   for (int f = 0; f < NF; ++f) acc[f][0] = acc[f][1] = acc[f][2] = T(0);
-  const int e0 = off[v], e1 = off[v + 1];
+  const int e0 = off[i], e1 = off[i + 1];
 #pragma unroll 2
   for (int e = e0; e < e1; ++e) {
-    const T* p = part + (size_t)__ldg(ent + e) * (4 * NF);
+    const T* p = part + (size_t)e * (4 * NF);
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if constexpr (sizeof(T) == 4) {
@@ -409,6 +409,7 @@ cudaError_t launch_tiles_ordered(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& 
   const int nv = (int)rel->verts->size;
   if (tl.ntiles == 0 || nv == 0) return cudaSuccess;
   MapIO<T> pio = io;
+  pio.unit_row = tl.unit_row;
   cudaError_t e = partial_buffer<T>(rel, stream, &pio.part);
   if (e != cudaSuccess) return e;
   e = launch_tiles<T, MODEL, OPS, AOS, true>(rel, mu0, lam0, pio, active, stream);
@@ -418,8 +419,9 @@ cudaError_t launch_tiles_ordered(ebb_rel_s* rel, T mu0, T lam0, const MapIO<T>& 
   if (OPS & OP_FORCE) outs[f++] = io.f;
   if (OPS & OP_KV) outs[f++] = io.Kw;
   if (OPS & OP_DIAG) outs[f++] = io.d;
-  partial_sum_kernel<T, NF, AOS><<<(nv + kSumThreads - 1) / kSumThreads, kSumThreads, 0, stream>>>(
-      nv, tl.vp_off, tl.vp_ent, rel->vindex.order, pio.part, outs[0], outs[1], outs[2], active);
+  if (tl.n_ord == 0) return cudaSuccess;
+  partial_sum_kernel<T, NF, AOS><<<(tl.n_ord + kSumThreads - 1) / kSumThreads, kSumThreads, 0, stream>>>(
+      tl.n_ord, nv, tl.ord_off, tl.ord_vtx, pio.part, outs[0], outs[1], outs[2], active);
   return cudaGetLastError();
 }
 

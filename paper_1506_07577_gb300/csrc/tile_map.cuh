@@ -169,13 +169,9 @@ __device__ __forceinline__ void tile_init(const TileView<T, OPS>& V) {
 // copies).  AOS: vertex-interleaved operands (MapIO::aos): the producer
 // copies each vertex's 16 bytes with one cp.async, the reduction adds each
 // vertex's three components with one vector atomic.  ORD: the ordered
-// variant, each run total stored to its partial row (MapIO::part) instead
-// of added into the fields.
-// Partial row of reduction unit `unit` in this CTA's j-th tile (ordered
-// tiled variant).
-__device__ __forceinline__ size_t part_row(int j, int G, int unit) {
-  return ((size_t)blockIdx.x + (size_t)j * G) * kTileTets + unit;
-}
+// variant, each run total stored to its partial row (MapIO::part, row index
+// MapIO::unit_row, read at the start of the tile) instead of added into the
+// fields.
 
 __device__ __forceinline__ void st_part4(float* p, float x, float y, float z) {
   *reinterpret_cast<float4*>(p) = make_float4(x, y, z, 0.f);
@@ -295,6 +291,10 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
     const unsigned char* st = ring + (size_t)sb * L.bytes;
     const T* su = slots + (size_t)sv * Z::slot_elems;
     const T* sw = su + 4 * Z::S;
+    // ordered variant: this unit's partial row, loaded now and used after
+    // phase 1 (the tile index is absolute: the ordered map maps every tile)
+    int urow = -1;
+    if constexpr (ORD) urow = __ldg(io.unit_row + ((size_t)blockIdx.x + (size_t)j * G) * TT + tid);
     T* sob = outs + (Z::OB == 2 ? (J & 1) : 0) * Z::out_elems;
     const bool ok = mbar_wait_or_abort(&full_b[sb], (J / RB) & 1u, abort_flag, wait_cycles) &&
                     mbar_wait_or_abort(&full_v[sv], (J / RV) & 1u, abort_flag, wait_cycles);
@@ -423,7 +423,7 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
         if constexpr (ORD) {
-          float* row = reinterpret_cast<float*>(io.part) + part_row(j, G, tid) * 8;
+          float* row = reinterpret_cast<float*>(io.part) + (size_t)urow * 8;
           *reinterpret_cast<float4*>(row) = make_float4(acc[0].x, acc[1].x, acc[2].x, 0.f);
           *reinterpret_cast<float4*>(row + 4) = make_float4(acc[0].y, acc[1].y, acc[2].y, 0.f);
         } else if constexpr (AOS) {
@@ -468,7 +468,7 @@ __device__ __forceinline__ bool tile_map_pass(const TileView<T, OPS>& V, int n_m
       if ((d >> 26) & 1u) {
         const int v = reinterpret_cast<const int*>(st + kBlobVtx)[(d >> 14) & 0xffu];
         if constexpr (ORD) {
-          T* row = io.part + part_row(j, G, tid) * (4 * NF);
+          T* row = io.part + (size_t)urow * (4 * NF);
 #pragma unroll
           for (int f = 0; f < NF; ++f) st_part4(row + 4 * f, acc[f], acc[NF + f], acc[2 * NF + f]);
         } else if constexpr (AOS) {
