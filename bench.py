@@ -35,6 +35,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -90,6 +91,30 @@ def kernel_sources_hash(files=None):
         with open(os.path.join(ROOT, "paper_1506_07577_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def host_info():
+    """The host the CPU figures come from: logical CPUs and the CPU model."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model in ("", platform.machine()):
+        try:  # Arm hosts name the model in lscpu, not in /proc/cpuinfo
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
 
 
 def _peaks():
@@ -831,7 +856,7 @@ def cpu_baseline(seconds, head, nh64, bat, adj):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    out = {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    out = {"value": done / el, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
            "sample": f"FP64 oracle force+K*w over the first {sample} (randomly numbered) tets of the permuted "
                      f"128^3 StVK mesh, repeated for {el:.1f} s ({done} tet evaluations), numpy single thread"}
     rng = np.random.default_rng(0)
@@ -927,7 +952,7 @@ def run_reference(args, rank, world):
             "config": {"workload": f"{args.n}^3 cube grid, 5 tets/cube, vertex and tet ids permuted, StVK E 1e5 "
                                    "nu 0.45, force+K*w", "n_tets": m.n_tets, "n_verts": m.n_verts,
                        "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"each step: FP64 oracle force+K*w over the first {sample} tets"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
