@@ -829,9 +829,79 @@ def adjoint_rollout(abi, torch, local_rank, args):
     return out, {"mesh": (ms, mus, lams, v0s), "grads": small}
 
 
+def small_configs(abi, torch, local_rank, stream):
+    """The launch-bound configurations, reported as us per step and per map
+    (their data fit in L2, so no roofline fraction):
+      C1: 8^3 grid, StVK E = 1e5, nu = 0.45, FP64, one implicit step from rest
+          (dt 1e-3, rho 1000, 50 CG iterations, early stop at 1e-14);
+      C3: 32^3 grid, StVK with per-tet Lame parameters within +-20%, FP64,
+          one implicit step from a random velocity (rtol 1e-12).
+    Each also times the FP64 fused force + K*w map on a random state.  The C1
+    step's result goes to the CPU leg for the oracle's check."""
+    from paper_1506_07577_gb300.device_mesh import DeviceTetMesh
+    dev = torch.device("cuda", local_rank)
+    out, c1_check = {}, None
+    cases = (("C1_8cubed", 8, False, 50, 1e-14, 0.0), ("C3_32cubed", 32, True, 4000, 1e-12, 0.05))
+    for name, n, per_tet, iters, rtol, vscale in cases:
+        m = meshgen.cube_grid(n, jitter=0.01, seed=1 if n == 8 else 3)
+        if per_tet:
+            mu, lam = meshgen.material_perturbed_lame(m.n_tets, 1e5, 0.45, 0.2, seed=3)
+            mu0, lam0 = 0.0, 0.0
+        else:
+            mu0, lam0 = (float(x) for x in meshgen.lame_from_young(1e5, 0.45))
+        v0 = vscale * meshgen.random_field(m.n_verts, seed=3)
+        v0[m.pinned] = 0.0
+        u = meshgen.random_displacement(m.X, n, amp=0.05, seed=4, smooth=0.01)
+        w = meshgen.random_field(m.n_verts, seed=5)
+        with DeviceTetMesh(m.X, m.tets, mu if per_tet else None, lam if per_tet else None, device=local_rank,
+                           stream=stream) as dm:
+            dm.bind("pinned", torch.from_numpy(m.pinned.astype(np.uint8)).to(dev))
+            us = dm.vertex_field("u", torch.float64)
+            vs = dm.vertex_field("v", torch.float64, value=v0)
+            v_init = vs.clone()
+            prm = abi.step_params(abi.EBB_STVK, 1e-3, 1000.0, mu0, lam0, precision=abi.EBB_PREC_F64,
+                                  max_iters=iters, rtol=rtol)
+            ts, reps = [], []
+            with torch.cuda.stream(stream):
+                for k in range(8):
+                    us.zero_()
+                    vs.copy_(v_init)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    reps.append(abi.ebb_cg_implicit_step(dm.ctx, dm.tets, "u", "v", "pinned", prm))
+                    b.record(stream)
+                    b.synchronize()
+                    if k >= 3:
+                        ts.append(a.elapsed_time(b) * 1e3)
+            rec = {"n_tets": m.n_tets, "n_verts": m.n_verts, "fp64_step_us": statistics.median(ts),
+                   "cg_iters": int(reps[-1].iters)}
+            if n == 8:
+                c1_check = {"mesh": m, "mu": mu0, "lam": lam0, "v0": v0,
+                            "u": dm._tensors["u"].cpu().numpy().T.copy(), "v": dm._tensors["v"].cpu().numpy().T.copy()}
+            dm.vertex_field("mu_", torch.float64, value=u)
+            dm.vertex_field("mw_", torch.float64, value=w)
+            dm.vertex_field("mf_", torch.float64)
+            dm.vertex_field("mk_", torch.float64)
+            o = abi.map_opts(abi.EBB_STVK, mu0, lam0, precision=abi.EBB_PREC_F64, flags=abi.EBB_MAP_ZERO_OUT)
+            ms = []
+            with torch.cuda.stream(stream):
+                for k in range(23):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    abi.ebb_map_tet_force_Kv(dm.ctx, dm.tets, "mu_", "mw_", "mf_", "mk_", o)
+                    b.record(stream)
+                    b.synchronize()
+                    if k >= 3:
+                        ms.append(a.elapsed_time(b) * 1e3)
+            rec["fp64_fused_map_us"] = statistics.median(ms)
+            rec["note"] = "launch-bound (data fit in L2): warm, no roofline fraction"
+            out[name] = rec
+    return out, c1_check
+
+
 # ---- the CPU leg: oracle timing and every result's error vs the oracle -----
 
-def cpu_baseline(seconds, head, nh64, bat, adj):
+def cpu_baseline(seconds, head, nh64, bat, adj, c1=None):
     """Times the FP64 oracle's force + K*w (single thread, numpy) on a
     contiguous sample of the headline mesh's tets, then checks the timed GPU
     results against the oracle: the maps at sampled vertices (each recomputed
@@ -839,8 +909,8 @@ def cpu_baseline(seconds, head, nh64, bat, adj):
     through the oracle's linear system at sampled free vertices (b and A dv
     from the tets around each vertex, dv the GPU's velocity change), the
     batched step on its smallest, a middle and its largest mesh (whole
-    oracle steps), and the rollout gradient on the small mesh (the oracle's
-    adjoint)."""
+    oracle steps), the rollout gradient on the small mesh (the oracle's
+    adjoint) and the C1 step (a whole oracle step)."""
     from oracle import adjoint, fem, implicit
     m, mu, lam, u, w = head["workload"]
     sample = min(m.n_tets, 131072)
@@ -922,6 +992,15 @@ def cpu_baseline(seconds, head, nh64, bat, adj):
         errs["adjoint_rollout_grad_4cubed"] = max(
             float(np.max(np.abs(a - b_)) / np.max(np.abs(b_))) for a, b_ in ((tgu, gu), (tgv, gv), (tgmu, gmu),
                                                                              (tglam, glam)))
+    if c1 is not None:
+        # the C1 FP64 step against the oracle's step (the whole field)
+        m = c1["mesh"]
+        B, V = fem.rest_shape(m.X, m.tets)
+        mass = fem.lumped_mass(V, m.tets, 1000.0, m.n_verts)
+        uo, vo, _ = implicit.implicit_step(m.X, np.zeros_like(m.X), c1["v0"], m.tets, B, V, mass, c1["mu"],
+                                           c1["lam"], fem.STVK, 1e-3, np.array(G), m.pinned, 50, 1e-14)
+        errs["c1_fp64_step_v"] = float(np.max(np.abs(c1["v"] - vo)) / np.max(np.abs(vo)))
+        errs["c1_fp64_step_u"] = float(np.max(np.abs(c1["u"] - uo)) / np.max(np.abs(uo)))
     out["gpu_errors_vs_oracle"] = errs
     return out
 
@@ -1098,13 +1177,14 @@ def run_ours(args, rank, world, local_rank):
     head = run_headline(args, abi, torch, dev, local_rank, stream, flush, dist, world, barrier)
     nt, nv = head["n_tets"], head["n_verts"]
     sub = {}
-    nh64 = bat = adj = None
+    nh64 = bat = adj = c1 = None
     if not args.headline_only:
         sub["nh64"], nh64 = run_nh64(args, abi, torch, local_rank, stream, flush)
         if args.batch_meshes > 0:
             sub["batched_step"], bat = batched_steps(abi, torch, local_rank, args)
         if not args.no_adjoint:
             sub["adjoint_rollout"], adj = adjoint_rollout(abi, torch, local_rank, args)
+        sub["small_configs"], c1 = small_configs(abi, torch, local_rank, stream)
 
     peak, peak_kind = _peaks()
     bpt = algorithmic_bytes_per_tet(nv, nt, False)
@@ -1153,7 +1233,7 @@ def run_ours(args, rank, world, local_rank):
             "reduction_variants": head["variants"]}
     line.update(sub)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, head, nh64, bat, adj)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, head, nh64, bat, adj, c1)
     print(json.dumps(line), flush=True)
 
 
